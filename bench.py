@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused horizontal + vertical decimating FIR (the downscaler
+filter stage of arXiv:1103.4881, Sec. 3) on one B300 per rank.
+
+Workload (default): 64 fp32 frames of 1080x1920, uniform [0,1) plus a seeded
+smooth gradient, 3/8 decimation with 8 Lanczos-3 taps per phase -> 405x720.
+One step = one batched persistent launch over the 64 frames, replayed from a
+CUDA graph.  Inputs (531 MB per step) are larger than the 126 MB L2, so every
+step streams them from HBM.
+
+Prints one JSON line (rank 0): frames/s, with the roofline of the fused
+kernel, the clocks seen during the timed region, the end-to-end figure
+through the host-buffer pipeline, the plain per-frame and unfused forms, and
+the CPU oracle as a baseline.  --impl reference times the CPU oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch64_1080x1920_f32")
+    ap.add_argument("--no-extras", action="store_true", help="skip per-frame / unfused / e2e / cpu legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs: torch copy, read+write)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
+
+
+def kernel_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("fused_fast.cu", "pixel.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1103_4881_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(workload)
+        if e and e.get("kernel_source_hash") == kernel_source_hash():
+            return int(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def time_cpu_oracle(w, budget_s=15.0):
+    """The oracle as it stands on this host's cores: whole frames of the
+    workload, OpenMP over frames, as many frames as fit the time budget."""
+    import numpy as np
+
+    import oracle
+    from paper_1103_4881_b300 import synth
+
+    cores = max(1, oracle.max_threads())
+    t = time.perf_counter()
+    x = synth.frames(w, range(1))
+    oracle.filter_f64(x, w.ratio[0], w.ratio[1], w.taps, threads=1)
+    one = time.perf_counter() - t
+    n = int(max(1, min(w.frames, cores * max(1, int(budget_s / max(one, 1e-3) / max(cores, 1))), 4 * cores)))
+    n = max(1, min(n, w.frames))
+    x = synth.frames(w, range(n))
+    fn = oracle.filter_u8 if w.dtype in (synth.DS_U8, synth.DS_U8_RGB) else oracle.filter_f64
+    t = time.perf_counter()
+    fn(x, w.ratio[0], w.ratio[1], w.taps, threads=0)
+    dt = time.perf_counter() - t
+    del x
+    return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "%d of the workload's %d frames (whole frames, FP64 loop nest, OpenMP over frames)" % (n, w.frames),
+            "seconds": round(dt, 3)}
+
+
+def reference_arm(args, w, rank, world):
+    """--impl reference: the CPU oracle, timed alone, on the same metric."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1103_4881_b300 import synth
+
+    cores = max(1, oracle.max_threads())
+    fn = oracle.filter_u8 if w.dtype in (synth.DS_U8, synth.DS_U8_RGB) else oracle.filter_f64
+    # one step = a band of rows from `cores` frames (one band per thread), sized
+    # so that warmup + steps take about a minute in total
+    x_full = synth.frames(w, range(min(cores, w.frames)))
+    q = w.ratio[1]
+    t = time.perf_counter()
+    fn(x_full[:1, : 8 * q], w.ratio[0], q, w.taps, threads=1)
+    per_row = (time.perf_counter() - t) / (8 * q)
+    total = max(1, args.steps + args.warmup)
+    rows = int(60.0 / total / max(per_row, 1e-9))
+    rows = max(q, min(w.height, rows - rows % q))
+    sample = x_full[:, :rows]
+    for _ in range(args.warmup):
+        fn(sample, w.ratio[0], q, w.taps, threads=0)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        fn(sample, w.ratio[0], q, w.taps, threads=0)
+    dt = time.perf_counter() - t
+    frames_per_step = sample.shape[0] * rows / w.height
+    value = frames_per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "frames": w.frames, "in": [w.height, w.width, w.channels],
+                   "out": [w.out_height, w.out_width, w.channels], "ratio": "%d/%d" % w.ratio, "taps": w.taps},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": "per step: the first %d rows of %d frames, one band per thread" % (rows, sample.shape[0])},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    from paper_1103_4881_b300 import synth
+
+    w = synth.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        reference_arm(args, w, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    import paper_1103_4881_b300 as ds
+    from paper_1103_4881_b300 import build
+
+    if rank == 0:
+        build.build()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+        dist.barrier()
+    dev_index = torch.cuda.current_device()
+
+    plan = ds.ds_plan_create(w.height, w.width, w.ratio, w.taps, w.dtype)
+    oh, ow, c = ds.ds_plan_out_shape(plan)
+    fin, fout = ds.ds_plan_frame_bytes(plan)
+    n = w.frames
+    x = synth.frames(w)
+    xin = torch.from_numpy(x).cuda()
+    out = torch.empty((n,) + w.out_frame_shape(), dtype=xin.dtype, device="cuda")
+    stream = torch.cuda.current_stream()
+    st = stream.cuda_stream
+
+    # the step: one batched persistent launch over the n frames, replayed as a CUDA graph
+    job = [(plan, xin.data_ptr(), out.data_ptr(), n)]
+    graph = ds.ds_graph_create(job)
+
+    def step():
+        ds.ds_graph_launch(graph, st)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ds.ds_stream_check(st)
+
+    def timed(fn, k):
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if pg:
+            t = torch.tensor([ms], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    ds.ds_launch_count()
+    with ClockSampler(dev_index) as clocks:
+        ms = timed(step, args.steps)
+    launches = ds.ds_launch_count()
+    ds.ds_stream_check(st)
+    clk = clocks.summary()
+
+    frames_total = n * world * args.steps
+    value = frames_total / (ms / 1e3)
+    alg_bytes = n * (fin + fout)  # input read once + output written once, per launch
+    launch_s = ms / 1e3 / args.steps
+    achieved = alg_bytes / launch_s / 1e9
+    peak, peak_src = measured_peak()
+    traffic = profiled_traffic(w.name)
+
+    line = {
+        "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "u8", 3: "u8"}[w.dtype], "data": "synthetic",
+        "config": {"workload": w.name, "frames_per_step": n, "in": [w.height, w.width, w.channels],
+                   "out": [oh, ow, c], "ratio": "%d/%d" % w.ratio, "taps": w.taps,
+                   "form": "batched persistent fused H+V kernel, CUDA graph replay",
+                   "l2": "inputs larger than L2 (%.0f MB per step vs 126 MB)" % (n * fin / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "peak_source": peak_src,
+                     "alg_bytes_per_launch": alg_bytes, "kernel_us": launch_s * 1e6},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+
+    if rank == 0 and not args.no_extras:
+        k2 = max(5, min(args.steps // 50, 50))
+        # plain per-frame: one ds_run per frame
+        def per_frame():
+            for i in range(n):
+                ds.ds_run(plan, xin.data_ptr() + i * fin, out.data_ptr() + i * fout, st)
+        per_frame()
+        ms_pf = timed(per_frame, k2)
+        # unfused two-kernel form over the batch
+        wsb = ds.ds_plan_workspace_bytes(plan) * n
+        ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+        def unfused():
+            ds.ds_run_unfused(plan, xin.data_ptr(), out.data_ptr(), n, ws.data_ptr(), wsb, st)
+        unfused()
+        ms_uf = timed(unfused, k2)
+        del ws
+        # batched without the graph (direct launch)
+        def direct():
+            ds.ds_run_frames(plan, xin.data_ptr(), out.data_ptr(), n, st)
+        direct()
+        ms_dl = timed(direct, k2)
+        line["forms"] = {
+            "batched_graph_fps": value / world,
+            "batched_direct_fps": n * k2 / (ms_dl / 1e3),
+            "per_frame_fused_fps": n * k2 / (ms_pf / 1e3),
+            "unfused_two_kernel_fps": n * k2 / (ms_uf / 1e3),
+            "unfused_alg_gbs": n * (fin + fout) * k2 / (ms_uf / 1e3) / 1e9,
+        }
+        # end to end through the C ABI with pinned host buffers (copies in the timed region)
+        host_in = torch.from_numpy(x).pin_memory()
+        host_out = torch.empty((n,) + w.out_frame_shape(), dtype=xin.dtype).pin_memory()
+        pipe = ds.ds_pipeline_create(plan, 4, 3)
+        ds.ds_pipeline_run(pipe, host_in.data_ptr(), host_out.data_ptr(), n)
+        k3 = 5
+        t = time.perf_counter()
+        for _ in range(k3):
+            ds.ds_pipeline_run(pipe, host_in.data_ptr(), host_out.data_ptr(), n)
+        dt = time.perf_counter() - t
+        ds.ds_pipeline_destroy(pipe)
+        line["e2e"] = {"value": n * k3 / dt, "unit": "frames/s", "h2d_bytes_per_step": n * fin,
+                       "d2h_bytes_per_step": n * fout, "api": "ds_pipeline_run (4-frame chunks, 3 streams)"}
+        ok = np.array_equal(host_out.numpy(), out.cpu().numpy())
+        line["e2e"]["matches_device_path"] = bool(ok)
+        del host_in, host_out
+        if world == 1:
+            line["cpu_baseline"] = time_cpu_oracle(w)
+    elif world > 1:
+        line["e2e"] = None
+
+    ds.ds_graph_destroy(graph)
+    ds.ds_destroy(plan)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

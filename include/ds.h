@@ -1,0 +1,247 @@
+/*
+ * ds.h -- C ABI of libds, a B300 (sm_103a) implementation of the separable
+ * decimating FIR filter stage ("downscaler") of Rodrigues, Guyomarc'h and
+ * Dekeyser, "Programming Massively Parallel Architectures using MARTE: a
+ * Case Study" (arXiv:1103.4881).
+ *
+ * The operation (paper Sec. 3, "Case Study: H.263 Video Downscaling"): a
+ * horizontal filter followed by a vertical filter; each maps packets of q
+ * input pixels to p output pixels ("interpolating packets of 8 pixels both
+ * row- and column-wise", 352 -> 132 per line at p/q = 3/8).  Every output is
+ * a K-tap dot product over a window of its line, the windows laid out by an
+ * Array-OL tiler (origin, paving, fitting) over a repetition space of
+ * independent elementary tasks (Sec. 3.A, "Downscaler Model").
+ *
+ * Readings of what the paper leaves open (identical in every entry point):
+ *   - n_out = floor(n_in * p / q) on each axis, the same ratio on both;
+ *   - output o = r*p + j (block r, phase j) is centred on input coordinate
+ *     r*q + (j + 1/2) q/p - 1/2 and reads the K pixels
+ *     r*q + b_j ... r*q + b_j + K - 1, b_j = floor(centre_j) - K/2 + 1,
+ *     each clamped to the frame (clamp-to-edge);
+ *   - taps: Lanczos-3 stretched by 6/K over the window, normalised to sum 1,
+ *     computed in FP64 on the host; FP32 copies for float data, Q14 integers
+ *     (round half up, residual on the largest tap) for uint8 data;
+ *   - FP32 / FP16 data: FP32 accumulation in tap order t = 0..K-1, FP32
+ *     intermediate, FP16 output rounded to nearest even;
+ *   - uint8 data: integer accumulation, (acc + 8192) >> 14 (floor shift) and
+ *     clamp to [0,255] after each pass, so the intermediate is a uint8 frame.
+ *
+ * Memory layout of every frame: dense row-major, no pitch; channels
+ * interleaved (DS_U8_RGB: R,G,B bytes per pixel).  A batch of n frames is n
+ * such frames back to back.  `in` / `out` are DEVICE pointers owned by the
+ * caller unless a function says otherwise.  All launches are asynchronous on
+ * the given stream (a cudaStream_t passed as void*; NULL = legacy default
+ * stream).  No entry point synchronises the device unless it says so.
+ *
+ * Errors: functions return DS_OK (0) or a negative ds_status; functions that
+ * return a pointer return NULL.  The reason is in ds_last_error() (a
+ * thread-local string, valid until the next call on the same thread).
+ */
+#ifndef DS_H
+#define DS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ds_plan ds_plan; /* opaque, immutable after creation (tuning aside) */
+
+/* Decimation ratio p/q: lowest terms, 0 < p < q, p <= 16, q <= 64. */
+typedef struct {
+    int p, q;
+} ds_ratio;
+
+/* Element type; the channel count is folded into it. */
+typedef enum {
+    DS_F32 = 0,    /* 1 channel, float                                  */
+    DS_F16 = 1,    /* 1 channel, IEEE half; FP32 accumulation            */
+    DS_U8 = 2,     /* 1 channel, uint8; Q14 taps                         */
+    DS_U8_RGB = 3  /* 3 interleaved channels, uint8; Q14 taps            */
+} ds_dtype;
+
+typedef enum {
+    DS_OK = 0,
+    DS_ERR_ARG = -1,         /* invalid argument                              */
+    DS_ERR_NOMEM = -2,       /* host or device allocation failed              */
+    DS_ERR_CUDA = -3,        /* a CUDA runtime/driver call failed             */
+    DS_ERR_TIMEOUT = -4,     /* a kernel gave up a bounded wait (device flag) */
+    DS_ERR_UNSUPPORTED = -5  /* valid, but not supported by this build        */
+} ds_status;
+
+/* ---------------------------------------------------------------------- */
+/* Plans                                                                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Create a plan for frames of in_h x in_w pixels filtered at `ratio` with
+ * `taps` (K) taps per phase (Sec. 3; Sec. 3.A for the tiler).  Host only:
+ * computes the phase windows and the FP64 / FP32 / Q14 tap tables and picks
+ * the kernel; no device memory is allocated and no kernel runs.
+ * Errors (NULL + ds_last_error): in_h or in_w < 1; ratio not in lowest terms
+ * or not in (0,1) or p > 16 or q > 64; taps odd or outside [2,16]; unknown
+ * dtype; an output extent of 0.
+ */
+ds_plan* ds_plan_create(int in_h, int in_w, ds_ratio ratio, int taps, ds_dtype dtype);
+
+/* Release a plan.  The caller must make sure no launch using it is still
+ * running (synchronise the streams it was used on first).  NULL is ignored. */
+void ds_destroy(ds_plan* plan);
+
+/* The arguments the plan was created with (any pointer may be NULL). */
+ds_status ds_plan_get_params(const ds_plan* plan, int* in_h, int* in_w, int* p, int* q, int* taps,
+                             int* dtype);
+
+/* Output extent floor(in*p/q) per axis and the channel count. */
+ds_status ds_plan_out_shape(const ds_plan* plan, int* out_h, int* out_w, int* channels);
+
+/* Input / output bytes of one frame. */
+ds_status ds_plan_frame_bytes(const ds_plan* plan, size_t* in_bytes, size_t* out_bytes);
+
+/*
+ * Copy the plan's tap tables, each row-major [p][K]; any pointer may be NULL.
+ * fp64: the exact taps; fp32: (float) of fp64 (used by DS_F32 / DS_F16);
+ * q14: the Q14 integers (used by DS_U8 / DS_U8_RGB).  Also returns the
+ * window start b_j of each phase in `window_start` ([p] ints) if not NULL.
+ */
+ds_status ds_plan_get_taps(const ds_plan* plan, double* fp64, float* fp32, short* q14,
+                           int* window_start);
+
+/*
+ * Describe the execution choice as a short JSON object written into buf
+ * (truncated to len bytes, always NUL-terminated): kernel, tile shape,
+ * rows per tile, CTAs per SM.
+ */
+ds_status ds_plan_describe(const ds_plan* plan, char* buf, size_t len);
+
+/*
+ * Tile schedule of the fused kernel (the "launch topology" the paper derives
+ * from the task multiplicity, Sec. 3.B.1): row_blocks = output row blocks
+ * per tile (each block is p output rows), ctas_per_sm = resident CTAs per SM
+ * of the persistent grid (0 = as many as fit).  Used by the autotuner.
+ * DS_ERR_ARG for row_blocks < 1 or ctas_per_sm < 0.
+ */
+ds_status ds_plan_set_schedule(ds_plan* plan, int row_blocks, int ctas_per_sm);
+ds_status ds_plan_get_schedule(const ds_plan* plan, int* row_blocks, int* ctas_per_sm);
+
+/* ---------------------------------------------------------------------- */
+/* Running                                                                  */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * Filter one frame: in (in_h x in_w x C elements) -> out (out_h x out_w x C),
+ * horizontal pass then vertical pass fused in one kernel; the intermediate
+ * stays in shared memory.  in and out must not overlap.
+ * DS_ERR_ARG: NULL plan / pointer.  DS_ERR_CUDA: launch failure.
+ */
+ds_status ds_run(const ds_plan* plan, const void* in, void* out, void* stream);
+
+/* Filter n_frames frames stored back to back (one launch). */
+ds_status ds_run_frames(const ds_plan* plan, const void* in, void* out, int n_frames,
+                        void* stream);
+
+/* One job of a batch: a frame (or n_frames frames back to back) of one plan. */
+typedef struct {
+    const ds_plan* plan;
+    const void* in;
+    void* out;
+    int n_frames; /* 0 is read as 1 */
+} ds_job;
+
+/*
+ * Filter a batch of jobs of any mix of plans (sizes, ratios, dtypes) with one
+ * persistent launch per kernel family (all fast-path plans share one
+ * launch); jobs whose plan needs the general kernel get their own launches
+ * on the same stream.  Job descriptors travel in the launch parameters: no
+ * device memory is allocated.  Batches beyond the per-launch descriptor limit
+ * are split into several launches.  DS_ERR_ARG: n < 0, NULL jobs with n > 0,
+ * NULL plan or pointer in a job.
+ */
+ds_status ds_batch_run(const ds_job* jobs, int n, void* stream);
+
+/*
+ * The unfused two-kernel form: a horizontal kernel writes the intermediate
+ * (FP32 for float dtypes, uint8 for uint8 dtypes) to `workspace` in device
+ * memory, a vertical kernel reads it back.  Same results as ds_run, bit for
+ * bit.  workspace_bytes must be at least ds_plan_workspace_bytes(plan) *
+ * n_frames.  DS_ERR_ARG otherwise.
+ */
+size_t ds_plan_workspace_bytes(const ds_plan* plan);
+ds_status ds_run_unfused(const ds_plan* plan, const void* in, void* out, int n_frames,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Synchronise `stream` and read the device status word that kernels set
+ * when a bounded wait gives up; the word is cleared by the read.
+ * DS_ERR_TIMEOUT if it was set, DS_ERR_CUDA on an asynchronous CUDA error.
+ */
+ds_status ds_stream_check(void* stream);
+
+/*
+ * Host-only self-check of the fused kernel's tile schedule for this plan:
+ * walks every tile of a frame with the kernel's own index arithmetic and
+ * verifies that TMA coordinates are aligned, every shared-memory access
+ * stays inside its buffer, the on-chip intermediate ring is never read
+ * before it is written or after it is overwritten, and every output element
+ * is written exactly once.  No device work.  DS_OK, or DS_ERR_ARG with the
+ * first violation in ds_last_error().  Plans without a fast kernel: DS_OK.
+ */
+ds_status ds_debug_check_plan(const ds_plan* plan);
+
+/* ---------------------------------------------------------------------- */
+/* CUDA graphs                                                              */
+/* ---------------------------------------------------------------------- */
+
+typedef struct ds_graph ds_graph;
+
+/*
+ * Capture ds_batch_run(jobs, n, .) into a CUDA graph and instantiate it; the
+ * job pointers are baked in.  NULL on error.  ds_graph_launch replays it on
+ * `stream` (one graph launch for the whole batch).
+ */
+ds_graph* ds_graph_create(const ds_job* jobs, int n);
+ds_status ds_graph_launch(ds_graph* graph, void* stream);
+void ds_graph_destroy(ds_graph* graph);
+
+/* ---------------------------------------------------------------------- */
+/* End-to-end pipeline with host buffers                                    */
+/* ---------------------------------------------------------------------- */
+
+typedef struct ds_pipeline ds_pipeline;
+
+/*
+ * A host-to-host pipeline for one plan: frames are copied host -> device,
+ * filtered and copied device -> host in chunks of `chunk_frames`, with
+ * `depth` chunks in flight on separate streams so that copies in both
+ * directions overlap the kernels (the transfer cost the paper measures in
+ * Sec. 4).  Owns its device staging buffers and streams.  NULL on error.
+ */
+ds_pipeline* ds_pipeline_create(const ds_plan* plan, int chunk_frames, int depth);
+
+/*
+ * Filter n_frames frames from host memory `in` into host memory `out` and
+ * wait for completion.  Page-locked (pinned) host buffers give overlapped
+ * copies; pageable memory works but serialises.  DS_ERR_ARG on NULL.
+ */
+ds_status ds_pipeline_run(ds_pipeline* pipe, const void* in, void* out, int n_frames);
+void ds_pipeline_destroy(ds_pipeline* pipe);
+
+/* ---------------------------------------------------------------------- */
+/* Misc                                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* ds_last_error(void);
+
+/* Library version string. */
+const char* ds_version(void);
+
+/* Number of kernel launches this library made on this host thread since the
+ * last call (the counter is reset by the call). */
+long long ds_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DS_H */

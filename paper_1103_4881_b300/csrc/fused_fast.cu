@@ -1,0 +1,1075 @@
+// fused_fast.cu -- the fused horizontal + vertical decimating FIR for B300.
+//
+// One persistent kernel runs the whole filter stage of the paper's
+// downscaler (Sec. 3: horizontal filter, then vertical filter, packets of q
+// pixels -> p outputs).  Work is cut into tiles: a strip of output columns
+// x a band of output row blocks of one frame.  Per CTA:
+//
+//   producer warp (one elected lane): TMA tensor loads
+//     (cp.async.bulk.tensor.3d) of SR input rows of the strip plus its left
+//     and right halo into an NSTAGE-deep shared-memory ring, completion
+//     tracked by mbarrier transaction counts;
+//   4 consumer warps:
+//     H pass -- every thread loads one contiguous chunk of a row (NB packets
+//       of q pixels) with conflict-free vector ld.shared, takes the halo
+//       pixels from its neighbour lanes with warp shuffles, and computes
+//       NB*p outputs per channel with the phase taps (kernel parameters, so
+//       FFMA operands come from the constant bank);
+//     the horizontal results go to an on-chip ring of intermediate rows
+//       (the intermediate never reaches HBM -- the paper's Sec. 3.B.4 removes
+//       host round trips between the two filters; this removes the device
+//       memory round trip as well);
+//     V pass -- as soon as the rows of an output block are in the ring,
+//       threads read them column-wise and write the p output rows.
+//
+// The H and V dot products accumulate in tap order t = 0..K-1 with fmaf from
+// 0, the same sequence as the general kernels, so results are identical bit
+// for bit whatever kernel, tile or batch computes them.
+//
+// Every wait on an mbarrier is bounded (%globaltimer, 1 s).  On expiry the
+// kernel records DS_ERR_TIMEOUT in a device status word, the consumers agree
+// on leaving through a barrier with OR-reduction, and the producer waits
+// (bounded) for the copies it issued before it returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "pixel.cuh"
+
+namespace ds {
+
+__device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out; 2 = bad class
+
+namespace {
+
+constexpr int kNWC = 4;                       // consumer warps
+constexpr int kThreads = (kNWC + 1) * 32;     // + one producer warp
+constexpr int kMaxJobs = 64;                  // job descriptors per launch
+constexpr int kMaxTaps = 24;                  // p*K of the fast classes
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+constexpr int kStatusTimeout = 1;
+constexpr int kStatusBadClass = 2;
+
+// ---------------------------------------------------------------------------
+// compile-time geometry
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cfloordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr int rup(int a, int m) { return cdiv(a, m) * m; }
+// window start of phase j: floor(((2j+1) q - p) / (2p)) - K/2 + 1
+__host__ __device__ constexpr int phase_b(int P, int Q, int K, int j) {
+  return cfloordiv((2 * j + 1) * Q - P, 2 * P) - K / 2 + 1;
+}
+constexpr int cmax(int a) { return a; }
+template <typename... R>
+constexpr int cmax(int a, int b, R... r) { return cmax(a > b ? a : b, r...); }
+
+template <typename T>
+struct TmaType;
+template <>
+struct TmaType<float> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
+template <>
+struct TmaType<__half> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; };
+template <>
+struct TmaType<uint8_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_UINT8; };
+
+// Intermediate type in the on-chip ring: FP32 for float data; FP16 for uint8
+// data, whose intermediate values are integers 0..255 (exact in FP16).
+template <typename T>
+struct RingOf { using type = float; };
+template <>
+struct RingOf<uint8_t> { using type = __half; };
+
+// A fast-path class: data type, channels, ratio P/Q, taps K, and the tile
+// shape -- NB packets per thread and row, WX warps across a strip, SR input
+// rows per pipeline stage, VE columns per thread in the V pass.
+template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int WX_, int SR_, int VE_>
+struct Cls {
+  using T = T_;
+  using R = typename RingOf<T_>::type;
+  static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_, WX = WX_, SR = SR_, VE = VE_;
+  static constexpr int WY = kNWC / WX;
+  static constexpr int SZ = (int)sizeof(T);
+  static constexpr int BMIN = phase_b(P, Q, K, 0);
+  static constexpr int BMAX = phase_b(P, Q, K, P - 1);
+  static constexpr int L = BMAX - BMIN + K;   // pattern length (rows or pixels per block window)
+  static constexpr int LH = -BMIN;            // halo pixels left of a block
+  static constexpr int RH = BMAX + K - Q;     // halo pixels right of a block
+  static constexpr int E = NB * Q * C;        // elements per thread and row
+  static constexpr int EB = E * SZ;
+  static constexpr int EW = EB / 4;
+  static constexpr int HWL = cdiv(LH * C * SZ, 4);  // halo words from the left lane
+  static constexpr int HWR = cdiv(RH * C * SZ, 4);  // halo words from the right lane
+  static constexpr int HLB = rup(LH * C * SZ, 16);  // left halo bytes in the window (TMA x alignment)
+  static constexpr int RHB = rup(RH * C * SZ, 16);
+  static constexpr int SBLK = 32 * NB * WX;         // packets (blocks) per strip
+  static constexpr int SPX = SBLK * Q;              // input pixels per strip
+  static constexpr int WINB = HLB + SPX * C * SZ + RHB;
+  static constexpr int NBOX = cdiv(WINB / SZ, 256);
+  static constexpr int BOXB = rup(cdiv(WINB, NBOX), 16);
+  static constexpr int BOXE = BOXB / SZ;
+  static constexpr int BOXSTR = rup(SR * BOXB, 128);  // each box lands 128-B aligned
+  static constexpr int STAGE_BYTES = NBOX * BOXSTR;
+  static constexpr int TX_BYTES = NBOX * SR * BOXB;
+  static constexpr int SOE = SBLK * P * C;            // intermediate elements per ring row
+  static constexpr int RING = 2 * SR + L + Q;         // ring rows (see consume_tile)
+  static constexpr int RING_BYTES = rup(RING * SOE * (int)sizeof(R), 16);
+  static constexpr int NX = (LH + NB * Q + RH) * C;   // elements one thread reads per row
+  static constexpr int VB = (EB % 16 == 0) ? 16 : ((EB % 8 == 0) ? 8 : 4);
+  static constexpr int NV = EB / VB;
+  static constexpr int ROT = (VB == 16 && (NV == 2 || NV == 4)) ? NV : 1;
+  static constexpr int NOUT = NB * P * C;             // H outputs per thread and row
+  __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
+  static_assert(EB % 4 == 0, "a thread's chunk must be whole words");
+  static_assert(HWL <= EW && HWR <= EW, "halo wider than a neighbour's chunk");
+  static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
+  static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
+  static_assert(SR % WY == 0 && kNWC % WX == 0, "stage rows must split over warp rows");
+  static_assert(SOE % VE == 0 && (VE == 1 || VE == 4), "V-pass vector width");
+  static_assert(P * K <= kMaxTaps, "tap table size");
+  static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
+};
+
+//                 id        T     C  P  Q  K  NB WX  SR VE
+using CF32_38 = Cls<kFcF32_38, float, 1, 3, 8, 8, 1, 1, 16, 1>;
+using CF32_12 = Cls<kFcF32_12, float, 1, 1, 2, 6, 4, 1, 16, 1>;
+using CF32_23 = Cls<kFcF32_23, float, 1, 2, 3, 6, 4, 1, 12, 1>;
+using CF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 1, 16, 1>;
+using CF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 1, 16, 1>;
+using CF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 4, 1, 12, 1>;
+using CU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 1, 8, 4>;
+using CU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 2, 2, 8, 4>;
+using CU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 1, 8, 4>;
+
+// ---------------------------------------------------------------------------
+// launch parameters
+// ---------------------------------------------------------------------------
+struct JobDesc {
+  CUtensorMap tmap;        // 3-D map: (W*C elements, H rows, n_frames)
+  void* out;
+  long long out_frame;     // elements per output frame
+  int H, W, OH, OW;
+  int nframes, cls, strips, chunks;
+  int rbc, tile_begin, tiles, out_vec;
+};
+static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor layout");
+
+struct FastParams {
+  JobDesc jobs[kMaxJobs];
+  float taps[kFcCount][kMaxTaps];  // FP32 taps, or Q14 taps as floats for uint8
+  int n_jobs;
+  int total_tiles;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t saddr32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of `parity` to complete; false after kWaitLimitNs, or
+// at once when *abort_flag becomes non-zero (if given).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 31u) == 0) {
+      if (abort_flag && *abort_flag) return false;
+      if (gtimer() - t0 > kWaitLimitNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr32(bar))
+      : "memory");
+}
+// Barrier over the consumer warps only (named barrier 1), with OR of `pred`.
+__device__ __forceinline__ int consumers_sync_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.s32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, %2, p;\n\t"
+      "selp.s32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "n"(kNWC * 32)
+      : "memory");
+  return r;
+}
+__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kNWC * 32) : "memory"); }
+
+// ---------------------------------------------------------------------------
+// tiles
+// ---------------------------------------------------------------------------
+struct Tile {
+  int job, frame, strip, chunk;
+};
+
+__host__ __device__ __forceinline__ Tile decode_tile(const FastParams& prm, int t) {
+  int lo = 0, hi = prm.n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prm.jobs[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const JobDesc& jd = prm.jobs[lo];
+  const int tl = t - jd.tile_begin;
+  const int per_frame = jd.strips * jd.chunks;
+  Tile r;
+  r.job = lo;
+  r.frame = tl / per_frame;
+  const int rem = tl - r.frame * per_frame;
+  r.chunk = rem / jd.strips;  // strips vary fastest: neighbouring CTAs share halos in L2
+  r.strip = rem - r.chunk * jd.strips;
+  return r;
+}
+
+struct Geo {
+  int rb0;   // first output row block of the tile
+  int nblk;  // row blocks in the tile
+  int ys;    // first input row of the tile's pattern (may be < 0)
+  int rows;  // input rows the tile needs
+  int nst;   // pipeline stages of the tile
+  int xw;    // first element (x coordinate) of the loaded window
+  int ox0;   // first output pixel of the strip
+};
+
+template <class Cl>
+__host__ __device__ __forceinline__ Geo tile_geo(const JobDesc& jd, const Tile& tl) {
+  Geo g;
+  g.rb0 = tl.chunk * jd.rbc;
+  const int nby = (jd.OH + Cl::P - 1) / Cl::P;
+  g.nblk = jd.rbc < nby - g.rb0 ? jd.rbc : nby - g.rb0;
+  g.ys = g.rb0 * Cl::Q + Cl::BMIN;
+  g.rows = (g.nblk - 1) * Cl::Q + Cl::L;
+  g.nst = (g.rows + Cl::SR - 1) / Cl::SR;
+  g.xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
+  g.ox0 = tl.strip * Cl::SBLK * Cl::P;
+  return g;
+}
+
+// Byte `byte` of window row `row` inside a stage: boxes are stored one after
+// the other, each as SR rows of BOXB bytes.
+template <class Cl>
+__device__ __forceinline__ const uint8_t* win_ptr(const uint8_t* stage, int row, int byte) {
+  const int box = byte / Cl::BOXB;
+  return stage + box * Cl::BOXSTR + row * Cl::BOXB + (byte - box * Cl::BOXB);
+}
+
+// ---------------------------------------------------------------------------
+// producer
+// ---------------------------------------------------------------------------
+template <class Cl, int NSTAGE, int STAGE_MAX>
+__device__ bool produce_tile(const JobDesc& jd, const Tile& tl, uint8_t* stages, uint64_t* full, uint64_t* empty,
+                             uint32_t& g, const volatile int* abort_flag) {
+  const Geo G = tile_geo<Cl>(jd, tl);
+  for (int k = 0; k < G.nst; ++k, ++g) {
+    const uint32_t slot = g % NSTAGE, round = g / NSTAGE;
+    if (round > 0 && !mbar_wait(&empty[slot], (round - 1) & 1u, abort_flag)) return false;
+    uint8_t* dst = stages + slot * STAGE_MAX;
+    mbar_expect_tx(&full[slot], Cl::TX_BYTES);
+#pragma unroll
+    for (int bx = 0; bx < Cl::NBOX; ++bx)
+      tma_load_3d(dst + bx * Cl::BOXSTR, &jd.tmap, &full[slot], G.xw + bx * Cl::BOXE, G.ys + k * Cl::SR, tl.frame);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// consumer: horizontal pass of one row
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float word_elem(const uint32_t* w, int byte);
+template <>
+__device__ __forceinline__ float word_elem<float>(const uint32_t* w, int byte) { return __uint_as_float(w[byte >> 2]); }
+template <>
+__device__ __forceinline__ float word_elem<__half>(const uint32_t* w, int byte) {
+  const uint32_t v = w[byte >> 2];
+  const unsigned short h = (byte & 2) ? (unsigned short)(v >> 16) : (unsigned short)(v & 0xffffu);
+  return __half2float(__ushort_as_half(h));
+}
+template <>
+__device__ __forceinline__ float word_elem<uint8_t>(const uint32_t* w, int byte) {
+  // byte -> float through the bit pattern of 2^23 + byte
+  return __uint_as_float(__byte_perm(w[byte >> 2], 0x4B000000u, 0x7540u | (unsigned)(byte & 3))) - 8388608.0f;
+}
+
+template <typename T>
+__device__ __forceinline__ float smem_elem(const uint8_t* p) { return px_to_f(*reinterpret_cast<const T*>(p)); }
+
+// Load this thread's EB-byte chunk of window row `row` into words w[0..EW).
+template <class Cl>
+__device__ __forceinline__ void load_chunk(const uint8_t* stage, int row, int byte0, int lane, uint32_t* w) {
+  constexpr int NV = Cl::NV, VB = Cl::VB, WPV = VB / 4;
+  // Lanes whose chunks would hit the same banks in one shared-memory phase
+  // start at a rotated vector; the words are put back in order afterwards.
+  const int rot = (Cl::ROT == 2) ? ((lane >> 2) & 1) : ((Cl::ROT == 4) ? ((lane >> 1) & 3) : 0);
+  uint32_t tmp[NV][WPV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    int pv = v + rot;
+    if (Cl::ROT > 1 && pv >= NV) pv -= NV;
+    const uint8_t* p = win_ptr<Cl>(stage, row, byte0 + pv * VB);
+    if constexpr (VB == 16) {
+      const uint4 x = *reinterpret_cast<const uint4*>(p);
+      tmp[v][0] = x.x; tmp[v][1] = x.y; tmp[v][2] = x.z; tmp[v][3] = x.w;
+    } else if constexpr (VB == 8) {
+      const uint2 x = *reinterpret_cast<const uint2*>(p);
+      tmp[v][0] = x.x; tmp[v][1] = x.y;
+    } else {
+      tmp[v][0] = *reinterpret_cast<const uint32_t*>(p);
+    }
+  }
+  // tmp[v] holds vector (v + rot) mod NV; put vector c back at w[c * WPV]
+  if constexpr (Cl::ROT == 2) {
+#pragma unroll
+    for (int q = 0; q < WPV; ++q) {
+      w[q] = rot ? tmp[1][q] : tmp[0][q];
+      w[WPV + q] = rot ? tmp[0][q] : tmp[1][q];
+    }
+  } else if constexpr (Cl::ROT == 4) {
+    // rotate right by rot = 2*r1 + r0: first by 2 (if r1), then by 1 (if r0)
+    const bool r1 = (rot & 2) != 0, r0 = (rot & 1) != 0;
+    uint32_t u[4][WPV];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < WPV; ++q) u[c][q] = r1 ? tmp[(c + 2) & 3][q] : tmp[c][q];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int q = 0; q < WPV; ++q) w[c * WPV + q] = r0 ? u[(c + 3) & 3][q] : u[c][q];
+  } else {
+#pragma unroll
+    for (int c = 0; c < NV; ++c)
+#pragma unroll
+      for (int q = 0; q < WPV; ++q) w[c * WPV + q] = tmp[c][q];
+  }
+}
+
+template <class Cl>
+__device__ __forceinline__ void ring_store(typename Cl::R* dst, const float* o) {
+  constexpr int N = Cl::NOUT;
+  if constexpr (sizeof(typename Cl::R) == 4) {
+    if constexpr (N % 4 == 0) {
+#pragma unroll
+      for (int i = 0; i < N / 4; ++i)
+        reinterpret_cast<float4*>(dst)[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+    } else if constexpr (N % 2 == 0) {
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) reinterpret_cast<float2*>(dst)[i] = make_float2(o[2 * i], o[2 * i + 1]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) dst[i] = o[i];
+    }
+  } else {
+    if constexpr (N % 2 == 0) {
+      uint32_t hw[N / 2];
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        const __half2 h2 = __floats2half2_rn(o[2 * i], o[2 * i + 1]);
+        hw[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      }
+      if constexpr (N % 8 == 0) {
+#pragma unroll
+        for (int i = 0; i < N / 8; ++i)
+          reinterpret_cast<uint4*>(dst)[i] = make_uint4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
+      } else if constexpr (N % 4 == 0) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) reinterpret_cast<uint2*>(dst)[i] = make_uint2(hw[2 * i], hw[2 * i + 1]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) reinterpret_cast<uint32_t*>(dst)[i] = hw[i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < N; ++i) dst[i] = __float2half_rn(o[i]);
+    }
+  }
+}
+
+template <class Cl>
+__device__ __forceinline__ void hrow(const uint8_t* stage, int row, int lane, int lg, bool active, bool interior,
+                                     int px0, int W, int xw, const float* __restrict__ taps,
+                                     typename Cl::R* __restrict__ dst) {
+  using T = typename Cl::T;
+  constexpr int HWL = Cl::HWL, EW = Cl::EW, HWR = Cl::HWR;
+  uint32_t w[HWL + EW + HWR];
+  const int byte0 = Cl::HLB + lg * Cl::EB;
+  load_chunk<Cl>(stage, row, byte0, lane, w + HWL);
+#pragma unroll
+  for (int i = 0; i < HWL; ++i) w[i] = __shfl_up_sync(0xffffffffu, w[HWL + EW - HWL + i], 1);
+#pragma unroll
+  for (int i = 0; i < HWR; ++i) w[HWL + EW + i] = __shfl_down_sync(0xffffffffu, w[HWL + i], 1);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < HWL; ++i)
+      w[i] = *reinterpret_cast<const uint32_t*>(win_ptr<Cl>(stage, row, byte0 - 4 * HWL + 4 * i));
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int i = 0; i < HWR; ++i)
+      w[HWL + EW + i] = *reinterpret_cast<const uint32_t*>(win_ptr<Cl>(stage, row, byte0 + Cl::EB + 4 * i));
+  }
+  if (!active) return;
+  float x[Cl::NX];
+  if (interior) {
+    constexpr int first = 4 * HWL - Cl::LH * Cl::C * Cl::SZ;  // byte of the first halo element in w
+#pragma unroll
+    for (int e = 0; e < Cl::NX; ++e) x[e] = word_elem<T>(w, first + e * Cl::SZ);
+  } else {
+    // frame border: clamp-to-edge reads straight from the window
+#pragma unroll
+    for (int e = 0; e < Cl::NX; ++e) {
+      const int px = clampi(px0 - Cl::LH + e / Cl::C, 0, W - 1);
+      const int el = px * Cl::C + (e % Cl::C) - xw;
+      x[e] = smem_elem<T>(win_ptr<Cl>(stage, row, el * Cl::SZ));
+    }
+  }
+  float o[Cl::NOUT];
+#pragma unroll
+  for (int n = 0; n < Cl::NB; ++n) {
+#pragma unroll
+    for (int j = 0; j < Cl::P; ++j) {
+#pragma unroll
+      for (int c = 0; c < Cl::C; ++c) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int t = 0; t < Cl::K; ++t)
+          acc = fmaf(taps[j * Cl::K + t], x[(n * Cl::Q + Cl::b(j) - Cl::BMIN + t) * Cl::C + c], acc);
+        o[(n * Cl::P + j) * Cl::C + c] = pass_round<T>(acc);
+      }
+    }
+  }
+  ring_store<Cl>(dst, o);
+}
+
+// ---------------------------------------------------------------------------
+// consumer: vertical pass of the blocks that became ready at stage k
+// ---------------------------------------------------------------------------
+template <class Cl>
+__device__ __forceinline__ void ring_load(const typename Cl::R* p, float* h) {
+  if constexpr (sizeof(typename Cl::R) == 4) {
+    if constexpr (Cl::VE == 4) {
+      const float4 v = *reinterpret_cast<const float4*>(p);
+      h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+    } else {
+      h[0] = *reinterpret_cast<const float*>(p);
+    }
+  } else {
+    if constexpr (Cl::VE == 4) {
+      const uint2 v = *reinterpret_cast<const uint2*>(p);
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+      h[0] = a.x; h[1] = a.y; h[2] = b.x; h[3] = b.y;
+    } else {
+      h[0] = __half2float(*reinterpret_cast<const __half*>(p));
+    }
+  }
+}
+
+// Row blocks (tile-relative) whose V pass runs at stage k: block m is ready
+// once its last pattern row m*Q + L - 1 has been loaded.
+template <class Cl>
+__host__ __device__ __forceinline__ void ready_blocks(const Geo& G, int k, int& m_lo, int& m_hi) {
+  m_lo = k * Cl::SR - Cl::L + 1;
+  m_lo = m_lo <= 0 ? 0 : (m_lo + Cl::Q - 1) / Cl::Q;
+  m_hi = (k + 1) * Cl::SR - Cl::L;
+  m_hi = m_hi < 0 ? -1 : m_hi / Cl::Q;
+  if (m_hi > G.nblk - 1 || k == G.nst - 1) m_hi = G.nblk - 1;
+}
+
+template <class Cl>
+__device__ __forceinline__ void vpass(const JobDesc& jd, const Tile& tl, const Geo& G, int k,
+                                      const float* __restrict__ taps, const typename Cl::R* __restrict__ ring,
+                                      int tid) {
+  using T = typename Cl::T;
+  int m_lo, m_hi;
+  ready_blocks<Cl>(G, k, m_lo, m_hi);
+  if (m_hi < m_lo) return;
+  const int ncols = min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
+  const int tpb = (ncols + Cl::VE - 1) / Cl::VE;
+  const int ntask = (m_hi - m_lo + 1) * tpb;
+  const int rowe = jd.OW * Cl::C;
+  T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)G.ox0 * Cl::C;
+  for (int task = tid; task < ntask; task += kNWC * 32) {
+    const int mb = task / tpb;
+    const int e0 = (task - mb * tpb) * Cl::VE;
+    const int r = G.rb0 + m_lo + mb;
+    float acc[Cl::P][Cl::VE];
+#pragma unroll
+    for (int j = 0; j < Cl::P; ++j)
+#pragma unroll
+      for (int v = 0; v < Cl::VE; ++v) acc[j][v] = 0.0f;
+#pragma unroll
+    for (int i = 0; i < Cl::L; ++i) {
+      const int yc = clampi(r * Cl::Q + Cl::BMIN + i, 0, jd.H - 1);
+      const int slot = (yc - G.ys) % Cl::RING;
+      float h[Cl::VE];
+      ring_load<Cl>(ring + slot * Cl::SOE + e0, h);
+#pragma unroll
+      for (int j = 0; j < Cl::P; ++j) {
+        const int t = i - (Cl::b(j) - Cl::BMIN);
+        if (t >= 0 && t < Cl::K) {
+#pragma unroll
+          for (int v = 0; v < Cl::VE; ++v) acc[j][v] = fmaf(taps[j * Cl::K + t], h[v], acc[j][v]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < Cl::P; ++j) {
+      const int oy = r * Cl::P + j;
+      if (oy >= jd.OH) break;
+      T* o = obase + (long long)oy * rowe + e0;
+      if constexpr (Cl::VE == 4) {
+        if (jd.out_vec && e0 + 4 <= ncols) {
+          uint32_t pk = 0;
+#pragma unroll
+          for (int v = 0; v < 4; ++v) pk |= (uint32_t)f_to_px<T>(pass_round<T>(acc[j][v])) << (8 * v);
+          *reinterpret_cast<uint32_t*>(o) = pk;
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            if (e0 + v < ncols) o[v] = f_to_px<T>(pass_round<T>(acc[j][v]));
+        }
+      } else {
+        o[0] = f_to_px<T>(pass_round<T>(acc[j][0]));
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// consumer: one tile
+// ---------------------------------------------------------------------------
+// Ring safety: ring rows are indexed by the tile-relative input row.  After
+// the barrier of stage k a fast warp may run the H pass of stage k+1 (rows
+// up to (k+2)*SR - 1) while a slow warp still runs the V pass of stage k,
+// whose rows start at or after k*SR - L + 1.  RING = 2*SR + L + Q rows keeps
+// the two apart; the next tile starts only after a consumer barrier.
+template <class Cl, int NSTAGE, int STAGE_MAX>
+__device__ bool consume_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl, const uint8_t* stages,
+                             uint8_t* ring_raw, uint64_t* full, uint64_t* empty, uint32_t& g) {
+  using R = typename Cl::R;
+  R* ring = reinterpret_cast<R*>(ring_raw);
+  const float* taps = prm.taps[Cl::id];
+  const Geo G = tile_geo<Cl>(jd, tl);
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int wx = warp % Cl::WX, wy = warp / Cl::WX;
+  const int lg = wx * 32 + lane;                         // chunk index across the strip
+  const int blk0 = tl.strip * Cl::SBLK + lg * Cl::NB;   // first packet of the chunk (frame coords)
+  const int px0 = blk0 * Cl::Q;
+  const bool active = blk0 * Cl::P < jd.OW;
+  const bool interior = (px0 - Cl::LH >= 0) && (px0 + Cl::NB * Cl::Q + Cl::RH <= jd.W);
+  for (int k = 0; k < G.nst; ++k, ++g) {
+    const uint32_t slot = g % NSTAGE, round = g / NSTAGE;
+    const bool ok = mbar_wait(&full[slot], round & 1u, nullptr);
+    const uint8_t* stage = stages + slot * STAGE_MAX;
+    if (ok) {
+      for (int i = wy; i < Cl::SR; i += Cl::WY) {
+        const int rel = k * Cl::SR + i;
+        const int y = G.ys + rel;
+        if (y < 0 || y >= jd.H || rel >= G.rows) continue;  // never read by the V pass
+        hrow<Cl>(stage, i, lane, lg, active, interior, px0, jd.W, G.xw, taps,
+                 ring + (rel % Cl::RING) * Cl::SOE + lg * Cl::NOUT);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[slot]);
+    if (consumers_sync_or(!ok)) return false;
+    vpass<Cl>(jd, tl, G, k, taps, ring, tid);
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// class dispatch and the kernel
+// ---------------------------------------------------------------------------
+template <class... Cs>
+struct Dispatch;
+template <>
+struct Dispatch<> {
+  template <class F>
+  __device__ static bool run(int, F&&) { return false; }
+};
+template <class C0, class... Rest>
+struct Dispatch<C0, Rest...> {
+  template <class F>
+  __device__ static bool run(int cls, F&& f) {
+    if (cls == C0::id) return f(C0{});
+    return Dispatch<Rest...>::run(cls, f);
+  }
+};
+
+template <int NSTAGE, class... Cs>
+struct KernelShape {
+  static constexpr int STAGE_MAX = cmax(Cs::STAGE_BYTES...);
+  static constexpr int RING_MAX = cmax(Cs::RING_BYTES...);
+  static constexpr int BAR_OFF = NSTAGE * STAGE_MAX + RING_MAX;
+  static constexpr int SMEM = 128 + BAR_OFF + 2 * NSTAGE * 8 + 16;
+};
+
+template <int NSTAGE, class... Cs>
+__global__ void __launch_bounds__(kThreads, 2) k_fused_tma(const __grid_constant__ FastParams prm) {
+  using KS = KernelShape<NSTAGE, Cs...>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint8_t* stages = smem;
+  uint8_t* ring = smem + NSTAGE * KS::STAGE_MAX;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + KS::BAR_OFF);
+  uint64_t* empty = full + NSTAGE;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTAGE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kNWC);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == kNWC) {
+    // ------------------------------- producer
+    if (lane != 0) return;
+    uint32_t g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; ok && t < prm.total_tiles; t += gridDim.x) {
+      const Tile tl = decode_tile(prm, t);
+      const JobDesc& jd = prm.jobs[tl.job];
+      ok = Dispatch<Cs...>::run(jd.cls, [&](auto cl) {
+        return produce_tile<decltype(cl), NSTAGE, KS::STAGE_MAX>(jd, tl, stages, full, empty, g, abort_flag);
+      });
+    }
+    if (!ok) {
+      // leave no copy in flight: wait (bounded) for the last round of each slot
+      atomicCAS(&g_fast_status, 0, kStatusTimeout);
+      for (uint32_t s = 0; s < NSTAGE && s < g; ++s) {
+        const uint32_t last = g - 1 - s;
+        mbar_wait(&full[last % NSTAGE], (last / NSTAGE) & 1u, nullptr);
+      }
+    }
+    return;
+  }
+
+  // --------------------------------- consumers
+  uint32_t g = 0;
+  bool first = true;
+  for (int t = blockIdx.x; t < prm.total_tiles; t += gridDim.x) {
+    const Tile tl = decode_tile(prm, t);
+    const JobDesc& jd = prm.jobs[tl.job];
+    if (!first) consumers_sync();  // the ring is reused by the next tile
+    first = false;
+    int code = kStatusBadClass;
+    const bool ok = Dispatch<Cs...>::run(jd.cls, [&](auto cl) {
+      code = kStatusTimeout;
+      return consume_tile<decltype(cl), NSTAGE, KS::STAGE_MAX>(prm, jd, tl, stages, ring, full, empty, g);
+    });
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        *abort_flag = 1;
+        atomicCAS(&g_fast_status, 0, code);
+      }
+      return;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct HostGeom {
+  int sblk, spx, p, q, boxe, sr, sz, c, ve;
+  CUtensorMapDataType dt;
+};
+
+template <class Cl>
+HostGeom host_geom() {
+  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::BOXE, Cl::SR, Cl::SZ, Cl::C, Cl::VE, TmaType<typename Cl::T>::v};
+}
+
+HostGeom geom_of(int cls) {
+  switch (cls) {
+    case kFcF32_38: return host_geom<CF32_38>();
+    case kFcF32_12: return host_geom<CF32_12>();
+    case kFcF32_23: return host_geom<CF32_23>();
+    case kFcF16_38: return host_geom<CF16_38>();
+    case kFcF16_12: return host_geom<CF16_12>();
+    case kFcF16_23: return host_geom<CF16_23>();
+    case kFcU8C3_38: return host_geom<CU8_38>();
+    case kFcU8C3_12: return host_geom<CU8_12>();
+    default: return host_geom<CU8_23>();
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+struct KernelInfo {
+  const void* fn;
+  int smem;
+};
+
+template <int NSTAGE, class... Cs>
+KernelInfo kernel_info() {
+  return KernelInfo{reinterpret_cast<const void*>(&k_fused_tma<NSTAGE, Cs...>), KernelShape<NSTAGE, Cs...>::SMEM};
+}
+
+// single-class kernels (uniform batches) and the all-class kernel (mixes)
+KernelInfo kernel_for(int cls) {
+  switch (cls) {
+    case kFcF32_38: return kernel_info<4, CF32_38>();
+    case kFcF32_12: return kernel_info<4, CF32_12>();
+    case kFcF32_23: return kernel_info<4, CF32_23>();
+    case kFcF16_38: return kernel_info<6, CF16_38>();
+    case kFcF16_12: return kernel_info<6, CF16_12>();
+    case kFcF16_23: return kernel_info<6, CF16_23>();
+    case kFcU8C3_38: return kernel_info<8, CU8_38>();
+    case kFcU8C3_12: return kernel_info<8, CU8_12>();
+    case kFcU8C3_23: return kernel_info<4, CU8_23>();
+    default:
+      return kernel_info<3, CF32_38, CF32_12, CF32_23, CF16_38, CF16_12, CF16_23, CU8_38, CU8_12, CU8_23>();
+  }
+}
+
+// Occupancy per kernel, computed once per process (one device).
+int ctas_per_sm(const KernelInfo& ki) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& e : cache)
+    if (e.first == ki.fn) return e.second;
+  int occ = 0;
+  if (cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki.fn, kThreads, ki.smem) != cudaSuccess) return 0;
+  cache.emplace_back(ki.fn, occ);
+  return occ;
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+void fill_taps(FastParams& prm) {
+  // the fast classes' taps depend only on (p, q, K): build them once with a
+  // throwaway plan of each class
+  static FastParams taps_only;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    std::memset(&taps_only, 0, sizeof(taps_only));
+    const int pq[3][3] = {{3, 8, 8}, {1, 2, 6}, {2, 3, 6}};
+    const ds_dtype dts[3] = {DS_F32, DS_F16, DS_U8_RGB};
+    for (int d = 0; d < 3; ++d)
+      for (int r = 0; r < 3; ++r) {
+        ds_plan* pl = ds_plan_create(64, 64, ds_ratio{pq[r][0], pq[r][1]}, pq[r][2], dts[d]);
+        if (!pl) continue;
+        const int cls = pl->fast_class;
+        for (int i = 0; i < pl->p * pl->K; ++i)
+          taps_only.taps[cls][i] = (dts[d] == DS_U8_RGB) ? (float)pl->q14[i] : pl->w32[i];
+        ds_destroy(pl);
+      }
+  });
+  std::memcpy(prm.taps, taps_only.taps, sizeof(prm.taps));
+}
+
+// Tile geometry of a job (everything but the tensor map).
+void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames) {
+  const HostGeom hg = geom_of(pl->fast_class);
+  jd.out = out;
+  jd.out_frame = (long long)pl->out_frame_elems();
+  jd.H = pl->in_h;
+  jd.W = pl->in_w;
+  jd.OH = pl->out_h;
+  jd.OW = pl->out_w;
+  jd.nframes = n_frames;
+  jd.cls = pl->fast_class;
+  const int nbx = (pl->out_w + hg.p - 1) / hg.p;
+  const int nby = (pl->out_h + hg.p - 1) / hg.p;
+  jd.strips = (nbx + hg.sblk - 1) / hg.sblk;
+  jd.rbc = std::max(1, std::min(pl->row_blocks, nby));
+  jd.chunks = (nby + jd.rbc - 1) / jd.rbc;
+  jd.tiles = jd.strips * jd.chunks * n_frames;
+  jd.out_vec = (((uintptr_t)out & 3u) == 0 && ((size_t)pl->out_w * pl->channels) % 4 == 0) ? 1 : 0;
+}
+
+ds_status encode_job(JobDesc& jd, const FastJob& job) {
+  const ds_plan* pl = job.plan;
+  const HostGeom hg = geom_of(pl->fast_class);
+  auto enc = encode_fn();
+  if (!enc) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return DS_ERR_CUDA;
+  }
+  const cuuint64_t row_elems = (cuuint64_t)pl->in_w * pl->channels;
+  cuuint64_t dims[3] = {row_elems, (cuuint64_t)pl->in_h, (cuuint64_t)job.n_frames};
+  cuuint64_t strides[2] = {row_elems * hg.sz, row_elems * hg.sz * (cuuint64_t)pl->in_h};
+  cuuint32_t box[3] = {(cuuint32_t)hg.boxe, (cuuint32_t)hg.sr, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(&jd.tmap, hg.dt, 3, const_cast<void*>(job.in), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed (%d) for a %dx%d frame", (int)r, pl->in_h, pl->in_w);
+    return DS_ERR_CUDA;
+  }
+  fill_job_geometry(jd, pl, job.out, job.n_frames);
+  return DS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host-side check of the kernel's index arithmetic
+// ---------------------------------------------------------------------------
+// Walks every tile of one frame the way the kernel does and checks: TMA x
+// coordinates are 16-byte aligned; every shared-memory read of the H pass
+// (vector chunks, halo words, clamped border reads) stays inside the loaded
+// window and never straddles a box; ring writes stay inside a ring row;
+// every ring row the V pass reads was written by the H pass of an earlier or
+// the same stage and is not overwritten by the next stage's H pass; every
+// output element is written exactly once; the shared-memory footprint fits.
+template <class Cl, int STAGE_MAX, int SMEM>
+std::string check_class(const JobDesc& jd) {
+  char buf[256];
+  auto fail = [&](const char* what, int a, int b) {
+    std::snprintf(buf, sizeof(buf), "class %d: %s (%d, %d)", Cl::id, what, a, b);
+    return std::string(buf);
+  };
+  if (SMEM > 227 * 1024) return fail("shared memory above 227 KB", SMEM, 0);
+  if (Cl::STAGE_BYTES > STAGE_MAX || Cl::BOXSTR < Cl::SR * Cl::BOXB) return fail("stage layout", Cl::STAGE_BYTES, STAGE_MAX);
+  const int win = Cl::NBOX * Cl::BOXB;
+  std::vector<int> written((size_t)jd.OH * jd.OW * Cl::C, 0);
+  for (int chunk = 0; chunk < jd.chunks; ++chunk) {
+    for (int strip = 0; strip < jd.strips; ++strip) {
+      const Tile tl{0, 0, strip, chunk};
+      const Geo G = tile_geo<Cl>(jd, tl);
+      if (G.nblk < 1 || G.ox0 >= jd.OW) return fail("empty tile", chunk, strip);
+      for (int bx = 0; bx < Cl::NBOX; ++bx) {
+        const long long xb = (long long)(G.xw + bx * Cl::BOXE) * Cl::SZ;
+        if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", G.xw, bx);
+      }
+      for (int lg = 0; lg < 32 * Cl::WX; ++lg) {
+        const int lane = lg & 31;
+        const int byte0 = Cl::HLB + lg * Cl::EB;
+        for (int v = 0; v < Cl::NV; ++v) {
+          const int b0 = byte0 + v * Cl::VB;
+          if (b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB || b0 + Cl::VB > win) return fail("chunk read", lg, v);
+        }
+        if (lane == 0 && byte0 - 4 * Cl::HWL < 0) return fail("left halo read", lg, byte0);
+        if (lane == 31 && byte0 + Cl::EB + 4 * Cl::HWR > win) return fail("right halo read", lg, byte0);
+        const int blk0 = strip * Cl::SBLK + lg * Cl::NB;
+        const int px0 = blk0 * Cl::Q;
+        const bool active = blk0 * Cl::P < jd.OW;
+        const bool interior = (px0 - Cl::LH >= 0) && (px0 + Cl::NB * Cl::Q + Cl::RH <= jd.W);
+        if (active && interior) {
+          // the interior path reads pixels px0 - LH .. px0 + NB*Q + RH - 1 from the chunk and halos:
+          // they must be the window elements the TMA placed there
+          const int first_el = (px0 - Cl::LH) * Cl::C - G.xw;
+          const int want = byte0 - Cl::LH * Cl::C * Cl::SZ;
+          if (first_el * Cl::SZ != want) return fail("chunk not at its pixels", first_el, want);
+        }
+        if (active && !interior) {
+          for (int e = 0; e < Cl::NX; ++e) {
+            int px = px0 - Cl::LH + e / Cl::C;
+            px = px < 0 ? 0 : (px > jd.W - 1 ? jd.W - 1 : px);
+            const int el = px * Cl::C + (e % Cl::C) - G.xw;
+            if (el < 0 || (el + 1) * Cl::SZ > win) return fail("border read", lg, el);
+          }
+        }
+        if (lg * Cl::NOUT + Cl::NOUT > Cl::SOE) return fail("ring write", lg, Cl::SOE);
+      }
+      std::vector<int> owner(Cl::RING, -1);
+      std::vector<int> done(G.nblk, 0);
+      auto h_rows = [&](int k, std::vector<int>& rels) {
+        rels.clear();
+        for (int i = 0; i < Cl::SR; ++i) {
+          const int rel = k * Cl::SR + i, y = G.ys + rel;
+          if (y < 0 || y >= jd.H || rel >= G.rows) continue;
+          rels.push_back(rel);
+        }
+      };
+      std::vector<int> cur, nxt;
+      for (int k = 0; k < G.nst; ++k) {
+        h_rows(k, cur);
+        for (int rel : cur) owner[rel % Cl::RING] = rel;
+        h_rows(k + 1, nxt);
+        int m_lo, m_hi;
+        ready_blocks<Cl>(G, k, m_lo, m_hi);
+        for (int m = m_lo; m <= m_hi; ++m) {
+          if (m < 0 || m >= G.nblk || done[m]) return fail("block scheduled twice or out of range", m, k);
+          done[m] = 1;
+          const int r = G.rb0 + m;
+          for (int i = 0; i < Cl::L; ++i) {
+            int yc = r * Cl::Q + Cl::BMIN + i;
+            yc = yc < 0 ? 0 : (yc > jd.H - 1 ? jd.H - 1 : yc);
+            const int rel = yc - G.ys;
+            if (rel < 0 || rel >= G.rows) return fail("V row outside the tile", rel, G.rows);
+            if (owner[rel % Cl::RING] != rel) return fail("V row not in the ring", rel, k);
+            for (int rn : nxt)
+              if (rn % Cl::RING == rel % Cl::RING) return fail("V row overwritten by the next stage", rel, rn);
+          }
+          const int ncols = std::min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
+          for (int j = 0; j < Cl::P; ++j) {
+            const int oy = r * Cl::P + j;
+            if (oy >= jd.OH) break;
+            for (int e = 0; e < ncols; ++e) written[((size_t)oy * jd.OW + G.ox0) * Cl::C + e]++;
+          }
+        }
+      }
+      for (int m = 0; m < G.nblk; ++m)
+        if (!done[m]) return fail("block never scheduled", m, chunk);
+    }
+  }
+  for (size_t i = 0; i < written.size(); ++i)
+    if (written[i] != 1) return fail("output element written != 1 times", (int)i, written[i]);
+  return std::string();
+}
+
+template <int NSTAGE, class Cl>
+std::string check_single(const JobDesc& jd) {
+  using KS = KernelShape<NSTAGE, Cl>;
+  return check_class<Cl, KS::STAGE_MAX, KS::SMEM>(jd);
+}
+
+template <class Cl>
+std::string check_mixed(const JobDesc& jd) {
+  using KS = KernelShape<3, CF32_38, CF32_12, CF32_23, CF16_38, CF16_12, CF16_23, CU8_38, CU8_12, CU8_23>;
+  return check_class<Cl, KS::STAGE_MAX, KS::SMEM>(jd);
+}
+
+std::string check_plan(const ds_plan* pl) {
+  JobDesc jd;
+  std::memset(&jd, 0, sizeof(jd));
+  fill_job_geometry(jd, pl, nullptr, 1);
+  std::string a, b;
+  switch (pl->fast_class) {
+    case kFcF32_38: a = check_single<4, CF32_38>(jd); b = check_mixed<CF32_38>(jd); break;
+    case kFcF32_12: a = check_single<4, CF32_12>(jd); b = check_mixed<CF32_12>(jd); break;
+    case kFcF32_23: a = check_single<4, CF32_23>(jd); b = check_mixed<CF32_23>(jd); break;
+    case kFcF16_38: a = check_single<6, CF16_38>(jd); b = check_mixed<CF16_38>(jd); break;
+    case kFcF16_12: a = check_single<6, CF16_12>(jd); b = check_mixed<CF16_12>(jd); break;
+    case kFcF16_23: a = check_single<6, CF16_23>(jd); b = check_mixed<CF16_23>(jd); break;
+    case kFcU8C3_38: a = check_single<8, CU8_38>(jd); b = check_mixed<CU8_38>(jd); break;
+    case kFcU8C3_12: a = check_single<8, CU8_12>(jd); b = check_mixed<CU8_12>(jd); break;
+    case kFcU8C3_23: a = check_single<4, CU8_23>(jd); b = check_mixed<CU8_23>(jd); break;
+    default: return std::string();
+  }
+  return a.empty() ? b : a;
+}
+
+ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
+  static thread_local FastParams prm;  // ~13 KB, too large for the stack of some callers
+  std::memset(&prm, 0, sizeof(prm));
+  fill_taps(prm);
+  int cls = jobs[0].plan->fast_class;
+  int want_ctas = jobs[0].plan->ctas_per_sm;
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    ds_status s = encode_job(prm.jobs[i], jobs[i]);
+    if (s != DS_OK) return s;
+    prm.jobs[i].tile_begin = tiles;
+    tiles += prm.jobs[i].tiles;
+    if (jobs[i].plan->fast_class != cls) cls = -1;
+    want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
+  }
+  prm.n_jobs = n;
+  prm.total_tiles = tiles;
+  if (tiles == 0) return DS_OK;
+  const KernelInfo ki = kernel_for(cls);
+  int occ = ctas_per_sm(ki);
+  if (occ <= 0) {
+    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", ki.smem);
+    return DS_ERR_UNSUPPORTED;
+  }
+  if (want_ctas > 0) occ = std::min(occ, want_ctas);
+  const int grid = std::min(tiles, sm_count() * occ);
+  void* args[] = {&prm};
+  cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(kThreads), args, (size_t)ki.smem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "k_fused_tma launch");
+  count_launches(1);
+  return DS_OK;
+}
+
+}  // namespace
+
+int fast_max_jobs_per_launch() { return kMaxJobs; }
+
+ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
+  for (int i = 0; i < n; i += kMaxJobs) {
+    ds_status s = launch_chunk(jobs + i, std::min(kMaxJobs, n - i), st);
+    if (s != DS_OK) return s;
+  }
+  return DS_OK;
+}
+
+ds_status debug_check_plan(const ds_plan* pl, std::string& msg) {
+  msg = check_plan(pl);
+  return msg.empty() ? DS_OK : DS_ERR_ARG;
+}
+
+ds_status read_device_status(int* status) {
+  int v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_fast_status, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+  if (v != 0) {
+    e = cudaMemcpyToSymbol(g_fast_status, &zero, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");
+  }
+  *status = v;
+  return DS_OK;
+}
+
+}  // namespace ds

@@ -1,0 +1,93 @@
+// internal.h -- shared host-side declarations of libds (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ds.h"
+
+namespace ds {
+
+constexpr int kMaxP = 16;
+constexpr int kMaxQ = 64;
+constexpr int kMaxK = 16;
+
+// Fast-path classes: (dtype, p/q, K) combinations with a hand-tuned TMA
+// kernel instantiation.  Everything else runs on the general kernels.
+enum FastClass : int {
+  kFcNone = -1,
+  kFcF32_38 = 0,  // float, 3/8, K=8
+  kFcF32_12,      // float, 1/2, K=6
+  kFcF32_23,      // float, 2/3, K=6
+  kFcF16_38,
+  kFcF16_12,
+  kFcF16_23,
+  kFcU8C3_38,     // uint8 RGB, 3/8, K=8
+  kFcU8C3_12,     // uint8 RGB, 1/2, K=6
+  kFcU8C3_23,     // uint8 RGB, 2/3, K=6
+  kFcCount
+};
+
+}  // namespace ds
+
+struct ds_plan {
+  int in_h = 0, in_w = 0, channels = 1, elem_size = 4;
+  int p = 1, q = 2, K = 2;
+  ds_dtype dtype = DS_F32;
+  int out_h = 0, out_w = 0;
+  int b[ds::kMaxP] = {};                     // window start of each phase
+  double w64[ds::kMaxP * ds::kMaxK] = {};    // FP64 taps [p][K]
+  float w32[ds::kMaxP * ds::kMaxK] = {};     // (float) of w64
+  short q14[ds::kMaxP * ds::kMaxK] = {};     // Q14 taps
+  int fast_class = ds::kFcNone;              // -1: general kernels only
+  int row_blocks = 0;                        // fused tile: output row blocks per tile
+  int ctas_per_sm = 0;                       // persistent grid: 0 = occupancy
+  bool force_general = false;                // DS_NO_TMA or unsupported alignment
+
+  size_t in_frame_elems() const { return (size_t)in_h * in_w * channels; }
+  size_t out_frame_elems() const { return (size_t)out_h * out_w * channels; }
+};
+
+namespace ds {
+
+// Error reporting (thread-local message).
+void set_error(const char* fmt, ...);
+void clear_error();
+ds_status cuda_fail(cudaError_t e, const char* what);
+
+// Launch accounting (per host thread).
+void count_launches(long long n);
+
+// Plan helpers (plan.cpp).
+int fast_class_of(int p, int q, int K, ds_dtype dtype);
+bool frame_tma_ok(const ds_plan* plan, const void* in, size_t frame_stride_bytes);
+
+// Kernel launchers.
+// fused_fast.cu: all jobs must have fast_class >= 0 and TMA-compatible input.
+struct FastJob {
+  const ds_plan* plan;
+  const void* in;
+  void* out;
+  int n_frames;
+};
+ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t stream);
+int fast_max_jobs_per_launch();
+ds_status read_device_status(int* status);  // reads and clears the status word
+ds_status debug_check_plan(const ds_plan* plan, std::string& msg);
+
+// general.cu: any plan, any alignment.
+ds_status launch_general_fused(const ds_plan* plan, const void* in, void* out, int n_frames,
+                               cudaStream_t stream);
+ds_status launch_unfused(const ds_plan* plan, const void* in, void* out, int n_frames,
+                         void* workspace, cudaStream_t stream);
+
+// Dispatch of one job to the best kernel (abi.cpp).
+ds_status run_jobs(const ds_job* jobs, int n, cudaStream_t stream);
+
+}  // namespace ds

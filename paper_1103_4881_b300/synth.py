@@ -1,0 +1,147 @@
+"""Seeded synthetic inputs for the downscaler workloads.
+
+Frames only: this module holds none of the filter's arithmetic.  The paper
+measures on its own 2000-frame CIF video (Sec. 3), which is not available;
+these generators stand in for it with the shapes, value ranges and seeds of
+the workload table below (numpy PCG64 streams, so the CUDA tests, the
+benchmark and the CPU oracle all see the same pixels).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+DS_F32, DS_F16, DS_U8, DS_U8_RGB = 0, 1, 2, 3
+NP_DTYPE = {DS_F32: np.float32, DS_F16: np.float16, DS_U8: np.uint8, DS_U8_RGB: np.uint8}
+CHANNELS = {DS_F32: 1, DS_F16: 1, DS_U8: 1, DS_U8_RGB: 3}
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    frames: int
+    height: int
+    width: int
+    ratio: tuple
+    taps: int
+    dtype: int
+    seed: int
+    content: str  # "uniform", "gradient", "bytes", "noisy_half"
+
+    @property
+    def channels(self) -> int:
+        return CHANNELS[self.dtype]
+
+    @property
+    def out_height(self) -> int:
+        return self.height * self.ratio[0] // self.ratio[1]
+
+    @property
+    def out_width(self) -> int:
+        return self.width * self.ratio[0] // self.ratio[1]
+
+    def frame_shape(self):
+        return (self.height, self.width) if self.channels == 1 else (self.height, self.width, self.channels)
+
+    def out_frame_shape(self):
+        oh, ow = self.out_height, self.out_width
+        return (oh, ow) if self.channels == 1 else (oh, ow, self.channels)
+
+    def bytes_per_frame(self) -> int:
+        """Algorithmic bytes: input read once plus output written once."""
+        isz = np.dtype(NP_DTYPE[self.dtype]).itemsize
+        return (self.height * self.width + self.out_height * self.out_width) * self.channels * isz
+
+
+WORKLOADS = {
+    # one 480x640 fp32 frame, uniform [0,1), 3/8 with 8 taps
+    "plain_480x640_f32": Workload("plain_480x640_f32", 1, 480, 640, (3, 8), 8, DS_F32, 1001, "uniform"),
+    # 64 fp32 1080x1920 frames, uniform plus a seeded smooth gradient, 3/8 K=8
+    "batch64_1080x1920_f32": Workload("batch64_1080x1920_f32", 64, 1080, 1920, (3, 8), 8, DS_F32, 2000, "gradient"),
+    # 300 uint8 RGB 1080x1920x3 frames, uniform bytes, 1/2 K=6, Q14 taps
+    "rgb300_1080x1920_u8": Workload("rgb300_1080x1920_u8", 300, 1080, 1920, (1, 2), 6, DS_U8_RGB, 3000, "bytes"),
+    # 128 fp16 2160x3840 frames, uniform + N(0, 0.05) clipped, 3/8 K=8
+    "uhd128_2160x3840_f16": Workload("uhd128_2160x3840_f16", 128, 2160, 3840, (3, 8), 8, DS_F16, 4000, "noisy_half"),
+}
+
+
+def frame(w: Workload, i: int) -> np.ndarray:
+    """Frame i of workload w (i is also the seed offset)."""
+    if w.content == "uniform":
+        rng = np.random.default_rng(w.seed + i)
+        return rng.random(w.frame_shape(), dtype=np.float32)
+    if w.content == "gradient":
+        rng = np.random.default_rng(w.seed + i)
+        u = rng.random((w.height, w.width), dtype=np.float32)
+        alpha, beta = rng.random(2)
+        gx = np.arange(w.width, dtype=np.float64) / max(1, w.width - 1)
+        gy = np.arange(w.height, dtype=np.float64) / max(1, w.height - 1)
+        v = (u + alpha * gx[None, :] + beta * gy[:, None]) / (1.0 + alpha + beta)
+        return v.astype(np.float32)
+    if w.content == "bytes":
+        rng = np.random.default_rng(w.seed + i)
+        return rng.integers(0, 256, w.frame_shape(), dtype=np.uint8)
+    if w.content == "noisy_half":
+        rng = np.random.default_rng(w.seed + i)
+        u = rng.random(w.frame_shape(), dtype=np.float32)
+        n = rng.normal(0.0, 0.05, w.frame_shape()).astype(np.float32)
+        return np.clip(u + n, 0.0, 1.0).astype(np.float16)
+    raise ValueError(w.content)
+
+
+def frames(w: Workload, idx=None) -> np.ndarray:
+    """Frames idx (default: all) stacked as (n, H, W[, C])."""
+    idx = range(w.frames) if idx is None else idx
+    return np.stack([frame(w, i) for i in idx])
+
+
+def random_frames(shape, dtype: int, seed: int) -> np.ndarray:
+    """Generic seeded frames for tests: floats uniform [0,1), bytes uniform 0..255."""
+    rng = np.random.default_rng(seed)
+    if dtype in (DS_U8, DS_U8_RGB):
+        return rng.integers(0, 256, shape, dtype=np.uint8)
+    x = rng.random(shape, dtype=np.float32)
+    return x.astype(NP_DTYPE[dtype])
+
+
+# --------------------------------------------------------------------------
+# serving mix: 2000 requests, Poisson arrivals at 5000/s
+# --------------------------------------------------------------------------
+SERVE_SIZES = ((480, 640), (720, 1280), (1080, 1920), (2160, 3840))
+SERVE_RATIOS = (((1, 2), 6), ((3, 8), 8), ((2, 3), 6))
+SERVE_DTYPES = (DS_U8_RGB, DS_F16, DS_F32)
+
+
+@dataclass(frozen=True)
+class Request:
+    rid: int
+    arrival_s: float
+    height: int
+    width: int
+    ratio: tuple
+    taps: int
+    dtype: int
+
+
+def serving_requests(n: int = 2000, rate_hz: float = 5000.0, seed_arrivals: int = 5000,
+                     seed_shapes: int = 5001):
+    """Requests with exponential inter-arrival times (mean 1/rate) and uniformly
+    drawn size, ratio and dtype."""
+    ra = np.random.default_rng(seed_arrivals)
+    t = np.cumsum(ra.exponential(1.0 / rate_hz, n))
+    rs = np.random.default_rng(seed_shapes)
+    si = rs.integers(0, len(SERVE_SIZES), n)
+    ri = rs.integers(0, len(SERVE_RATIOS), n)
+    di = rs.integers(0, len(SERVE_DTYPES), n)
+    out = []
+    for k in range(n):
+        (h, w), (ratio, taps), dt = SERVE_SIZES[si[k]], SERVE_RATIOS[ri[k]], SERVE_DTYPES[di[k]]
+        out.append(Request(k, float(t[k]), h, w, ratio, taps, dt))
+    return out
+
+
+def request_frame(req: Request) -> np.ndarray:
+    """Pixel content of a request: uniform floats / bytes, seeded by its id."""
+    shape = (req.height, req.width) if CHANNELS[req.dtype] == 1 else (req.height, req.width, 3)
+    return random_frames(shape, req.dtype, 6000 + req.rid)
