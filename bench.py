@@ -38,6 +38,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch64_1080x1920_f32")
+    ap.add_argument("--frames", type=int, default=0, help="override the workload's frame count (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip per-frame / unfused / e2e / cpu legs")
     return ap.parse_args()
 
@@ -214,6 +215,10 @@ def main():
     from paper_1103_4881_b300 import synth
 
     w = synth.WORKLOADS[args.workload]
+    if args.frames > 0:
+        import dataclasses
+
+        w = dataclasses.replace(w, frames=args.frames)
     if args.impl == "reference":
         reference_arm(args, w, rank, world)
         return

@@ -26,7 +26,7 @@
 // 0, the same sequence as the general kernels, so results are identical bit
 // for bit whatever kernel, tile or batch computes them.
 //
-// Every wait on an mbarrier is bounded (%globaltimer, 1 s).  On expiry the
+// Every wait on an mbarrier is bounded (2e9 SM clock cycles, about 1 s).  On expiry the
 // kernel records DS_ERR_TIMEOUT in a device status word, the consumers agree
 // on leaving through a barrier with OR-reduction, and the producer waits
 // (bounded) for the copies it issued before it returns.
@@ -48,11 +48,15 @@ __device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out; 2 = bad clas
 
 namespace {
 
-constexpr int kNWC = 4;                       // consumer warps
+constexpr int kNH = 8;                        // horizontal-pass warps
+constexpr int kNV = 4;                        // vertical-pass warps
+constexpr int kNWC = kNH + kNV;               // consumer warps
 constexpr int kThreads = (kNWC + 1) * 32;     // + one producer warp
+constexpr int kNRS = 4;                       // intermediate ring capacity, in stages
 constexpr int kMaxJobs = 64;                  // job descriptors per launch
 constexpr int kMaxTaps = 24;                  // p*K of the fast classes
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;
+constexpr long long kWaitLimitCycles = 2000000000ll;  // ~1 s at the B300's 2.03 GHz
+constexpr uint32_t kSuspendHintNs = 20000;             // a waiting thread sleeps up to 20 us per poll
 constexpr int kStatusTimeout = 1;
 constexpr int kStatusBadClass = 2;
 
@@ -66,6 +70,7 @@ __host__ __device__ constexpr int rup(int a, int m) { return cdiv(a, m) * m; }
 __host__ __device__ constexpr int phase_b(int P, int Q, int K, int j) {
   return cfloordiv((2 * j + 1) * Q - P, 2 * P) - K / 2 + 1;
 }
+__host__ __device__ constexpr int pow2_at_least(int a) { return a <= 1 ? 1 : 2 * pow2_at_least((a + 1) / 2); }
 constexpr int cmax(int a) { return a; }
 template <typename... R>
 constexpr int cmax(int a, int b, R... r) { return cmax(a > b ? a : b, r...); }
@@ -94,7 +99,7 @@ struct Cls {
   using T = T_;
   using R = typename RingOf<T_>::type;
   static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_, WX = WX_, SR = SR_, VE = VE_;
-  static constexpr int WY = kNWC / WX;
+  static constexpr int WY = kNH / WX;
   static constexpr int SZ = (int)sizeof(T);
   static constexpr int BMIN = phase_b(P, Q, K, 0);
   static constexpr int BMAX = phase_b(P, Q, K, P - 1);
@@ -104,8 +109,6 @@ struct Cls {
   static constexpr int E = NB * Q * C;        // elements per thread and row
   static constexpr int EB = E * SZ;
   static constexpr int EW = EB / 4;
-  static constexpr int HWL = cdiv(LH * C * SZ, 4);  // halo words from the left lane
-  static constexpr int HWR = cdiv(RH * C * SZ, 4);  // halo words from the right lane
   static constexpr int HLB = rup(LH * C * SZ, 16);  // left halo bytes in the window (TMA x alignment)
   static constexpr int RHB = rup(RH * C * SZ, 16);
   static constexpr int SBLK = 32 * NB * WX;         // packets (blocks) per strip
@@ -118,31 +121,38 @@ struct Cls {
   static constexpr int STAGE_BYTES = NBOX * BOXSTR;
   static constexpr int TX_BYTES = NBOX * SR * BOXB;
   static constexpr int SOE = SBLK * P * C;            // intermediate elements per ring row
-  static constexpr int RING = 2 * SR + L + Q;         // ring rows (see consume_tile)
+  static constexpr int RING = kNRS * SR;              // ring rows: kNRS stages of SR rows
+  static constexpr int RING_MASK = RING - 1;
+  static constexpr int D = cdiv(L - 1, SR);           // V of stage k reads rows of stages k-D..k
   static constexpr int RING_BYTES = rup(RING * SOE * (int)sizeof(R), 16);
   static constexpr int NX = (LH + NB * Q + RH) * C;   // elements one thread reads per row
   static constexpr int VB = (EB % 16 == 0) ? 16 : ((EB % 8 == 0) ? 8 : 4);
   static constexpr int NV = EB / VB;
-  static constexpr int ROT = (VB == 16 && (NV == 2 || NV == 4)) ? NV : 1;
+  static constexpr int HB = cdiv(LH * C * SZ, VB);   // halo vectors a thread loads before its chunk
+  static constexpr int HA = cdiv(RH * C * SZ, VB);   // ... and after it
+  static constexpr int NVT = HB + NV + HA;           // vectors per thread and row
+  static constexpr int NWT = NVT * VB / 4;           // words per thread and row
   static constexpr int NOUT = NB * P * C;             // H outputs per thread and row
   __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
   static_assert(EB % 4 == 0, "a thread's chunk must be whole words");
-  static_assert(HWL <= EW && HWR <= EW, "halo wider than a neighbour's chunk");
+  static_assert(HB * VB <= HLB && HA * VB <= RHB, "halo vectors must lie in the loaded window");
   static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
   static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
-  static_assert(SR % WY == 0 && kNWC % WX == 0, "stage rows must split over warp rows");
-  static_assert(SOE % VE == 0 && (VE == 1 || VE == 4), "V-pass vector width");
+  static_assert(SR % WY == 0 && kNH % WX == 0, "stage rows must split over warp rows");
+  static_assert((SR & (SR - 1)) == 0 && kNRS >= D + 1, "ring of kNRS power-of-two stages");
+  static_assert(SOE % 4 == 0 && VE == 4, "V pass works on groups of 4 columns");
+  static_assert((RING & RING_MASK) == 0, "ring size");
   static_assert(P * K <= kMaxTaps, "tap table size");
   static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
 };
 
 //                 id        T     C  P  Q  K  NB WX  SR VE
-using CF32_38 = Cls<kFcF32_38, float, 1, 3, 8, 8, 1, 1, 16, 1>;
-using CF32_12 = Cls<kFcF32_12, float, 1, 1, 2, 6, 4, 1, 16, 1>;
-using CF32_23 = Cls<kFcF32_23, float, 1, 2, 3, 6, 4, 1, 12, 1>;
-using CF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 1, 16, 1>;
-using CF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 1, 16, 1>;
-using CF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 4, 1, 12, 1>;
+using CF32_38 = Cls<kFcF32_38, float, 1, 3, 8, 8, 1, 1, 16, 4>;
+using CF32_12 = Cls<kFcF32_12, float, 1, 1, 2, 6, 4, 1, 16, 4>;
+using CF32_23 = Cls<kFcF32_23, float, 1, 2, 3, 6, 2, 1, 16, 4>;
+using CF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 1, 16, 4>;
+using CF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 1, 16, 4>;
+using CF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 1, 16, 4>;
 using CU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 1, 8, 4>;
 using CU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 2, 2, 8, 4>;
 using CU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 1, 8, 4>;
@@ -185,28 +195,26 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(saddr32(bar)), "r"(parity)
+      : "r"(saddr32(bar)), "r"(parity), "r"(kSuspendHintNs)
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-// Wait for the phase of `parity` to complete; false after kWaitLimitNs, or
-// at once when *abort_flag becomes non-zero (if given).
+// Wait for the phase of `parity` to complete; false after about a second
+// (kWaitLimitCycles SM clock cycles, counted from the 4th failed poll), or at
+// once when *abort_flag becomes non-zero (if given).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
-  if (mbar_try(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
+#pragma unroll 1
+  for (int it = 0; it < 4; ++it)
+    if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 31u) == 0) {
+    if ((it & 3u) == 0) {
       if (abort_flag && *abort_flag) return false;
-      if (gtimer() - t0 > kWaitLimitNs) return false;
+      if (clock64() - t0 > kWaitLimitCycles) return false;
     }
   }
 }
@@ -217,21 +225,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr32(bar))
       : "memory");
 }
-// Barrier over the consumer warps only (named barrier 1), with OR of `pred`.
-__device__ __forceinline__ int consumers_sync_or(int pred) {
-  int r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.s32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, 1, %2, p;\n\t"
-      "selp.s32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"(pred), "n"(kNWC * 32)
-      : "memory");
-  return r;
-}
-__device__ __forceinline__ void consumers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kNWC * 32) : "memory"); }
-
 // ---------------------------------------------------------------------------
 // tiles
 // ---------------------------------------------------------------------------
@@ -282,12 +275,13 @@ __host__ __device__ __forceinline__ Geo tile_geo(const JobDesc& jd, const Tile& 
   return g;
 }
 
-// Byte `byte` of window row `row` inside a stage: boxes are stored one after
-// the other, each as SR rows of BOXB bytes.
+// Offset of byte `byte` of window row 0 inside a stage: boxes are stored one
+// after the other, each as SR rows of BOXB bytes (BOXSTR bytes apart), so row
+// r of the window starts r * BOXB bytes further in every box.
 template <class Cl>
-__device__ __forceinline__ const uint8_t* win_ptr(const uint8_t* stage, int row, int byte) {
+__host__ __device__ __forceinline__ int win_off(int byte) {
   const int box = byte / Cl::BOXB;
-  return stage + box * Cl::BOXSTR + row * Cl::BOXB + (byte - box * Cl::BOXB);
+  return byte + box * (Cl::BOXSTR - Cl::BOXB);
 }
 
 // ---------------------------------------------------------------------------
@@ -331,56 +325,82 @@ __device__ __forceinline__ float word_elem<uint8_t>(const uint32_t* w, int byte)
 template <typename T>
 __device__ __forceinline__ float smem_elem(const uint8_t* p) { return px_to_f(*reinterpret_cast<const T*>(p)); }
 
-// Load this thread's EB-byte chunk of window row `row` into words w[0..EW).
+// Per-thread shared-memory offsets (row 0 of a stage) of the vectors the H
+// pass loads: HB halo vectors, the thread's own NV vectors, HA halo vectors,
+// consecutive in the window.  They depend only on the lane: computed once.
 template <class Cl>
-__device__ __forceinline__ void load_chunk(const uint8_t* stage, int row, int byte0, int lane, uint32_t* w) {
-  constexpr int NV = Cl::NV, VB = Cl::VB, WPV = VB / 4;
-  // Lanes whose chunks would hit the same banks in one shared-memory phase
-  // start at a rotated vector; the words are put back in order afterwards.
-  const int rot = (Cl::ROT == 2) ? ((lane >> 2) & 1) : ((Cl::ROT == 4) ? ((lane >> 1) & 3) : 0);
-  uint32_t tmp[NV][WPV];
+struct Offs {
+  int v[Cl::NVT];
+};
+
+template <class Cl>
+__device__ __forceinline__ Offs<Cl> thread_offs(int lg) {
+  Offs<Cl> o;
+  const int first = Cl::HLB + lg * Cl::EB - Cl::HB * Cl::VB;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    int pv = v + rot;
-    if (Cl::ROT > 1 && pv >= NV) pv -= NV;
-    const uint8_t* p = win_ptr<Cl>(stage, row, byte0 + pv * VB);
-    if constexpr (VB == 16) {
+  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = win_off<Cl>(first + v * Cl::VB);
+  return o;
+}
+
+// Load the thread's vectors of one window row into words w[0..NWT).
+template <class Cl>
+__device__ __forceinline__ void load_row(const uint8_t* rowbase, const Offs<Cl>& o, uint32_t* w) {
+  constexpr int WPV = Cl::VB / 4;
+#pragma unroll
+  for (int v = 0; v < Cl::NVT; ++v) {
+    const uint8_t* p = rowbase + o.v[v];
+    if constexpr (Cl::VB == 16) {
       const uint4 x = *reinterpret_cast<const uint4*>(p);
-      tmp[v][0] = x.x; tmp[v][1] = x.y; tmp[v][2] = x.z; tmp[v][3] = x.w;
-    } else if constexpr (VB == 8) {
+      w[v * WPV] = x.x; w[v * WPV + 1] = x.y; w[v * WPV + 2] = x.z; w[v * WPV + 3] = x.w;
+    } else if constexpr (Cl::VB == 8) {
       const uint2 x = *reinterpret_cast<const uint2*>(p);
-      tmp[v][0] = x.x; tmp[v][1] = x.y;
+      w[v * WPV] = x.x; w[v * WPV + 1] = x.y;
     } else {
-      tmp[v][0] = *reinterpret_cast<const uint32_t*>(p);
+      w[v] = *reinterpret_cast<const uint32_t*>(p);
     }
-  }
-  // tmp[v] holds vector (v + rot) mod NV; put vector c back at w[c * WPV]
-  if constexpr (Cl::ROT == 2) {
-#pragma unroll
-    for (int q = 0; q < WPV; ++q) {
-      w[q] = rot ? tmp[1][q] : tmp[0][q];
-      w[WPV + q] = rot ? tmp[0][q] : tmp[1][q];
-    }
-  } else if constexpr (Cl::ROT == 4) {
-    // rotate right by rot = 2*r1 + r0: first by 2 (if r1), then by 1 (if r0)
-    const bool r1 = (rot & 2) != 0, r0 = (rot & 1) != 0;
-    uint32_t u[4][WPV];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int q = 0; q < WPV; ++q) u[c][q] = r1 ? tmp[(c + 2) & 3][q] : tmp[c][q];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int q = 0; q < WPV; ++q) w[c * WPV + q] = r0 ? u[(c + 3) & 3][q] : u[c][q];
-  } else {
-#pragma unroll
-    for (int c = 0; c < NV; ++c)
-#pragma unroll
-      for (int q = 0; q < WPV; ++q) w[c * WPV + q] = tmp[c][q];
   }
 }
 
+// Clamp-to-edge in the loaded window: the columns of a warp's read range that
+// lie outside the frame (TMA filled them with zeros) get the value of the
+// first / last column of their row.  Pixel ranges [l_lo, 0) and [r_lo, r_hi).
+struct EdgeFix {
+  int l_lo, nl, r_lo, nr;  // first pixel and element counts, left and right
+};
+
+template <class Cl>
+__host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int wx, int W) {
+  const int seg0 = strip * Cl::SPX + wx * 32 * Cl::NB * Cl::Q - Cl::LH;       // first pixel the warp reads
+  const int seg1 = strip * Cl::SPX + (wx + 1) * 32 * Cl::NB * Cl::Q + Cl::RH;  // one past the last
+  EdgeFix f;
+  f.l_lo = seg0;
+  f.nl = seg0 < 0 ? ((seg1 < 0 ? seg1 : 0) - seg0) * Cl::C : 0;
+  f.r_lo = W > seg0 ? W : seg0;
+  const int lim = W + Cl::NB * Cl::Q + Cl::RH;  // active lanes read no further
+  const int r_hi = seg1 < lim ? seg1 : lim;
+  f.nr = r_hi > f.r_lo ? (r_hi - f.r_lo) * Cl::C : 0;
+  return f;
+}
+
+template <class Cl>
+__device__ __forceinline__ void apply_edge_fix(uint8_t* rowbase, const EdgeFix& f, int lane, int W, int xw) {
+  using T = typename Cl::T;
+  for (int e = lane; e < f.nl + f.nr; e += 32) {
+    const bool left = e < f.nl;
+    const int k = left ? e : e - f.nl;
+    const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
+    const int src = (left ? 0 : W - 1) * Cl::C + c - xw;
+    const int dst = px * Cl::C + c - xw;
+    *reinterpret_cast<T*>(rowbase + win_off<Cl>(dst * Cl::SZ)) =
+        *reinterpret_cast<const T*>(rowbase + win_off<Cl>(src * Cl::SZ));
+  }
+  // these generic-proxy writes must land before the TMA refills the stage
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+}
+
+// Store a thread's NOUT horizontal results into its slice of a ring row with
+// the widest aligned vector stores (the slice starts at lg * NOUT elements).
 template <class Cl>
 __device__ __forceinline__ void ring_store(typename Cl::R* dst, const float* o) {
   constexpr int N = Cl::NOUT;
@@ -422,44 +442,17 @@ __device__ __forceinline__ void ring_store(typename Cl::R* dst, const float* o) 
   }
 }
 
+// Horizontal pass of one window row whose words the thread has loaded (see
+// load_row): NB packets of Q pixels per thread, each giving P outputs per
+// channel, stored to the thread's slice of a ring row.
 template <class Cl>
-__device__ __forceinline__ void hrow(const uint8_t* stage, int row, int lane, int lg, bool active, bool interior,
-                                     int px0, int W, int xw, const float* __restrict__ taps,
+__device__ __forceinline__ void hrow(const uint32_t* w, const float* __restrict__ taps,
                                      typename Cl::R* __restrict__ dst) {
   using T = typename Cl::T;
-  constexpr int HWL = Cl::HWL, EW = Cl::EW, HWR = Cl::HWR;
-  uint32_t w[HWL + EW + HWR];
-  const int byte0 = Cl::HLB + lg * Cl::EB;
-  load_chunk<Cl>(stage, row, byte0, lane, w + HWL);
-#pragma unroll
-  for (int i = 0; i < HWL; ++i) w[i] = __shfl_up_sync(0xffffffffu, w[HWL + EW - HWL + i], 1);
-#pragma unroll
-  for (int i = 0; i < HWR; ++i) w[HWL + EW + i] = __shfl_down_sync(0xffffffffu, w[HWL + i], 1);
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < HWL; ++i)
-      w[i] = *reinterpret_cast<const uint32_t*>(win_ptr<Cl>(stage, row, byte0 - 4 * HWL + 4 * i));
-  }
-  if (lane == 31) {
-#pragma unroll
-    for (int i = 0; i < HWR; ++i)
-      w[HWL + EW + i] = *reinterpret_cast<const uint32_t*>(win_ptr<Cl>(stage, row, byte0 + Cl::EB + 4 * i));
-  }
-  if (!active) return;
   float x[Cl::NX];
-  if (interior) {
-    constexpr int first = 4 * HWL - Cl::LH * Cl::C * Cl::SZ;  // byte of the first halo element in w
+  constexpr int first = Cl::HB * Cl::VB - Cl::LH * Cl::C * Cl::SZ;  // byte of the first halo element in w
 #pragma unroll
-    for (int e = 0; e < Cl::NX; ++e) x[e] = word_elem<T>(w, first + e * Cl::SZ);
-  } else {
-    // frame border: clamp-to-edge reads straight from the window
-#pragma unroll
-    for (int e = 0; e < Cl::NX; ++e) {
-      const int px = clampi(px0 - Cl::LH + e / Cl::C, 0, W - 1);
-      const int el = px * Cl::C + (e % Cl::C) - xw;
-      x[e] = smem_elem<T>(win_ptr<Cl>(stage, row, el * Cl::SZ));
-    }
-  }
+  for (int e = 0; e < Cl::NX; ++e) x[e] = word_elem<T>(w, first + e * Cl::SZ);
   float o[Cl::NOUT];
 #pragma unroll
   for (int n = 0; n < Cl::NB; ++n) {
@@ -481,27 +474,6 @@ __device__ __forceinline__ void hrow(const uint8_t* stage, int row, int lane, in
 // ---------------------------------------------------------------------------
 // consumer: vertical pass of the blocks that became ready at stage k
 // ---------------------------------------------------------------------------
-template <class Cl>
-__device__ __forceinline__ void ring_load(const typename Cl::R* p, float* h) {
-  if constexpr (sizeof(typename Cl::R) == 4) {
-    if constexpr (Cl::VE == 4) {
-      const float4 v = *reinterpret_cast<const float4*>(p);
-      h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
-    } else {
-      h[0] = *reinterpret_cast<const float*>(p);
-    }
-  } else {
-    if constexpr (Cl::VE == 4) {
-      const uint2 v = *reinterpret_cast<const uint2*>(p);
-      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-      h[0] = a.x; h[1] = a.y; h[2] = b.x; h[3] = b.y;
-    } else {
-      h[0] = __half2float(*reinterpret_cast<const __half*>(p));
-    }
-  }
-}
-
 // Row blocks (tile-relative) whose V pass runs at stage k: block m is ready
 // once its last pattern row m*Q + L - 1 has been loaded.
 template <class Cl>
@@ -513,106 +485,201 @@ __host__ __device__ __forceinline__ void ready_blocks(const Geo& G, int k, int& 
   if (m_hi > G.nblk - 1 || k == G.nst - 1) m_hi = G.nblk - 1;
 }
 
+// Four consecutive intermediate values of one ring row.
 template <class Cl>
-__device__ __forceinline__ void vpass(const JobDesc& jd, const Tile& tl, const Geo& G, int k,
-                                      const float* __restrict__ taps, const typename Cl::R* __restrict__ ring,
-                                      int tid) {
+__device__ __forceinline__ void ring_load4(const typename Cl::R* p, float* h) {
+  if constexpr (sizeof(typename Cl::R) == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
+  } else {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+    h[0] = a.x; h[1] = a.y; h[2] = b.x; h[3] = b.y;
+  }
+}
+
+// Store four output values (vector store when aligned and complete).
+template <typename T>
+__device__ __forceinline__ void store4(T* o, const float* v, bool vec, int n_valid) {
+  if (vec && n_valid >= 4) {
+    if constexpr (sizeof(T) == 4) {
+      *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (sizeof(T) == 2) {
+      const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+      *reinterpret_cast<uint2*>(o) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
+    } else {
+      uint32_t pk = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) pk |= (uint32_t)f_to_px<T>(v[i]) << (8 * i);
+      *reinterpret_cast<uint32_t*>(o) = pk;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (i < n_valid) o[i] = f_to_px<T>(v[i]);
+  }
+}
+
+// Output row r*P + J, columns e0..e0+3 of the strip: the K taps of phase J
+// over the ring rows of its window, in tap order.  `rbase` is the ring row of
+// the tile's relative row 0.
+template <class Cl, int J>
+__device__ __forceinline__ void vtask(const JobDesc& jd, const Geo& G, const float* __restrict__ taps,
+                                      const typename Cl::R* __restrict__ ring, int rbase, int r, int e0,
+                                      typename Cl::T* o, int n_valid) {
   using T = typename Cl::T;
-  int m_lo, m_hi;
-  ready_blocks<Cl>(G, k, m_lo, m_hi);
-  if (m_hi < m_lo) return;
-  const int ncols = min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
-  const int tpb = (ncols + Cl::VE - 1) / Cl::VE;
-  const int ntask = (m_hi - m_lo + 1) * tpb;
-  const int rowe = jd.OW * Cl::C;
-  T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)G.ox0 * Cl::C;
-  for (int task = tid; task < ntask; task += kNWC * 32) {
-    const int mb = task / tpb;
-    const int e0 = (task - mb * tpb) * Cl::VE;
-    const int r = G.rb0 + m_lo + mb;
-    float acc[Cl::P][Cl::VE];
+  const int row0 = r * Cl::Q + Cl::b(J);  // first input row of the window
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float h[4];
+  if (row0 >= 0 && row0 + Cl::K - 1 < jd.H) {
+    const int q0 = rbase + row0 - G.ys;
+    const int s0 = q0 & Cl::RING_MASK;
+    if (s0 + Cl::K <= Cl::RING) {
+      const typename Cl::R* p = ring + s0 * Cl::SOE + e0;  // K consecutive ring rows
 #pragma unroll
-    for (int j = 0; j < Cl::P; ++j)
+      for (int t = 0; t < Cl::K; ++t) {
+        ring_load4<Cl>(p + t * Cl::SOE, h);
 #pragma unroll
-      for (int v = 0; v < Cl::VE; ++v) acc[j][v] = 0.0f;
+        for (int v = 0; v < 4; ++v) acc[v] = fmaf(taps[J * Cl::K + t], h[v], acc[v]);
+      }
+    } else {
 #pragma unroll
-    for (int i = 0; i < Cl::L; ++i) {
-      const int yc = clampi(r * Cl::Q + Cl::BMIN + i, 0, jd.H - 1);
-      const int slot = (yc - G.ys) % Cl::RING;
-      float h[Cl::VE];
-      ring_load<Cl>(ring + slot * Cl::SOE + e0, h);
+      for (int t = 0; t < Cl::K; ++t) {
+        ring_load4<Cl>(ring + ((q0 + t) & Cl::RING_MASK) * Cl::SOE + e0, h);
 #pragma unroll
-      for (int j = 0; j < Cl::P; ++j) {
-        const int t = i - (Cl::b(j) - Cl::BMIN);
-        if (t >= 0 && t < Cl::K) {
-#pragma unroll
-          for (int v = 0; v < Cl::VE; ++v) acc[j][v] = fmaf(taps[j * Cl::K + t], h[v], acc[j][v]);
-        }
+        for (int v = 0; v < 4; ++v) acc[v] = fmaf(taps[J * Cl::K + t], h[v], acc[v]);
       }
     }
+  } else {
+    // frame top / bottom: clamp-to-edge rows
 #pragma unroll
-    for (int j = 0; j < Cl::P; ++j) {
-      const int oy = r * Cl::P + j;
-      if (oy >= jd.OH) break;
-      T* o = obase + (long long)oy * rowe + e0;
-      if constexpr (Cl::VE == 4) {
-        if (jd.out_vec && e0 + 4 <= ncols) {
-          uint32_t pk = 0;
+    for (int t = 0; t < Cl::K; ++t) {
+      const int yc = clampi(row0 + t, 0, jd.H - 1);
+      ring_load4<Cl>(ring + ((rbase + yc - G.ys) & Cl::RING_MASK) * Cl::SOE + e0, h);
 #pragma unroll
-          for (int v = 0; v < 4; ++v) pk |= (uint32_t)f_to_px<T>(pass_round<T>(acc[j][v])) << (8 * v);
-          *reinterpret_cast<uint32_t*>(o) = pk;
-        } else {
-#pragma unroll
-          for (int v = 0; v < 4; ++v)
-            if (e0 + v < ncols) o[v] = f_to_px<T>(pass_round<T>(acc[j][v]));
-        }
-      } else {
-        o[0] = f_to_px<T>(pass_round<T>(acc[j][0]));
-      }
+      for (int v = 0; v < 4; ++v) acc[v] = fmaf(taps[J * Cl::K + t], h[v], acc[v]);
     }
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) acc[v] = pass_round<T>(acc[v]);
+  store4<T>(o, acc, jd.out_vec != 0, n_valid);
+}
+
+template <class Cl, int J>
+__device__ __forceinline__ void vtask_phase(int j, const JobDesc& jd, const Geo& G, const float* taps,
+                                            const typename Cl::R* ring, int rbase, int r, int e0,
+                                            typename Cl::T* o, int n_valid) {
+  if constexpr (J < Cl::P) {
+    if (j == J) vtask<Cl, J>(jd, G, taps, ring, rbase, r, e0, o, n_valid);
+    else vtask_phase<Cl, J + 1>(j, jd, G, taps, ring, rbase, r, e0, o, n_valid);
   }
 }
 
 // ---------------------------------------------------------------------------
-// consumer: one tile
+// consumers: one tile
 // ---------------------------------------------------------------------------
-// Ring safety: ring rows are indexed by the tile-relative input row.  After
-// the barrier of stage k a fast warp may run the H pass of stage k+1 (rows
-// up to (k+2)*SR - 1) while a slow warp still runs the V pass of stage k,
-// whose rows start at or after k*SR - L + 1.  RING = 2*SR + L + Q rows keeps
-// the two apart; the next tile starts only after a consumer barrier.
+// Three pipelines meet here.  TMA -> H warps through full/empty (one stage
+// of input rows each).  H warps -> V warps through hdone/vdone over the ring
+// of intermediate rows, which holds kNRS stages: the rows of stage g live in
+// ring rows (g*SR .. g*SR+SR-1) mod RING.  The V pass of stage g reads rows of
+// stages g-D..g only (its blocks' windows are L <= D*SR+1 rows tall), so the
+// H pass of stage g may overwrite stage g-kNRS once the V pass of stage
+// g-kNRS+D is done.  When the class changes between tiles (the all-class
+// kernel), the ring layout changes with it and the H pass waits for every
+// earlier V pass instead.
 template <class Cl, int NSTAGE, int STAGE_MAX>
-__device__ bool consume_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl, const uint8_t* stages,
-                             uint8_t* ring_raw, uint64_t* full, uint64_t* empty, uint32_t& g) {
+__device__ bool h_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl, uint8_t* stages,
+                       uint8_t* ring_raw, uint64_t* full, uint64_t* empty, uint64_t* hdone, uint64_t* vdone,
+                       uint32_t& g, bool class_changed, const volatile int* abort_flag) {
   using R = typename Cl::R;
   R* ring = reinterpret_cast<R*>(ring_raw);
   const float* taps = prm.taps[Cl::id];
   const Geo G = tile_geo<Cl>(jd, tl);
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wx = warp % Cl::WX, wy = warp / Cl::WX;
   const int lg = wx * 32 + lane;                         // chunk index across the strip
   const int blk0 = tl.strip * Cl::SBLK + lg * Cl::NB;   // first packet of the chunk (frame coords)
   const int px0 = blk0 * Cl::Q;
   const bool active = blk0 * Cl::P < jd.OW;
-  const bool interior = (px0 - Cl::LH >= 0) && (px0 + Cl::NB * Cl::Q + Cl::RH <= jd.W);
+  (void)px0;
+  const Offs<Cl> of = thread_offs<Cl>(lg);
+  const EdgeFix fix = edge_fix<Cl>(tl.strip, wx, jd.W);
+  R* const ring_mine = ring + lg * Cl::NOUT;
   for (int k = 0; k < G.nst; ++k, ++g) {
-    const uint32_t slot = g % NSTAGE, round = g / NSTAGE;
-    const bool ok = mbar_wait(&full[slot], round & 1u, nullptr);
-    const uint8_t* stage = stages + slot * STAGE_MAX;
-    if (ok) {
-      for (int i = wy; i < Cl::SR; i += Cl::WY) {
-        const int rel = k * Cl::SR + i;
-        const int y = G.ys + rel;
-        if (y < 0 || y >= jd.H || rel >= G.rows) continue;  // never read by the V pass
-        hrow<Cl>(stage, i, lane, lg, active, interior, px0, jd.W, G.xw, taps,
-                 ring + (rel % Cl::RING) * Cl::SOE + lg * Cl::NOUT);
+    const uint32_t slot = g % NSTAGE;
+    bool ok = mbar_wait(&full[slot], (g / NSTAGE) & 1u, abort_flag);
+    const int dep = (class_changed && k == 0) ? (int)g - 1 : (int)g - kNRS + Cl::D;
+    if (ok && dep >= 0) ok = mbar_wait(&vdone[dep % kNRS], (uint32_t)(dep / kNRS) & 1u, abort_flag);
+    if (!ok) return false;
+    uint8_t* stage = stages + slot * STAGE_MAX;
+    // the warp's rows of this stage: border fix-ups, then all loads, then the
+    // arithmetic (so the loads of every row are in flight together)
+    constexpr int NR = Cl::SR / Cl::WY;
+    bool valid[NR];
+    uint32_t w[NR][Cl::NWT];
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+      const int i = wy + s * Cl::WY;
+      const int rel = k * Cl::SR + i;
+      const int y = G.ys + rel;
+      valid[s] = y >= 0 && y < jd.H && rel < G.rows;  // other rows are never read by the V pass
+      if (valid[s] && fix.nl + fix.nr > 0) apply_edge_fix<Cl>(stage + i * Cl::BOXB, fix, lane, jd.W, G.xw);
+    }
+#pragma unroll
+    for (int s = 0; s < NR; ++s)
+      if (valid[s]) load_row<Cl>(stage + (wy + s * Cl::WY) * Cl::BOXB, of, w[s]);
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < NR; ++s)
+        if (valid[s])
+          hrow<Cl>(w[s], taps, ring_mine + ((g * Cl::SR + wy + s * Cl::WY) & Cl::RING_MASK) * Cl::SOE);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&empty[slot]);
+      mbar_arrive(&hdone[g % kNRS]);
+    }
+  }
+  return true;
+}
+
+template <class Cl>
+__device__ bool v_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl, const uint8_t* ring_raw,
+                       uint64_t* hdone, uint64_t* vdone, uint32_t& g, const volatile int* abort_flag) {
+  using T = typename Cl::T;
+  using R = typename Cl::R;
+  const R* ring = reinterpret_cast<const R*>(ring_raw);
+  const float* taps = prm.taps[Cl::id];
+  const Geo G = tile_geo<Cl>(jd, tl);
+  const int vw = (threadIdx.x >> 5) - kNH, lane = threadIdx.x & 31;
+  const int ncols = min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
+  const int rowe = jd.OW * Cl::C;
+  T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)G.ox0 * Cl::C;
+  const int rbase = (int)((g * Cl::SR) & Cl::RING_MASK);  // ring row of the tile's first row
+  for (int k = 0; k < G.nst; ++k, ++g) {
+    if (!mbar_wait(&hdone[g % kNRS], (g / kNRS) & 1u, abort_flag)) return false;
+    int m_lo, m_hi;
+    ready_blocks<Cl>(G, k, m_lo, m_hi);
+    // one (block, phase) pair per warp at a time, so the phase -- and with it
+    // the compiled tap sequence -- is uniform across the warp; lanes take
+    // groups of 4 columns (groups past the frame's right edge are skipped)
+    constexpr int TPR = Cl::SOE / 4;
+    const int npairs = (m_hi - m_lo + 1) * Cl::P;
+    for (int pair = vw; pair < npairs; pair += kNV) {
+      const int mb = pair / Cl::P, j = pair - mb * Cl::P;
+      const int r = G.rb0 + m_lo + mb;
+      const int oy = r * Cl::P + j;
+      if (oy >= jd.OH) continue;
+      T* const orow = obase + (long long)oy * rowe;
+      for (int grp = lane; grp < TPR; grp += 32) {
+        const int e0 = grp * 4;
+        if (e0 >= ncols) break;
+        vtask_phase<Cl, 0>(j, jd, G, taps, ring, rbase, r, e0, orow + e0, ncols - e0);
       }
     }
     __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[slot]);
-    if (consumers_sync_or(!ok)) return false;
-    vpass<Cl>(jd, tl, G, k, taps, ring, tid);
+    if (lane == 0) mbar_arrive(&vdone[g % kNRS]);
   }
   return true;
 }
@@ -641,11 +708,14 @@ struct KernelShape {
   static constexpr int STAGE_MAX = cmax(Cs::STAGE_BYTES...);
   static constexpr int RING_MAX = cmax(Cs::RING_BYTES...);
   static constexpr int BAR_OFF = NSTAGE * STAGE_MAX + RING_MAX;
-  static constexpr int SMEM = 128 + BAR_OFF + 2 * NSTAGE * 8 + 16;
+  static constexpr int SMEM = 128 + BAR_OFF + (2 * NSTAGE + 2 * kNRS) * 8 + 16;
 };
 
-template <int NSTAGE, class... Cs>
-__global__ void __launch_bounds__(kThreads, 2) k_fused_tma(const __grid_constant__ FastParams prm) {
+// MINB: resident CTAs per SM the registers are budgeted for (2 for the
+// single-class kernels; 1 for the all-class kernel, whose union of code paths
+// needs more registers).
+template <int NSTAGE, int MINB, class... Cs>
+__global__ void __launch_bounds__(kThreads, MINB) k_fused_tma(const __grid_constant__ FastParams prm) {
   using KS = KernelShape<NSTAGE, Cs...>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -653,13 +723,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_tma(const __grid_constant
   uint8_t* ring = smem + NSTAGE * KS::STAGE_MAX;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + KS::BAR_OFF);
   uint64_t* empty = full + NSTAGE;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NSTAGE);
+  uint64_t* hdone = empty + NSTAGE;
+  uint64_t* vdone = hdone + kNRS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(vdone + kNRS);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kNWC);
+      mbar_init(&empty[s], kNH);
+    }
+    for (int s = 0; s < kNRS; ++s) {
+      mbar_init(&hdone[s], kNH);
+      mbar_init(&vdone[s], kNV);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -681,6 +757,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_tma(const __grid_constant
     }
     if (!ok) {
       // leave no copy in flight: wait (bounded) for the last round of each slot
+      *abort_flag = 1;
       atomicCAS(&g_fast_status, 0, kStatusTimeout);
       for (uint32_t s = 0; s < NSTAGE && s < g; ++s) {
         const uint32_t last = g - 1 - s;
@@ -690,21 +767,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_tma(const __grid_constant
     return;
   }
 
-  // --------------------------------- consumers
+  // --------------------------------- consumers: H warps and V warps
   uint32_t g = 0;
-  bool first = true;
+  int prev_cls = -1;
   for (int t = blockIdx.x; t < prm.total_tiles; t += gridDim.x) {
     const Tile tl = decode_tile(prm, t);
     const JobDesc& jd = prm.jobs[tl.job];
-    if (!first) consumers_sync();  // the ring is reused by the next tile
-    first = false;
     int code = kStatusBadClass;
+    const bool changed = prev_cls >= 0 && prev_cls != jd.cls;
+    prev_cls = jd.cls;
     const bool ok = Dispatch<Cs...>::run(jd.cls, [&](auto cl) {
       code = kStatusTimeout;
-      return consume_tile<decltype(cl), NSTAGE, KS::STAGE_MAX>(prm, jd, tl, stages, ring, full, empty, g);
+      if (warp < kNH)
+        return h_tile<decltype(cl), NSTAGE, KS::STAGE_MAX>(prm, jd, tl, stages, ring, full, empty, hdone, vdone, g,
+                                                         changed, abort_flag);
+      return v_tile<decltype(cl)>(prm, jd, tl, ring, hdone, vdone, g, abort_flag);
     });
     if (!ok) {
-      if (threadIdx.x == 0) {
+      if (lane == 0) {
         *abort_flag = 1;
         atomicCAS(&g_fast_status, 0, code);
       }
@@ -760,7 +840,8 @@ struct KernelInfo {
 
 template <int NSTAGE, class... Cs>
 KernelInfo kernel_info() {
-  return KernelInfo{reinterpret_cast<const void*>(&k_fused_tma<NSTAGE, Cs...>), KernelShape<NSTAGE, Cs...>::SMEM};
+  constexpr int minb = sizeof...(Cs) == 1 ? 2 : 1;
+  return KernelInfo{reinterpret_cast<const void*>(&k_fused_tma<NSTAGE, minb, Cs...>), KernelShape<NSTAGE, Cs...>::SMEM};
 }
 
 // single-class kernels (uniform batches) and the all-class kernel (mixes)
@@ -901,51 +982,43 @@ std::string check_class(const JobDesc& jd) {
         const long long xb = (long long)(G.xw + bx * Cl::BOXE) * Cl::SZ;
         if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", G.xw, bx);
       }
-      for (int lg = 0; lg < 32 * Cl::WX; ++lg) {
-        const int lane = lg & 31;
-        const int byte0 = Cl::HLB + lg * Cl::EB;
-        for (int v = 0; v < Cl::NV; ++v) {
-          const int b0 = byte0 + v * Cl::VB;
-          if (b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB || b0 + Cl::VB > win) return fail("chunk read", lg, v);
+      for (int wx = 0; wx < Cl::WX; ++wx) {
+        const EdgeFix fx = edge_fix<Cl>(strip, wx, jd.W);
+        // fix-up sources and destinations stay in the window
+        for (int e = 0; e < fx.nl + fx.nr; ++e) {
+          const bool left = e < fx.nl;
+          const int k2 = left ? e : e - fx.nl;
+          const int px = (left ? fx.l_lo : fx.r_lo) + k2 / Cl::C, c = k2 % Cl::C;
+          const int src = (left ? 0 : jd.W - 1) * Cl::C + c - G.xw, dst = px * Cl::C + c - G.xw;
+          if (src < 0 || (src + 1) * Cl::SZ > win || dst < 0 || (dst + 1) * Cl::SZ > win)
+            return fail("edge fix outside the window", src, dst);
+          if (px >= 0 && px < jd.W) return fail("edge fix inside the frame", px, jd.W);
         }
-        if (lane == 0 && byte0 - 4 * Cl::HWL < 0) return fail("left halo read", lg, byte0);
-        if (lane == 31 && byte0 + Cl::EB + 4 * Cl::HWR > win) return fail("right halo read", lg, byte0);
-        const int blk0 = strip * Cl::SBLK + lg * Cl::NB;
-        const int px0 = blk0 * Cl::Q;
-        const bool active = blk0 * Cl::P < jd.OW;
-        const bool interior = (px0 - Cl::LH >= 0) && (px0 + Cl::NB * Cl::Q + Cl::RH <= jd.W);
-        if (active && interior) {
-          // the interior path reads pixels px0 - LH .. px0 + NB*Q + RH - 1 from the chunk and halos:
-          // they must be the window elements the TMA placed there
-          const int first_el = (px0 - Cl::LH) * Cl::C - G.xw;
-          const int want = byte0 - Cl::LH * Cl::C * Cl::SZ;
-          if (first_el * Cl::SZ != want) return fail("chunk not at its pixels", first_el, want);
-        }
-        if (active && !interior) {
-          for (int e = 0; e < Cl::NX; ++e) {
-            int px = px0 - Cl::LH + e / Cl::C;
-            px = px < 0 ? 0 : (px > jd.W - 1 ? jd.W - 1 : px);
-            const int el = px * Cl::C + (e % Cl::C) - G.xw;
-            if (el < 0 || (el + 1) * Cl::SZ > win) return fail("border read", lg, el);
+        for (int lane = 0; lane < 32; ++lane) {
+          const int lg = wx * 32 + lane;
+          const int first = Cl::HLB + lg * Cl::EB - Cl::HB * Cl::VB;
+          for (int v = 0; v < Cl::NVT; ++v) {
+            const int b0 = first + v * Cl::VB;
+            if (b0 < 0 || b0 + Cl::VB > win || b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB)
+              return fail("vector read", lg, b0);
           }
+          const int blk0 = strip * Cl::SBLK + lg * Cl::NB;
+          const int px0 = blk0 * Cl::Q;
+          if (blk0 * Cl::P >= jd.OW) continue;  // inactive lane: loads only
+          // element e of the thread (pixel px0 - LH + e/C) sits at window element px*C + c - xw
+          const int el0 = (px0 - Cl::LH) * Cl::C - G.xw;
+          if (el0 * Cl::SZ != first + Cl::HB * Cl::VB - Cl::LH * Cl::C * Cl::SZ) return fail("chunk not at its pixels", lg, el0);
+          for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
+            if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lg, px);
+            if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lg, px);
+          }
+          if (lg * Cl::NOUT + Cl::NOUT > Cl::SOE) return fail("ring write", lg, Cl::SOE);
         }
-        if (lg * Cl::NOUT + Cl::NOUT > Cl::SOE) return fail("ring write", lg, Cl::SOE);
       }
-      std::vector<int> owner(Cl::RING, -1);
+      // ring rule: the V pass of stage k may read only rows the H pass wrote in
+      // stages k-D..k (the H pass of stage k+kNRS-D overwrites stage k-D)
       std::vector<int> done(G.nblk, 0);
-      auto h_rows = [&](int k, std::vector<int>& rels) {
-        rels.clear();
-        for (int i = 0; i < Cl::SR; ++i) {
-          const int rel = k * Cl::SR + i, y = G.ys + rel;
-          if (y < 0 || y >= jd.H || rel >= G.rows) continue;
-          rels.push_back(rel);
-        }
-      };
-      std::vector<int> cur, nxt;
       for (int k = 0; k < G.nst; ++k) {
-        h_rows(k, cur);
-        for (int rel : cur) owner[rel % Cl::RING] = rel;
-        h_rows(k + 1, nxt);
         int m_lo, m_hi;
         ready_blocks<Cl>(G, k, m_lo, m_hi);
         for (int m = m_lo; m <= m_hi; ++m) {
@@ -957,9 +1030,9 @@ std::string check_class(const JobDesc& jd) {
             yc = yc < 0 ? 0 : (yc > jd.H - 1 ? jd.H - 1 : yc);
             const int rel = yc - G.ys;
             if (rel < 0 || rel >= G.rows) return fail("V row outside the tile", rel, G.rows);
-            if (owner[rel % Cl::RING] != rel) return fail("V row not in the ring", rel, k);
-            for (int rn : nxt)
-              if (rn % Cl::RING == rel % Cl::RING) return fail("V row overwritten by the next stage", rel, rn);
+            const int st = rel / Cl::SR;
+            if (st > k) return fail("V row not yet written", rel, k);
+            if (k - st > Cl::D) return fail("V row older than the ring keeps", rel, k);
           }
           const int ncols = std::min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
           for (int j = 0; j < Cl::P; ++j) {

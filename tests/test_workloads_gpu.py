@@ -1,0 +1,105 @@
+"""Full-size workloads on the GPU, in the launch configuration the benchmark
+uses (one batched launch over all frames of the workload), checked against
+the CPU oracle on every frame (fp32 batch) or on a seeded sample of frames
+that always includes the first and the last (the large uint8 / fp16 batches).
+"""
+import numpy as np
+import pytest
+
+import paper_1103_4881_b300 as ds
+from paper_1103_4881_b300 import synth
+from tests.gpu_util import assert_parity, finish, oracle_out, out_buffer, stream
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_workload(w, graph=False):
+    import torch
+
+    pl = ds.ds_plan_create(w.height, w.width, w.ratio, w.taps, w.dtype)
+    x = synth.frames(w)
+    xd = torch.from_numpy(x).cuda()
+    out = out_buffer(pl, w.frames)
+    if graph:
+        g = ds.ds_graph_create([(pl, xd.data_ptr(), out.data_ptr(), w.frames)])
+        try:
+            ds.ds_graph_launch(g, stream())
+            finish()
+        finally:
+            ds.ds_graph_destroy(g)
+    else:
+        ds.ds_run_frames(pl, xd.data_ptr(), out.data_ptr(), w.frames, stream())
+        finish()
+    return pl, x, xd, out
+
+
+def _sample(w, k, seed):
+    rng = np.random.default_rng(seed)
+    mid = rng.choice(np.arange(1, w.frames - 1), size=min(k, w.frames - 2), replace=False)
+    return sorted({0, w.frames - 1, *mid.tolist()})
+
+
+def test_plain_480x640_f32(oracle):
+    w = synth.WORKLOADS["plain_480x640_f32"]
+    pl, x, xd, out = _run_workload(w)
+    try:
+        want = oracle_out(oracle, x, w.ratio[0], w.ratio[1], w.taps, w.dtype)
+        assert out.shape == (1, 180, 240)
+        err = assert_parity(out.cpu().numpy(), want, w.dtype, w.name)
+        print("%s max |err| = %.3g" % (w.name, err))
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_batch64_1080x1920_f32_all_frames(oracle):
+    import torch
+
+    w = synth.WORKLOADS["batch64_1080x1920_f32"]
+    pl, x, xd, out = _run_workload(w, graph=True)
+    try:
+        got = out.cpu().numpy()
+        want = oracle_out(oracle, x, w.ratio[0], w.ratio[1], w.taps, w.dtype)
+        err = assert_parity(got, want, w.dtype, w.name)
+        print("%s max |err| = %.3g over %d frames" % (w.name, err, w.frames))
+        # plain per-frame launches and the unfused form give the same bits
+        fin, fout = ds.ds_plan_frame_bytes(pl)
+        o2 = torch.zeros_like(out)
+        for i in (0, 17, 63):
+            ds.ds_run(pl, xd.data_ptr() + i * fin, o2.data_ptr() + i * fout, stream())
+        nb = ds.ds_plan_workspace_bytes(pl) * w.frames
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        o3 = torch.zeros_like(out)
+        ds.ds_run_unfused(pl, xd.data_ptr(), o3.data_ptr(), w.frames, ws.data_ptr(), nb, stream())
+        finish()
+        for i in (0, 17, 63):
+            np.testing.assert_array_equal(o2[i].cpu().numpy(), got[i])
+        np.testing.assert_array_equal(o3.cpu().numpy(), got)
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_rgb300_1080x1920_u8_sampled(oracle):
+    w = synth.WORKLOADS["rgb300_1080x1920_u8"]
+    pl, x, xd, out = _run_workload(w)
+    try:
+        idx = _sample(w, 10, 3)
+        got = out[idx].cpu().numpy()
+        want = oracle_out(oracle, x[idx], w.ratio[0], w.ratio[1], w.taps, w.dtype)
+        assert_parity(got, want, w.dtype, w.name)
+        assert got.shape[1:] == (540, 960, 3)
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_uhd128_2160x3840_f16_sampled(oracle):
+    w = synth.WORKLOADS["uhd128_2160x3840_f16"]
+    pl, x, xd, out = _run_workload(w)
+    try:
+        idx = _sample(w, 6, 4)
+        got = out[idx].cpu().numpy()
+        want = oracle_out(oracle, x[idx], w.ratio[0], w.ratio[1], w.taps, w.dtype)
+        err = assert_parity(got, want, w.dtype, w.name)
+        print("%s max |err| = %.3g on frames %s" % (w.name, err, idx))
+        assert got.shape[1:] == (810, 1440)
+    finally:
+        ds.ds_destroy(pl)
