@@ -132,6 +132,12 @@ struct Cls {
   static constexpr int HA = cdiv(RH * C * SZ, VB);   // ... and after it
   static constexpr int NVT = HB + NV + HA;           // vectors per thread and row
   static constexpr int NWT = NVT * VB / 4;           // words per thread and row
+  // With 16-byte vectors and a 32-byte lane stride, the lanes of one
+  // 8-lane shared-memory phase cover only half the 16-byte bank groups for a
+  // fixed vector index (2-way conflicts).  Lanes 4-7 of each phase then load
+  // their 4 vectors in the order 1,2,3,0, which makes every phase hit 8
+  // distinct bank groups; the vectors are put back in order with selects.
+  static constexpr bool ROT = (VB == 16 && EB == 32 && NVT == 4);
   static constexpr int NOUT = NB * P * C;             // H outputs per thread and row
   __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
   static_assert(EB % 4 == 0, "a thread's chunk must be whole words");
@@ -327,18 +333,24 @@ __device__ __forceinline__ float smem_elem(const uint8_t* p) { return px_to_f(*r
 
 // Per-thread shared-memory offsets (row 0 of a stage) of the vectors the H
 // pass loads: HB halo vectors, the thread's own NV vectors, HA halo vectors,
-// consecutive in the window.  They depend only on the lane: computed once.
+// consecutive in the window, in the (possibly rotated) order they are loaded.
+// They depend only on the lane: computed once.
 template <class Cl>
 struct Offs {
   int v[Cl::NVT];
+  bool rot;
 };
 
 template <class Cl>
 __device__ __forceinline__ Offs<Cl> thread_offs(int lg) {
   Offs<Cl> o;
   const int first = Cl::HLB + lg * Cl::EB - Cl::HB * Cl::VB;
+  o.rot = Cl::ROT && ((lg >> 2) & 1);
 #pragma unroll
-  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = win_off<Cl>(first + v * Cl::VB);
+  for (int v = 0; v < Cl::NVT; ++v) {
+    const int pv = o.rot ? (v + 1) % Cl::NVT : v;
+    o.v[v] = win_off<Cl>(first + pv * Cl::VB);
+  }
   return o;
 }
 
@@ -346,17 +358,29 @@ __device__ __forceinline__ Offs<Cl> thread_offs(int lg) {
 template <class Cl>
 __device__ __forceinline__ void load_row(const uint8_t* rowbase, const Offs<Cl>& o, uint32_t* w) {
   constexpr int WPV = Cl::VB / 4;
+  if constexpr (Cl::ROT) {
+    uint4 r[4];
 #pragma unroll
-  for (int v = 0; v < Cl::NVT; ++v) {
-    const uint8_t* p = rowbase + o.v[v];
-    if constexpr (Cl::VB == 16) {
-      const uint4 x = *reinterpret_cast<const uint4*>(p);
-      w[v * WPV] = x.x; w[v * WPV + 1] = x.y; w[v * WPV + 2] = x.z; w[v * WPV + 3] = x.w;
-    } else if constexpr (Cl::VB == 8) {
-      const uint2 x = *reinterpret_cast<const uint2*>(p);
-      w[v * WPV] = x.x; w[v * WPV + 1] = x.y;
-    } else {
-      w[v] = *reinterpret_cast<const uint32_t*>(p);
+    for (int v = 0; v < 4; ++v) r[v] = *reinterpret_cast<const uint4*>(rowbase + o.v[v]);
+    // r[v] holds vector (v + rot) mod 4
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const uint4 x = o.rot ? r[(v + 3) & 3] : r[v];
+      w[v * 4] = x.x; w[v * 4 + 1] = x.y; w[v * 4 + 2] = x.z; w[v * 4 + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < Cl::NVT; ++v) {
+      const uint8_t* p = rowbase + o.v[v];
+      if constexpr (Cl::VB == 16) {
+        const uint4 x = *reinterpret_cast<const uint4*>(p);
+        w[v * WPV] = x.x; w[v * WPV + 1] = x.y; w[v * WPV + 2] = x.z; w[v * WPV + 3] = x.w;
+      } else if constexpr (Cl::VB == 8) {
+        const uint2 x = *reinterpret_cast<const uint2*>(p);
+        w[v * WPV] = x.x; w[v * WPV + 1] = x.y;
+      } else {
+        w[v] = *reinterpret_cast<const uint32_t*>(p);
+      }
     }
   }
 }
@@ -444,16 +468,14 @@ __device__ __forceinline__ void ring_store(typename Cl::R* dst, const float* o) 
 
 // Horizontal pass of one window row whose words the thread has loaded (see
 // load_row): NB packets of Q pixels per thread, each giving P outputs per
-// channel, stored to the thread's slice of a ring row.
+// channel, pass-rounded, in o[(n*P + j)*C + c].
 template <class Cl>
-__device__ __forceinline__ void hrow(const uint32_t* w, const float* __restrict__ taps,
-                                     typename Cl::R* __restrict__ dst) {
+__device__ __forceinline__ void hcompute(const uint32_t* w, const float* __restrict__ taps, float* o) {
   using T = typename Cl::T;
   float x[Cl::NX];
   constexpr int first = Cl::HB * Cl::VB - Cl::LH * Cl::C * Cl::SZ;  // byte of the first halo element in w
 #pragma unroll
   for (int e = 0; e < Cl::NX; ++e) x[e] = word_elem<T>(w, first + e * Cl::SZ);
-  float o[Cl::NOUT];
 #pragma unroll
   for (int n = 0; n < Cl::NB; ++n) {
 #pragma unroll
@@ -468,6 +490,14 @@ __device__ __forceinline__ void hrow(const uint32_t* w, const float* __restrict_
       }
     }
   }
+}
+
+// ... and stored to the thread's slice of a ring row.
+template <class Cl>
+__device__ __forceinline__ void hrow(const uint32_t* w, const float* __restrict__ taps,
+                                     typename Cl::R* __restrict__ dst) {
+  float o[Cl::NOUT];
+  hcompute<Cl>(w, taps, o);
   ring_store<Cl>(dst, o);
 }
 
@@ -608,9 +638,11 @@ __device__ bool h_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl,
   R* const ring_mine = ring + lg * Cl::NOUT;
   for (int k = 0; k < G.nst; ++k, ++g) {
     const uint32_t slot = g % NSTAGE;
-    bool ok = mbar_wait(&full[slot], (g / NSTAGE) & 1u, abort_flag);
+    // wait results are made warp-uniform, so a timeout takes the whole warp out
+    bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (g / NSTAGE) & 1u, abort_flag));
     const int dep = (class_changed && k == 0) ? (int)g - 1 : (int)g - kNRS + Cl::D;
-    if (ok && dep >= 0) ok = mbar_wait(&vdone[dep % kNRS], (uint32_t)(dep / kNRS) & 1u, abort_flag);
+    if (ok && dep >= 0)
+      ok = __all_sync(0xffffffffu, mbar_wait(&vdone[dep % kNRS], (uint32_t)(dep / kNRS) & 1u, abort_flag));
     if (!ok) return false;
     uint8_t* stage = stages + slot * STAGE_MAX;
     // the warp's rows of this stage: border fix-ups, then all loads, then the
@@ -658,7 +690,7 @@ __device__ bool v_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl,
   T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)G.ox0 * Cl::C;
   const int rbase = (int)((g * Cl::SR) & Cl::RING_MASK);  // ring row of the tile's first row
   for (int k = 0; k < G.nst; ++k, ++g) {
-    if (!mbar_wait(&hdone[g % kNRS], (g / kNRS) & 1u, abort_flag)) return false;
+    if (!__all_sync(0xffffffffu, mbar_wait(&hdone[g % kNRS], (g / kNRS) & 1u, abort_flag))) return false;
     int m_lo, m_hi;
     ready_blocks<Cl>(G, k, m_lo, m_hi);
     // one (block, phase) pair per warp at a time, so the phase -- and with it
@@ -794,6 +826,289 @@ __global__ void __launch_bounds__(kThreads, MINB) k_fused_tma(const __grid_const
 }
 
 // ---------------------------------------------------------------------------
+// row-streaming kernel: one self-contained pipeline per warp
+// ---------------------------------------------------------------------------
+// Each warp owns a tile (a strip of 32*NB packets x a band of output row
+// blocks of one frame) and runs the whole filter on it by itself:
+//   lane 0 issues TMA loads of SR input rows (plus the strip's halo) into the
+//   warp's private ring of NST stages, each stage with its own mbarrier;
+//   every input row goes through the horizontal pass in registers and lands
+//   in a sliding window of the last L filtered rows, also in registers
+//   (L rows x NOUT values per lane: the intermediate never leaves the SM);
+//   each time Q new rows have entered the window, the warp computes the P
+//   output rows of one block from the window and stores them.
+// Rows above / below the frame are never loaded: their window slots take a
+// copy of the first / last filtered row (clamp-to-edge); columns outside the
+// frame are fixed up in shared memory as in the other kernel.  Warps
+// synchronise with nothing but their own TMA completions.
+__host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
+template <class B, int SR_, int NST_>
+struct RCls : B {
+  static constexpr int SRR = SR_;                          // input rows per stage
+  static constexpr int NST = NST_;                         // stages per warp
+  static constexpr int BOXSTR = rup(SR_ * B::BOXB, 128);   // (hides the base's stage layout)
+  static constexpr int RSTAGE = B::NBOX * BOXSTR;
+  static constexpr int RTX = B::NBOX * SR_ * B::BOXB;      // TMA bytes per stage
+  static constexpr int WARP_BYTES = NST_ * RSTAGE;
+  static constexpr bool ROT = false;                       // bank rotation off: the selects cost more here
+  // The stream of a tile is cut so that the window prologue (the first L-Q
+  // pattern rows) fills whole stages, EXTRA rows being loaded before the first
+  // pattern row; after it, every group of U = lcm(SR, Q) rows is USTG stages
+  // and UBLK block steps, so each row's stage offset and window slot are
+  // compile-time constants.
+  static constexpr int PRE = B::L - B::Q;
+  static constexpr int NPS = cdiv(PRE, SR_);
+  static constexpr int EXTRA = NPS * SR_ - PRE;
+  static constexpr int U = SR_ / cgcd(SR_, B::Q) * B::Q;
+  static constexpr int USTG = U / SR_;
+  static constexpr int UBLK = U / B::Q;
+  static_assert(B::WX == 1, "one warp per strip");
+  static_assert(PRE > B::LH, "the window prologue must reach frame row 0");
+  static_assert(B::L * B::NOUT <= 48, "register window too large");
+  static_assert(U <= 16, "iteration unit too long to unroll");
+};
+
+//                 base class   SR NST
+using RF32_38 = RCls<CF32_38, 4, 3>;
+using RF32_12 = RCls<CF32_12, 4, 3>;
+using RF32_23 = RCls<CF32_23, 6, 3>;
+using RF16_38 = RCls<CF16_38, 4, 3>;
+using RF16_12 = RCls<CF16_12, 4, 3>;
+using RF16_23 = RCls<CF16_23, 6, 3>;
+using CU8_12w = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 2, 1, 8, 4>;
+using RU8_12 = RCls<CU8_12w, 4, 3>;
+
+// Store n_valid (<= N) consecutive output values with the widest aligned stores.
+template <typename T, int N>
+__device__ __forceinline__ void store_run(T* o, const float* v, int n_valid) {
+  constexpr int BYTES = N * (int)sizeof(T);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(o);
+  if (n_valid >= N) {
+    if constexpr (sizeof(T) == 4) {
+      if constexpr (BYTES % 16 == 0) {
+        if ((a & 15) == 0) {
+#pragma unroll
+          for (int i = 0; i < N / 4; ++i)
+            reinterpret_cast<float4*>(o)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+          return;
+        }
+      }
+      if constexpr (BYTES % 8 == 0) {
+        if ((a & 7) == 0) {
+#pragma unroll
+          for (int i = 0; i < N / 2; ++i) reinterpret_cast<float2*>(o)[i] = make_float2(v[2 * i], v[2 * i + 1]);
+          return;
+        }
+      }
+    } else if constexpr (sizeof(T) == 2) {
+      if constexpr (N % 2 == 0) {
+        if ((a & 3) == 0) {
+#pragma unroll
+          for (int i = 0; i < N / 2; ++i) reinterpret_cast<__half2*>(o)[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
+          return;
+        }
+      }
+    } else {
+      if constexpr (N % 2 == 0) {
+        if ((a & 1) == 0) {
+#pragma unroll
+          for (int i = 0; i < N / 2; ++i)
+            reinterpret_cast<unsigned short*>(o)[i] =
+                (unsigned short)((uint32_t)f_to_px<T>(v[2 * i]) | ((uint32_t)f_to_px<T>(v[2 * i + 1]) << 8));
+          return;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+    if (i < n_valid) o[i] = f_to_px<T>(v[i]);
+}
+
+template <class Cl, int WPC, int MINB>
+__global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__ FastParams prm) {
+  using T = typename Cl::T;
+  constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P, K = Cl::K, NOUT = Cl::NOUT, SR = Cl::SRR, NST = Cl::NST;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* const ring = smem + warp * Cl::WARP_BYTES;
+  uint64_t* const full = reinterpret_cast<uint64_t*>(smem + WPC * Cl::WARP_BYTES) + warp * NST;
+  if (lane == 0) {
+    for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncwarp();
+  const float* taps = prm.taps[Cl::id];
+  const Offs<Cl> of = thread_offs<Cl>(lane);
+  const int gw = blockIdx.x * WPC + warp, nw = gridDim.x * WPC;
+  uint32_t g = 0;       // this warp's stage counter over all its tiles (mbarrier phases)
+  uint32_t issued = 0;  // one past the last stage issued
+  bool ok = true;
+  for (int t = gw; ok && t < prm.total_tiles; t += nw) {
+    const Tile tl = decode_tile(prm, t);
+    const JobDesc& jd = prm.jobs[tl.job];
+    if (jd.cls != Cl::id) {
+      ok = false;
+      break;
+    }
+    const int H = jd.H;
+    const int nby = (jd.OH + P - 1) / P;
+    const int rb0 = tl.chunk * jd.rbc;
+    const int nblk = min(jd.rbc, nby - rb0);
+    const int ys = rb0 * Q + Cl::BMIN;  // first pattern row; < 0 only for the top band (then == BMIN)
+    const int nst = Cl::NPS + (nblk * Q + SR - 1) / SR;
+    const int ystream = ys - Cl::EXTRA;  // frame row of stage 0's first row
+    const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
+    const EdgeFix fix = edge_fix<Cl>(tl.strip, 0, jd.W);
+    const bool fixing = fix.nl + fix.nr > 0;
+    const int blk0 = tl.strip * Cl::SBLK + lane * Cl::NB;
+    const bool active = blk0 * P < jd.OW;
+    const int n_valid = jd.OW * Cl::C - blk0 * P * Cl::C;
+    T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)blk0 * P * Cl::C;
+    const long long rowe = (long long)jd.OW * Cl::C;
+
+    auto issue = [&](int s) {  // stage s of the tile into slot (g + s) mod NST
+      const uint32_t G = g + (uint32_t)s, slot = G % NST;
+      mbar_expect_tx(&full[slot], Cl::RTX);
+#pragma unroll
+      for (int bx = 0; bx < Cl::NBOX; ++bx)
+        tma_load_3d(ring + slot * Cl::RSTAGE + bx * Cl::BOXSTR, &jd.tmap, &full[slot], xw + bx * Cl::BOXE,
+                    ystream + s * SR, tl.frame);
+    };
+    if (lane == 0)
+      for (int s = 0; s < NST && s < nst; ++s) issue(s);
+    issued = g + (uint32_t)min(NST, nst);
+    // wait for stage s; returns the stage's row-0 base, or nullptr on timeout
+    auto stage_wait = [&](int s) -> uint8_t* {
+      const uint32_t G = g + (uint32_t)s, slot = G % NST;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (G / NST) & 1u, nullptr))) return nullptr;
+      return ring + slot * Cl::RSTAGE;
+    };
+    // stage s fully read: refill its slot with stage s + NST
+    auto stage_release = [&](int s) {
+      __syncwarp();
+      if (s + NST < nst) {
+        if (lane == 0) issue(s + NST);
+        issued = g + (uint32_t)(s + NST + 1);
+      }
+    };
+    // H pass of one loaded row into o[0..NOUT)
+    auto hrow_regs = [&](uint8_t* rowbase, float* o) {
+      if (fixing) apply_edge_fix<Cl>(rowbase, fix, lane, jd.W, xw);
+      uint32_t w[Cl::NWT];
+      load_row<Cl>(rowbase, of, w);
+      if (active) hcompute<Cl>(w, taps, o);
+    };
+
+    float win[L][NOUT];
+    // ---- prologue: pattern rows 0 .. L-Q-1
+#pragma unroll
+    for (int ps = 0; ps < Cl::NPS; ++ps) {
+      uint8_t* sb = stage_wait(ps);
+      if (!sb) {
+        ok = false;
+        break;
+      }
+#pragma unroll
+      for (int r = 0; r < SR; ++r) {
+        const int i = ps * SR + r - Cl::EXTRA;  // pattern row index
+        if (i < 0) continue;                    // loaded only to align the stages
+        const int y = ys + i;
+        if (y < 0) continue;                    // top band: filled from frame row 0 below
+        if (i > 0 && y >= H) {
+#pragma unroll
+          for (int k = 0; k < NOUT; ++k) win[i][k] = win[i - 1][k];
+        } else {
+          hrow_regs(sb + r * Cl::BOXB, win[i]);
+        }
+      }
+      stage_release(ps);
+    }
+    if (!ok) break;
+    if (ys < 0) {  // ys == BMIN: slots 0..LH-1 are frame row 0, held in slot LH
+#pragma unroll
+      for (int i = 0; i < Cl::LH; ++i)
+#pragma unroll
+        for (int k = 0; k < NOUT; ++k) win[i][k] = win[Cl::LH][k];
+    }
+    // ---- block steps, U rows (USTG stages, UBLK blocks) at a time
+    const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
+    for (int u = 0; ok && u < nunits; ++u) {
+#pragma unroll
+      for (int st = 0; st < Cl::USTG; ++st) {
+        const int s = Cl::NPS + u * Cl::USTG + st;
+        if (s >= nst) break;
+        uint8_t* sb = stage_wait(s);
+        if (!sb) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int r = 0; r < SR; ++r) {
+          constexpr int dummy = 0;
+          (void)dummy;
+          const int ru = st * SR + r;       // row within the unit
+          const int bq = ru / Q, q = ru - bq * Q;
+          const int m = u * Cl::UBLK + bq;  // block step
+          if (m < nblk) {
+            const int i = L - Q + q;
+            const int y = ys + m * Q + i;
+            if (y >= H) {
+#pragma unroll
+              for (int k = 0; k < NOUT; ++k) win[i][k] = win[i - 1][k];
+            } else {
+              hrow_regs(sb + r * Cl::BOXB, win[i]);
+            }
+            if (q == Q - 1) {
+              // the window holds block m's pattern: its P output rows
+              if (active) {
+                const int rr = rb0 + m;
+#pragma unroll
+                for (int jv = 0; jv < P; ++jv) {
+                  const int oy = rr * P + jv;
+                  if (oy < jd.OH) {
+                    float acc[NOUT];
+#pragma unroll
+                    for (int k = 0; k < NOUT; ++k) acc[k] = 0.0f;
+#pragma unroll
+                    for (int tt = 0; tt < K; ++tt) {
+                      const float wt = taps[jv * K + tt];
+#pragma unroll
+                      for (int k = 0; k < NOUT; ++k) acc[k] = fmaf(wt, win[Cl::b(jv) - Cl::BMIN + tt][k], acc[k]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < NOUT; ++k) acc[k] = pass_round<T>(acc[k]);
+                    store_run<T, NOUT>(obase + (long long)oy * rowe, acc, n_valid);
+                  }
+                }
+              }
+#pragma unroll
+              for (int i2 = 0; i2 < L - Q; ++i2)
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) win[i2][k] = win[i2 + Q][k];
+            }
+          }
+        }
+        stage_release(s);
+      }
+    }
+    g += (uint32_t)nst;
+  }
+  if (!ok) {
+    // a wait gave up (or a job of the wrong class): record it and leave no
+    // copy in flight
+    if (lane == 0) {
+      atomicCAS(&g_fast_status, 0, kStatusTimeout);
+      for (uint32_t G = (issued > (uint32_t)NST ? issued - NST : 0); G < issued; ++G)
+        mbar_wait(&full[G % NST], (G / NST) & 1u, nullptr);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct HostGeom {
@@ -805,17 +1120,34 @@ template <class Cl>
 HostGeom host_geom() {
   return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::BOXE, Cl::SR, Cl::SZ, Cl::C, Cl::VE, TmaType<typename Cl::T>::v};
 }
+template <class Cl>
+HostGeom host_geom_rows() {
+  HostGeom g = host_geom<Cl>();
+  g.sr = Cl::SRR;
+  return g;
+}
 
+// Classes with a row-streaming kernel (their register window fits).
+bool has_rows_kernel(int cls) {
+  switch (cls) {
+    case kFcF32_38: case kFcF32_12: case kFcF32_23:
+    case kFcF16_38: case kFcF16_12: case kFcF16_23:
+    case kFcU8C3_12: return true;
+    default: return false;
+  }
+}
+
+// Geometry of the kernel that runs class `cls`.
 HostGeom geom_of(int cls) {
   switch (cls) {
-    case kFcF32_38: return host_geom<CF32_38>();
-    case kFcF32_12: return host_geom<CF32_12>();
-    case kFcF32_23: return host_geom<CF32_23>();
-    case kFcF16_38: return host_geom<CF16_38>();
-    case kFcF16_12: return host_geom<CF16_12>();
-    case kFcF16_23: return host_geom<CF16_23>();
+    case kFcF32_38: return host_geom_rows<RF32_38>();
+    case kFcF32_12: return host_geom_rows<RF32_12>();
+    case kFcF32_23: return host_geom_rows<RF32_23>();
+    case kFcF16_38: return host_geom_rows<RF16_38>();
+    case kFcF16_12: return host_geom_rows<RF16_12>();
+    case kFcF16_23: return host_geom_rows<RF16_23>();
     case kFcU8C3_38: return host_geom<CU8_38>();
-    case kFcU8C3_12: return host_geom<CU8_12>();
+    case kFcU8C3_12: return host_geom_rows<RU8_12>();
     default: return host_geom<CU8_23>();
   }
 }
@@ -836,28 +1168,36 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 struct KernelInfo {
   const void* fn;
   int smem;
+  int threads;
 };
 
 template <int NSTAGE, class... Cs>
 KernelInfo kernel_info() {
   constexpr int minb = sizeof...(Cs) == 1 ? 2 : 1;
-  return KernelInfo{reinterpret_cast<const void*>(&k_fused_tma<NSTAGE, minb, Cs...>), KernelShape<NSTAGE, Cs...>::SMEM};
+  return KernelInfo{reinterpret_cast<const void*>(&k_fused_tma<NSTAGE, minb, Cs...>), KernelShape<NSTAGE, Cs...>::SMEM,
+                    kThreads};
 }
 
-// single-class kernels (uniform batches) and the all-class kernel (mixes)
+constexpr int kRowsWPC = 4;  // warps (independent pipelines) per CTA of the row-streaming kernel
+
+template <class Cl>
+KernelInfo rows_info() {
+  constexpr int smem = 128 + kRowsWPC * (Cl::WARP_BYTES + Cl::NST * 8);
+  return KernelInfo{reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, 1>), smem, kRowsWPC * 32};
+}
+
+// The kernel that runs class `cls` (all jobs of a launch share the class).
 KernelInfo kernel_for(int cls) {
   switch (cls) {
-    case kFcF32_38: return kernel_info<4, CF32_38>();
-    case kFcF32_12: return kernel_info<4, CF32_12>();
-    case kFcF32_23: return kernel_info<4, CF32_23>();
-    case kFcF16_38: return kernel_info<6, CF16_38>();
-    case kFcF16_12: return kernel_info<6, CF16_12>();
-    case kFcF16_23: return kernel_info<6, CF16_23>();
+    case kFcF32_38: return rows_info<RF32_38>();
+    case kFcF32_12: return rows_info<RF32_12>();
+    case kFcF32_23: return rows_info<RF32_23>();
+    case kFcF16_38: return rows_info<RF16_38>();
+    case kFcF16_12: return rows_info<RF16_12>();
+    case kFcF16_23: return rows_info<RF16_23>();
     case kFcU8C3_38: return kernel_info<8, CU8_38>();
-    case kFcU8C3_12: return kernel_info<8, CU8_12>();
-    case kFcU8C3_23: return kernel_info<4, CU8_23>();
-    default:
-      return kernel_info<3, CF32_38, CF32_12, CF32_23, CF16_38, CF16_12, CF16_23, CU8_38, CU8_12, CU8_23>();
+    case kFcU8C3_12: return rows_info<RU8_12>();
+    default: return kernel_info<4, CU8_23>();
   }
 }
 
@@ -870,7 +1210,7 @@ int ctas_per_sm(const KernelInfo& ki) {
     if (e.first == ki.fn) return e.second;
   int occ = 0;
   if (cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki.fn, kThreads, ki.smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki.fn, ki.threads, ki.smem) != cudaSuccess) return 0;
   cache.emplace_back(ki.fn, occ);
   return occ;
 }
@@ -1051,6 +1391,131 @@ std::string check_class(const JobDesc& jd) {
   return std::string();
 }
 
+// Host-side walk of the row-streaming kernel: the same TMA / window / edge
+// checks as above, plus a replay of its stream and register-window logic on
+// frame-row indices -- every V block must see exactly the clamped rows of
+// its window, every stream row must be the next frame row in order, every
+// output element is written once.
+template <class Cl, int WPC>
+std::string check_rows(const JobDesc& jd) {
+  char buf[256];
+  auto fail = [&](const char* what, int a, int b) {
+    std::snprintf(buf, sizeof(buf), "rows class %d: %s (%d, %d)", Cl::id, what, a, b);
+    return std::string(buf);
+  };
+  constexpr int smem = 128 + WPC * (Cl::WARP_BYTES + Cl::NST * 8);
+  if (smem > 227 * 1024) return fail("shared memory above 227 KB", smem, 0);
+  if (Cl::BOXSTR < Cl::SRR * Cl::BOXB) return fail("stage layout", Cl::BOXSTR, 0);
+  const int win = Cl::NBOX * Cl::BOXB;
+  constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P;
+  std::vector<int> written((size_t)jd.OH * jd.OW * Cl::C, 0);
+  const int nby = (jd.OH + P - 1) / P;
+  for (int chunk = 0; chunk < jd.chunks; ++chunk) {
+    for (int strip = 0; strip < jd.strips; ++strip) {
+      const int rb0 = chunk * jd.rbc;
+      const int nblk = std::min(jd.rbc, nby - rb0);
+      if (nblk < 1) return fail("empty tile", chunk, strip);
+      const int ys = rb0 * Q + Cl::BMIN;
+      const int ye = (rb0 + nblk - 1) * Q + Cl::BMIN + L;
+      const int y0 = std::max(ys, 0), nrow = std::min(ye, jd.H) - y0;
+      if (nrow < 1) return fail("empty stream", ys, ye);
+      if (ys < 0 && ys != Cl::BMIN) return fail("top band offset", ys, 0);
+      const int xw = strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
+      for (int bx = 0; bx < Cl::NBOX; ++bx) {
+        const long long xb = (long long)(xw + bx * Cl::BOXE) * Cl::SZ;
+        if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", xw, bx);
+      }
+      const EdgeFix fx = edge_fix<Cl>(strip, 0, jd.W);
+      for (int e = 0; e < fx.nl + fx.nr; ++e) {
+        const bool left = e < fx.nl;
+        const int k2 = left ? e : e - fx.nl;
+        const int px = (left ? fx.l_lo : fx.r_lo) + k2 / Cl::C, c = k2 % Cl::C;
+        const int src = (left ? 0 : jd.W - 1) * Cl::C + c - xw, dst = px * Cl::C + c - xw;
+        if (src < 0 || (src + 1) * Cl::SZ > win || dst < 0 || (dst + 1) * Cl::SZ > win)
+          return fail("edge fix outside the window", src, dst);
+      }
+      for (int lane = 0; lane < 32; ++lane) {
+        const int first = Cl::HLB + lane * Cl::EB - Cl::HB * Cl::VB;
+        for (int v = 0; v < Cl::NVT; ++v) {
+          const int b0 = first + v * Cl::VB;
+          if (b0 < 0 || b0 + Cl::VB > win || b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB)
+            return fail("vector read", lane, b0);
+        }
+        const int blk0 = strip * Cl::SBLK + lane * Cl::NB, px0 = blk0 * Cl::Q;
+        if (blk0 * P >= jd.OW) continue;
+        for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
+          if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lane, px);
+          if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lane, px);
+        }
+      }
+      // replay of the stream and window on frame-row indices: stage s holds
+      // frame rows ystream + s*SR .. + SR - 1
+      const int nst = Cl::NPS + (nblk * Q + Cl::SRR - 1) / Cl::SRR;
+      const int ystream = ys - Cl::EXTRA;
+      int wrow[64];
+      int sr = 0;  // rows consumed from the stream, checked against their position
+      auto take = [&](int s, int r, int i) -> std::string {
+        if (s >= nst) return fail("stage beyond the tile", s, nst);
+        wrow[i] = ystream + s * Cl::SRR + r;
+        ++sr;
+        return std::string();
+      };
+      for (int ps = 0; ps < Cl::NPS; ++ps)
+        for (int r = 0; r < Cl::SRR; ++r) {
+          const int i = ps * Cl::SRR + r - Cl::EXTRA;
+          if (i < 0) continue;
+          const int y = ys + i;
+          if (y < 0) continue;
+          if (i > 0 && y >= jd.H) { wrow[i] = wrow[i - 1]; continue; }
+          std::string e = take(ps, r, i);
+          if (!e.empty()) return e;
+          if (wrow[i] != y) return fail("prologue row mismatch", i, wrow[i]);
+        }
+      if (ys < 0)
+        for (int i = 0; i < Cl::LH; ++i) wrow[i] = wrow[Cl::LH];
+      const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
+      for (int u = 0; u < nunits; ++u)
+        for (int st = 0; st < Cl::USTG; ++st) {
+          const int s = Cl::NPS + u * Cl::USTG + st;
+          if (s >= nst) break;
+          for (int r = 0; r < Cl::SRR; ++r) {
+            const int ru = st * Cl::SRR + r, bq = ru / Q, q = ru - bq * Q, m = u * Cl::UBLK + bq;
+            if (m >= nblk) continue;
+            const int i = L - Q + q, y = ys + m * Q + i;
+            if (y >= jd.H) wrow[i] = wrow[i - 1];
+            else {
+              std::string e = take(s, r, i);
+              if (!e.empty()) return e;
+              if (wrow[i] != y) return fail("stream row mismatch", i, wrow[i]);
+            }
+            if (q != Q - 1) continue;
+            const int rr = rb0 + m;
+            for (int i2 = 0; i2 < L; ++i2) {
+              int want = rr * Q + Cl::BMIN + i2;
+              want = want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want);
+              if (wrow[i2] != want) return fail("window row mismatch", i2, wrow[i2]);
+            }
+            for (int lane = 0; lane < 32; ++lane) {
+              const int blk0 = strip * Cl::SBLK + lane * Cl::NB;
+              if (blk0 * P >= jd.OW) continue;
+              const int nv = std::min(Cl::NOUT, jd.OW * Cl::C - blk0 * P * Cl::C);
+              for (int jv = 0; jv < P; ++jv) {
+                const int oy = rr * P + jv;
+                if (oy >= jd.OH) continue;
+                for (int k = 0; k < nv; ++k) written[((size_t)oy * jd.OW) * Cl::C + (size_t)blk0 * P * Cl::C + k]++;
+              }
+            }
+            for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
+          }
+        }
+      if (sr != nrow) return fail("stream rows left over", sr, nrow);
+    }
+  }
+  for (size_t i = 0; i < written.size(); ++i)
+    if (written[i] != 1) return fail("output element written != 1 times", (int)i, written[i]);
+  return std::string();
+}
+
 template <int NSTAGE, class Cl>
 std::string check_single(const JobDesc& jd) {
   using KS = KernelShape<NSTAGE, Cl>;
@@ -1068,6 +1533,17 @@ std::string check_plan(const ds_plan* pl) {
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);
   std::string a, b;
+  if (has_rows_kernel(pl->fast_class)) {
+    switch (pl->fast_class) {
+      case kFcF32_38: return check_rows<RF32_38, kRowsWPC>(jd);
+      case kFcF32_12: return check_rows<RF32_12, kRowsWPC>(jd);
+      case kFcF32_23: return check_rows<RF32_23, kRowsWPC>(jd);
+      case kFcF16_38: return check_rows<RF16_38, kRowsWPC>(jd);
+      case kFcF16_12: return check_rows<RF16_12, kRowsWPC>(jd);
+      case kFcF16_23: return check_rows<RF16_23, kRowsWPC>(jd);
+      default: return check_rows<RU8_12, kRowsWPC>(jd);
+    }
+  }
   switch (pl->fast_class) {
     case kFcF32_38: a = check_single<4, CF32_38>(jd); b = check_mixed<CF32_38>(jd); break;
     case kFcF32_12: a = check_single<4, CF32_12>(jd); b = check_mixed<CF32_12>(jd); break;
@@ -1087,7 +1563,7 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   static thread_local FastParams prm;  // ~13 KB, too large for the stack of some callers
   std::memset(&prm, 0, sizeof(prm));
   fill_taps(prm);
-  int cls = jobs[0].plan->fast_class;
+  const int cls = jobs[0].plan->fast_class;  // launch_fast groups jobs by class
   int want_ctas = jobs[0].plan->ctas_per_sm;
   int tiles = 0;
   for (int i = 0; i < n; ++i) {
@@ -1095,7 +1571,6 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
     if (s != DS_OK) return s;
     prm.jobs[i].tile_begin = tiles;
     tiles += prm.jobs[i].tiles;
-    if (jobs[i].plan->fast_class != cls) cls = -1;
     want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
   }
   prm.n_jobs = n;
@@ -1108,9 +1583,11 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
     return DS_ERR_UNSUPPORTED;
   }
   if (want_ctas > 0) occ = std::min(occ, want_ctas);
-  const int grid = std::min(tiles, sm_count() * occ);
+  // the row-streaming kernel runs one tile per warp, the other one per CTA
+  const int per_cta = has_rows_kernel(cls) ? ki.threads / 32 : 1;
+  const int grid = std::min((tiles + per_cta - 1) / per_cta, sm_count() * occ);
   void* args[] = {&prm};
-  cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(kThreads), args, (size_t)ki.smem, st);
+  cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, (size_t)ki.smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "k_fused_tma launch");
   count_launches(1);
   return DS_OK;
@@ -1120,10 +1597,18 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
 
 int fast_max_jobs_per_launch() { return kMaxJobs; }
 
+// One launch per class present (each kernel is specialised for its class),
+// at most kMaxJobs descriptors per launch.
 ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
-  for (int i = 0; i < n; i += kMaxJobs) {
-    ds_status s = launch_chunk(jobs + i, std::min(kMaxJobs, n - i), st);
-    if (s != DS_OK) return s;
+  std::vector<FastJob> group;
+  for (int cls = 0; cls < kFcCount; ++cls) {
+    group.clear();
+    for (int i = 0; i < n; ++i)
+      if (jobs[i].plan->fast_class == cls) group.push_back(jobs[i]);
+    for (size_t i = 0; i < group.size(); i += kMaxJobs) {
+      ds_status s = launch_chunk(group.data() + i, (int)std::min<size_t>(kMaxJobs, group.size() - i), st);
+      if (s != DS_OK) return s;
+    }
   }
   return DS_OK;
 }

@@ -142,7 +142,7 @@ def test_batch_mixed_plans_equal_solo_runs(oracle):
         ds.ds_batch_run([(pl, i.data_ptr(), o.data_ptr(), 2) for pl, i, o in zip(plans, ins, outs)], stream())
         finish()
         launches = ds.ds_launch_count()
-        assert launches == 1 + 2  # one persistent launch + two general-kernel jobs
+        assert launches == 5 + 2  # one launch per fast class present + two general-kernel jobs
         for k, (o, s) in enumerate(zip(outs, solo)):
             np.testing.assert_array_equal(o.cpu().numpy(), s, err_msg="job %d" % k)
         # graph replay of the same batch
