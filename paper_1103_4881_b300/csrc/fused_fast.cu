@@ -33,6 +33,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -45,6 +46,14 @@
 namespace ds {
 
 __device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out; 2 = bad class
+
+// Dynamic tile scheduling of the row-streaming kernel: launch slot s hands out
+// tiles from g_tile_next[s]; the last warp to finish puts both counters of
+// its slot back to zero.  Launches take slots in turn, so launches that can
+// overlap (different streams) use different counters.
+constexpr int kSchedSlots = 1024;
+__device__ unsigned int g_tile_next[kSchedSlots];
+__device__ unsigned int g_warps_done[kSchedSlots];
 
 namespace {
 
@@ -181,6 +190,7 @@ struct FastParams {
   float taps[kFcCount][kMaxTaps];  // FP32 taps, or Q14 taps as floats for uint8
   int n_jobs;
   int total_tiles;
+  int sched_slot;                  // row kernel: dynamic scheduling slot
 };
 
 // ---------------------------------------------------------------------------
@@ -943,11 +953,17 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
   __syncwarp();
   const float* taps = prm.taps[Cl::id];
   const Offs<Cl> of = thread_offs<Cl>(lane);
-  const int gw = blockIdx.x * WPC + warp, nw = gridDim.x * WPC;
+  const unsigned nwarps = gridDim.x * WPC;
+  unsigned* const next = &g_tile_next[prm.sched_slot];
+  auto next_tile = [&]() -> int {
+    unsigned t = 0;
+    if (lane == 0) t = atomicAdd(next, 1u);
+    return (int)__shfl_sync(0xffffffffu, t, 0);
+  };
   uint32_t g = 0;       // this warp's stage counter over all its tiles (mbarrier phases)
   uint32_t issued = 0;  // one past the last stage issued
   bool ok = true;
-  for (int t = gw; ok && t < prm.total_tiles; t += nw) {
+  for (int t = next_tile(); ok && t < prm.total_tiles; t = next_tile()) {
     const Tile tl = decode_tile(prm, t);
     const JobDesc& jd = prm.jobs[tl.job];
     if (jd.cls != Cl::id) {
@@ -1104,6 +1120,15 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       atomicCAS(&g_fast_status, 0, kStatusTimeout);
       for (uint32_t G = (issued > (uint32_t)NST ? issued - NST : 0); G < issued; ++G)
         mbar_wait(&full[G % NST], (G / NST) & 1u, nullptr);
+    }
+  }
+  // the last warp out resets the slot for its next launch
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(&g_warps_done[prm.sched_slot], 1u) == nwarps - 1) {
+      g_tile_next[prm.sched_slot] = 0;
+      g_warps_done[prm.sched_slot] = 0;
+      __threadfence();
     }
   }
 }
@@ -1575,6 +1600,8 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   }
   prm.n_jobs = n;
   prm.total_tiles = tiles;
+  static std::atomic<unsigned> slot_counter{0};
+  prm.sched_slot = (int)(slot_counter.fetch_add(1) % kSchedSlots);
   if (tiles == 0) return DS_OK;
   const KernelInfo ki = kernel_for(cls);
   int occ = ctas_per_sm(ki);
@@ -1625,6 +1652,10 @@ ds_status read_device_status(int* status) {
   if (v != 0) {
     e = cudaMemcpyToSymbol(g_fast_status, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");
+    // a kernel that gave up may have left its scheduling slot unreset
+    static const unsigned zeros[kSchedSlots] = {};
+    cudaMemcpyToSymbol(g_tile_next, zeros, sizeof(zeros));
+    cudaMemcpyToSymbol(g_warps_done, zeros, sizeof(zeros));
   }
   *status = v;
   return DS_OK;
