@@ -172,6 +172,27 @@ ds_status ds_run_unfused(const ds_plan* plan, const void* in, void* out, int n_f
                          void* workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * The unfused form without caller workspace, for callers that cannot
+ * allocate device memory on the call path (a serving loop that must not stall
+ * on cudaMalloc, an application with a device memory budget fixed at start-up,
+ * a host program whose own allocator must own the device).  The paper has no
+ * counterpart; this is a deployment variant of ds_run_unfused.
+ * The intermediate lives in one fixed device array of
+ * ds_static_workspace_bytes() (32 MiB) per GPU, held until the process exits;
+ * the call allocates nothing.  DS_ERR_ARG when the plan's intermediate for
+ * n_frames frames (ds_plan_workspace_bytes * n_frames) exceeds it.
+ * The first call on a device looks up the array's device address (host
+ * set-up, no allocation): make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (every
+ * value a call reads it has written first); calls whose launches overlap on
+ * the GPU -- on different streams or from different host threads -- race on
+ * it and must be serialised by the caller.
+ */
+size_t ds_static_workspace_bytes(void);
+ds_status ds_run_unfused_static(const ds_plan* plan, const void* in, void* out, int n_frames,
+                                void* stream);
+
+/*
  * Synchronise `stream` and read the device status word that kernels set
  * when a bounded wait gives up; the word is cleared by the read.
  * DS_ERR_TIMEOUT if it was set, DS_ERR_CUDA on an asynchronous CUDA error.

@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "ds_run", "ds_run_frames", "ds_batch_run", "ds_plan_workspace_bytes", "ds_run_unfused",
     "ds_stream_check", "ds_debug_check_plan", "ds_graph_create", "ds_graph_launch", "ds_graph_destroy",
     "ds_pipeline_create", "ds_pipeline_run", "ds_pipeline_destroy", "ds_last_error", "ds_version",
-    "ds_launch_count",
+    "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static",
 )
 
 
@@ -90,6 +90,8 @@ def lib() -> ctypes.CDLL:
         "ds_last_error": (ctypes.c_char_p, []),
         "ds_version": (ctypes.c_char_p, []),
         "ds_launch_count": (ctypes.c_longlong, []),
+        "ds_static_workspace_bytes": (sz, []),
+        "ds_run_unfused_static": (i, [vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -219,6 +221,17 @@ def ds_run_unfused(plan: int, in_ptr: int, out_ptr: int, n_frames: int, workspac
 def ds_debug_check_plan(plan: int) -> None:
     """Host-only check of the fused kernel's index arithmetic for this plan."""
     _check(lib().ds_debug_check_plan(_ptr(plan)))
+
+
+def ds_static_workspace_bytes() -> int:
+    """Size of the fixed device array ds_run_unfused_static uses."""
+    return int(lib().ds_static_workspace_bytes())
+
+
+def ds_run_unfused_static(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: int = 0) -> None:
+    """Unfused form with its intermediate in the library's fixed device array:
+    for callers that cannot allocate device memory on the call path."""
+    _check(lib().ds_run_unfused_static(_ptr(plan), _ptr(in_ptr), _ptr(out_ptr), n_frames, _ptr(stream)))
 
 
 def ds_stream_check(stream: int = 0) -> None:
