@@ -1205,10 +1205,12 @@ KernelInfo kernel_info() {
 
 constexpr int kRowsWPC = 4;  // warps (independent pipelines) per CTA of the row-streaming kernel
 
+// Registers are budgeted for 4 resident CTAs (16 warps) per SM, which the
+// shared-memory footprint of the stage rings also allows.
 template <class Cl>
 KernelInfo rows_info() {
   constexpr int smem = 128 + kRowsWPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  return KernelInfo{reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, 1>), smem, kRowsWPC * 32};
+  return KernelInfo{reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, 4>), smem, kRowsWPC * 32};
 }
 
 // The kernel that runs class `cls` (all jobs of a launch share the class).
