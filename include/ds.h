@@ -125,6 +125,17 @@ ds_status ds_plan_describe(const ds_plan* plan, char* buf, size_t len);
 ds_status ds_plan_set_schedule(ds_plan* plan, int row_blocks, int ctas_per_sm);
 ds_status ds_plan_get_schedule(const ds_plan* plan, int* row_blocks, int* ctas_per_sm);
 
+/*
+ * Autotuner: time ds_run_frames(plan, in, out, n_frames) for each candidate
+ * band height (output row blocks per tile) with CUDA events on `stream`,
+ * `iters` launches each after one warm-up, and keep the fastest in the plan.
+ * Every candidate produces identical bits.  Synchronises the stream.  The
+ * chosen value and its time per launch (us) are returned if the pointers are
+ * not NULL.  DS_ERR_ARG on NULL pointers, n_frames < 1 or iters < 1.
+ */
+ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frames, void* stream,
+                           int iters, int* best_row_blocks, float* best_us);
+
 /* ---------------------------------------------------------------------- */
 /* Running                                                                  */
 /* ---------------------------------------------------------------------- */

@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "ds_run", "ds_run_frames", "ds_batch_run", "ds_plan_workspace_bytes", "ds_run_unfused",
     "ds_stream_check", "ds_debug_check_plan", "ds_graph_create", "ds_graph_launch", "ds_graph_destroy",
     "ds_pipeline_create", "ds_pipeline_run", "ds_pipeline_destroy", "ds_last_error", "ds_version",
-    "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static",
+    "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static", "ds_plan_autotune",
 )
 
 
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         "ds_version": (ctypes.c_char_p, []),
         "ds_launch_count": (ctypes.c_longlong, []),
         "ds_static_workspace_bytes": (sz, []),
+        "ds_plan_autotune": (i, [vp, vp, vp, i, vp, i, ip, ctypes.POINTER(ctypes.c_float)]),
         "ds_run_unfused_static": (i, [vp, vp, vp, i, vp]),
     }
     for name, (res, args) in sig.items():
@@ -180,6 +181,15 @@ def ds_plan_get_schedule(plan: int):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(lib().ds_plan_get_schedule(_ptr(plan), ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def ds_plan_autotune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: int = 0, iters: int = 10):
+    """Time the candidate tile bands on the given buffers, keep the fastest;
+    returns (row_blocks, us_per_launch)."""
+    rb, us = ctypes.c_int(), ctypes.c_float()
+    _check(lib().ds_plan_autotune(_ptr(plan), _ptr(in_ptr), _ptr(out_ptr), n_frames, _ptr(stream), iters,
+                                  ctypes.byref(rb), ctypes.byref(us)))
+    return rb.value, us.value
 
 
 # ---------------------------------------------------------------------- running
