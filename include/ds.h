@@ -120,6 +120,11 @@ ds_status ds_plan_describe(const ds_plan* plan, char* buf, size_t len);
  * from the task multiplicity, Sec. 3.B.1): row_blocks = output row blocks
  * per tile (each block is p output rows), ctas_per_sm = resident CTAs per SM
  * of the persistent grid (0 = as many as fit).  Used by the autotuner.
+ * A new plan has a per-class default band and no fixed schedule: a launch
+ * whose work would not fill the GPU's pipelines at that band (one frame, a
+ * small batch) then runs shorter bands.  After ds_plan_set_schedule (or
+ * ds_plan_autotune) every launch uses row_blocks as given.  The schedule
+ * never changes the results, only the time.
  * DS_ERR_ARG for row_blocks < 1 or ctas_per_sm < 0.
  */
 ds_status ds_plan_set_schedule(ds_plan* plan, int row_blocks, int ctas_per_sm);

@@ -185,9 +185,17 @@ struct JobDesc {
 };
 static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor layout");
 
+// Q14 taps of the uint8 classes as pairs of int16 for dp2a, [class - first
+// uint8 class][window-start parity][phase][pair]: for parity a, pair i holds
+// taps 2i - a (low half) and 2i + 1 - a (high half), zero outside 0..K-1, so
+// a window that starts on an odd slot is read from the even slot before it.
+constexpr int kU8Classes = 3;
+constexpr int kMaxPairs = 5;  // (K + 1) / 2 + 1 for K <= 8
+
 struct FastParams {
   JobDesc jobs[kMaxJobs];
   float taps[kFcCount][kMaxTaps];  // FP32 taps, or Q14 taps as floats for uint8
+  uint32_t tap2[kU8Classes][2][3][kMaxPairs];
   int n_jobs;
   int total_tiles;
   int sched_slot;                  // row kernel: dynamic scheduling slot
@@ -875,7 +883,8 @@ struct RCls : B {
   static constexpr int UBLK = U / B::Q;
   static_assert(B::WX == 1, "one warp per strip");
   static_assert(PRE > B::LH, "the window prologue must reach frame row 0");
-  static_assert(B::L * B::NOUT <= 48, "register window too large");
+  static_assert(B::L * (sizeof(typename B::T) == 1 ? (B::NOUT + 3) / 4 : B::NOUT) <= 48,
+                "register window too large");
   static_assert(U <= 16, "iteration unit too long to unroll");
 };
 
@@ -886,8 +895,13 @@ using RF32_23 = RCls<CF32_23, 6, 3>;
 using RF16_38 = RCls<CF16_38, 4, 3>;
 using RF16_12 = RCls<CF16_12, 4, 3>;
 using RF16_23 = RCls<CF16_23, 6, 3>;
-using CU8_12w = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 2, 1, 8, 4>;
-using RU8_12 = RCls<CU8_12w, 4, 3>;
+// uint8 RGB (integer row math): one warp per strip, chunks of whole words
+using CU8_38r = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 1, 8, 4>;
+using CU8_12r = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 1, 8, 4>;
+using CU8_23r = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 1, 8, 4>;
+using RU8_38 = RCls<CU8_38r, 4, 3>;
+using RU8_12 = RCls<CU8_12r, 4, 3>;
+using RU8_23 = RCls<CU8_23r, 3, 3>;
 
 // Store n_valid (<= N) consecutive output values with the widest aligned stores.
 template <typename T, int N>
@@ -936,10 +950,242 @@ __device__ __forceinline__ void store_run(T* o, const float* v, int n_valid) {
     if (i < n_valid) o[i] = f_to_px<T>(v[i]);
 }
 
+// ---------------------------------------------------------------------------
+// row math of the row-streaming kernel
+// ---------------------------------------------------------------------------
+// What one row of the register window holds, how the H pass fills it from a
+// loaded input row and how the V pass turns the window into P output rows.
+
+template <class Cl, bool INT = (sizeof(typename Cl::T) == 1)>
+struct RowMath;
+
+// Float data: FP32 values, FMA chains in tap order.
+template <class Cl>
+struct RowMath<Cl, false> {
+  using T = typename Cl::T;
+  static constexpr int N = Cl::NOUT;
+  struct Row {
+    float v[N];
+  };
+  __device__ static __forceinline__ void h(const uint32_t* w, const FastParams& prm, Row& r) {
+    hcompute<Cl>(w, prm.taps[Cl::id], r.v);
+  }
+  __device__ static __forceinline__ void copy(Row& d, const Row& s) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) d.v[k] = s.v[k];
+  }
+  // the P output rows of block rr from the window
+  __device__ static __forceinline__ void v(const Row (&win)[Cl::L], const FastParams& prm, T* obase,
+                                           long long rowe, int rr, int OH, int n_valid) {
+    const float* taps = prm.taps[Cl::id];
+#pragma unroll
+    for (int jv = 0; jv < Cl::P; ++jv) {
+      const int oy = rr * Cl::P + jv;
+      if (oy < OH) {
+        float acc[N];
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[k] = 0.0f;
+#pragma unroll
+        for (int tt = 0; tt < Cl::K; ++tt) {
+          const float wt = taps[jv * Cl::K + tt];
+#pragma unroll
+          for (int k = 0; k < N; ++k) acc[k] = fmaf(wt, win[Cl::b(jv) - Cl::BMIN + tt].v[k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < N; ++k) acc[k] = pass_round<T>(acc[k]);
+        store_run<T, N>(obase + (long long)oy * rowe, acc, n_valid);
+      }
+    }
+  }
+};
+
+// dp2a: c + a.lo16 * b.byte(2h) + a.hi16 * b.byte(2h+1), taps signed,
+// pixels unsigned; h = 0 (.lo) or 1 (.hi).
+template <int HALF>
+__device__ __forceinline__ int dp2a(uint32_t taps, uint32_t px, int c) {
+  int d;
+  if constexpr (HALF == 0) asm("dp2a.lo.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(taps), "r"(px), "r"(c));
+  else asm("dp2a.hi.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(taps), "r"(px), "r"(c));
+  return d;
+}
+
+// Bytes p0 <= p1 <= p2 <= p3 of the word array w (spanning at most four
+// words, every one of them inside the array) as one word, byte k = byte pk.
+// The positions are compile-time constants after unrolling, so the selectors
+// fold and only the words that hold one of the bytes are read.
+__device__ __forceinline__ uint32_t gather4(const uint32_t* w, int p0, int p1, int p2, int p3) {
+  const int pos[4] = {p0, p1, p2, p3};
+  const int a = p0 >> 2, top = (p3 >> 2) - a;
+  unsigned s1 = 0, s2 = 0, s3 = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int wi = (pos[k] >> 2) - a, by = pos[k] & 3;
+    if (wi <= 1) {
+      s1 |= (unsigned)(wi * 4 + by) << (4 * k);
+      s3 |= (unsigned)k << (4 * k);
+    } else {
+      s2 |= (unsigned)((wi - 2) * 4 + by) << (4 * k);
+      s3 |= (unsigned)(4 + (top == 2 ? by : k)) << (4 * k);
+    }
+  }
+  if (top == 0) return __byte_perm(w[a], w[a], s1);
+  const uint32_t r1 = __byte_perm(w[a], w[a + 1], s1);
+  if (top == 1) return r1;
+  if (top == 2) return __byte_perm(r1, w[a + 2], s3);
+  return __byte_perm(r1, __byte_perm(w[a + 2], w[a + 3], s2), s3);
+}
+
+// (acc + 2^13) >> 14 has been taken by starting acc at 2^13: floor shift, clamp.
+__device__ __forceinline__ int u8_round(int acc) { return __vimin_s32_relu(acc >> 14, 255); }
+
+// Four values 0..255 as the bytes of one word (v0 lowest).
+__device__ __forceinline__ uint32_t pack4(int v0, int v1, int v2, int v3) {
+  return __byte_perm(__byte_perm((uint32_t)v0, (uint32_t)v1, 0x0040u), __byte_perm((uint32_t)v2, (uint32_t)v3, 0x0040u),
+                     0x5410u);
+}
+
+// Store n_valid (<= 4*NW) bytes of words w to o with the widest aligned stores.
+template <int NB>
+__device__ __forceinline__ void store_bytes(uint8_t* o, const uint32_t* w, int n_valid) {
+  constexpr int NW = (NB + 3) / 4;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(o);
+  if (n_valid >= NB && (a & 3) == 0) {
+#pragma unroll
+    for (int i = 0; i < NB / 4; ++i) reinterpret_cast<uint32_t*>(o)[i] = w[i];
+#pragma unroll
+    for (int i = NB / 4 * 4; i < NB; ++i) o[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+    return;
+  }
+  if (n_valid >= NB && (a & 1) == 0) {
+#pragma unroll
+    for (int i = 0; i < NB / 2; ++i)
+      reinterpret_cast<unsigned short*>(o)[i] = (unsigned short)(w[(2 * i) >> 2] >> (8 * ((2 * i) & 3)));
+    if constexpr (NB % 2) o[NB - 1] = (uint8_t)(w[(NB - 1) >> 2] >> (8 * ((NB - 1) & 3)));
+    return;
+  }
+  (void)NW;
+#pragma unroll
+  for (int i = 0; i < NB; ++i)
+    if (i < n_valid) o[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+}
+
+// uint8 data: exact integer arithmetic with packed bytes.  A window row holds
+// the lane's NOUT horizontal results as bytes (4 per word, in output order).
+// The H pass first gathers each channel's pixels into words of 4 consecutive
+// pixels, then every output is K/2 (+1 for a window starting on an odd
+// pixel) dp2a steps over pixel pairs against the int16 tap pairs; the V pass
+// interleaves the bytes of window rows 2m and 2m+1 column by column and does
+// the same over row pairs.  Sums start at 2^13, so (acc + 2^13) >> 14 is a
+// plain shift; the results are the bits of the float kernels and the oracle.
+template <class Cl>
+struct RowMath<Cl, true> {
+  using T = uint8_t;
+  static constexpr int C = Cl::C, Q = Cl::Q, P = Cl::P, K = Cl::K, L = Cl::L, BMIN = Cl::BMIN;
+  static constexpr int N = Cl::NOUT;
+  static constexpr int NW = (N + 3) / 4;
+  static constexpr int NXP = Cl::LH + Cl::NB * Q + Cl::RH;  // window pixels of a lane
+  static constexpr int NCW = (NXP + 1 + 3) / 4;             // channel words (+1: odd-start pad)
+  static constexpr int NPR = (L + 2) / 2;                   // window row pairs (+1 slot of pad)
+  static constexpr int U8I = Cl::id - kFcU8C3_38;
+  static_assert(Cl::HB * Cl::VB >= Cl::LH * C, "pixel slot 0 must be a loaded byte");
+  static_assert(Cl::HB * Cl::VB - Cl::LH * C + NXP * C <= Cl::NVT * Cl::VB, "gathered bytes must be loaded");
+  static_assert(U8I >= 0 && U8I < kU8Classes && P <= 3 && (K + 2) / 2 <= kMaxPairs, "tap pair table");
+  struct Row {
+    uint32_t w[NW];
+  };
+  __device__ static __forceinline__ void copy(Row& d, const Row& s) {
+#pragma unroll
+    for (int k = 0; k < NW; ++k) d.w[k] = s.w[k];
+  }
+  __device__ static __forceinline__ uint32_t tp(const FastParams& prm, int par, int j, int i) {
+    return prm.tap2[U8I][par][j][i];
+  }
+  __device__ static __forceinline__ void h(const uint32_t* w, const FastParams& prm, Row& r) {
+    constexpr int first = Cl::HB * Cl::VB - Cl::LH * C;  // byte of pixel slot 0, channel 0
+    uint32_t cw[C][NCW];
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+      for (int k = 0; k < NCW; ++k) {
+        int pos[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int slot = (4 * k + i < NXP) ? 4 * k + i : NXP - 1;  // pad slots: any byte
+          pos[i] = first + slot * C + c;
+        }
+        cw[c][k] = gather4(w, pos[0], pos[1], pos[2], pos[3]);
+      }
+    int v[N];
+#pragma unroll
+    for (int n = 0; n < Cl::NB; ++n)
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
+        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          int acc = 8192;
+#pragma unroll
+          for (int i = 0; i < npair; ++i) {
+            const int pi = pr0 + i;
+            acc = (pi & 1) ? dp2a<1>(tp(prm, par, j, i), cw[c][pi >> 1], acc)
+                           : dp2a<0>(tp(prm, par, j, i), cw[c][pi >> 1], acc);
+          }
+          v[(n * P + j) * C + c] = u8_round(acc);
+        }
+      }
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const int e = 4 * k;
+      r.w[k] = pack4(v[e], e + 1 < N ? v[e + 1] : 0, e + 2 < N ? v[e + 2] : 0, e + 3 < N ? v[e + 3] : 0);
+    }
+  }
+  __device__ static __forceinline__ void v(const Row (&win)[L], const FastParams& prm, T* obase, long long rowe,
+                                           int rr, int OH, int n_valid) {
+    // one word column g (4 output columns) at a time: row-pair words
+    // pl = bytes 0,1 of rows 2m and 2m+1 interleaved, ph = bytes 2,3
+    uint32_t o[P][NW];
+#pragma unroll
+    for (int g = 0; g < NW; ++g) {
+      uint32_t pl[NPR], ph[NPR];
+#pragma unroll
+      for (int m = 0; m < NPR; ++m) {
+        const int r0 = 2 * m < L ? 2 * m : L - 1, r1 = 2 * m + 1 < L ? 2 * m + 1 : L - 1;
+        pl[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x5140u);
+        ph[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x7362u);
+      }
+#pragma unroll
+      for (int jv = 0; jv < P; ++jv) {
+        const int s0 = Cl::b(jv) - BMIN;
+        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
+        int v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          int acc = 8192;
+#pragma unroll
+          for (int i = 0; i < npair; ++i) {
+            const uint32_t word = (e & 2) ? ph[pr0 + i] : pl[pr0 + i];
+            acc = (e & 1) ? dp2a<1>(tp(prm, par, jv, i), word, acc) : dp2a<0>(tp(prm, par, jv, i), word, acc);
+          }
+          v[e] = u8_round(acc);
+        }
+        o[jv][g] = pack4(v[0], v[1], v[2], v[3]);
+      }
+    }
+#pragma unroll
+    for (int jv = 0; jv < P; ++jv) {
+      const int oy = rr * P + jv;
+      if (oy < OH) store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
+    }
+  }
+};
+
 template <class Cl, int WPC, int MINB>
 __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__ FastParams prm) {
   using T = typename Cl::T;
-  constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P, K = Cl::K, NOUT = Cl::NOUT, SR = Cl::SRR, NST = Cl::NST;
+  using RM = RowMath<Cl>;
+  using Row = typename RM::Row;
+  constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P, SR = Cl::SRR, NST = Cl::NST;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -951,7 +1197,6 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncwarp();
-  const float* taps = prm.taps[Cl::id];
   const Offs<Cl> of = thread_offs<Cl>(lane);
   const unsigned nwarps = gridDim.x * WPC;
   unsigned* const next = &g_tile_next[prm.sched_slot];
@@ -1011,15 +1256,15 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
         issued = g + (uint32_t)(s + NST + 1);
       }
     };
-    // H pass of one loaded row into o[0..NOUT)
-    auto hrow_regs = [&](uint8_t* rowbase, float* o) {
+    // H pass of one loaded row into a window row
+    auto hrow_regs = [&](uint8_t* rowbase, Row& o) {
       if (fixing) apply_edge_fix<Cl>(rowbase, fix, lane, jd.W, xw);
       uint32_t w[Cl::NWT];
       load_row<Cl>(rowbase, of, w);
-      if (active) hcompute<Cl>(w, taps, o);
+      if (active) RM::h(w, prm, o);
     };
 
-    float win[L][NOUT];
+    Row win[L];
     // ---- prologue: pattern rows 0 .. L-Q-1
 #pragma unroll
     for (int ps = 0; ps < Cl::NPS; ++ps) {
@@ -1035,8 +1280,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
         const int y = ys + i;
         if (y < 0) continue;                    // top band: filled from frame row 0 below
         if (i > 0 && y >= H) {
-#pragma unroll
-          for (int k = 0; k < NOUT; ++k) win[i][k] = win[i - 1][k];
+          RM::copy(win[i], win[i - 1]);
         } else {
           hrow_regs(sb + r * Cl::BOXB, win[i]);
         }
@@ -1046,9 +1290,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     if (!ok) break;
     if (ys < 0) {  // ys == BMIN: slots 0..LH-1 are frame row 0, held in slot LH
 #pragma unroll
-      for (int i = 0; i < Cl::LH; ++i)
-#pragma unroll
-        for (int k = 0; k < NOUT; ++k) win[i][k] = win[Cl::LH][k];
+      for (int i = 0; i < Cl::LH; ++i) RM::copy(win[i], win[Cl::LH]);
     }
     // ---- block steps, U rows (USTG stages, UBLK blocks) at a time
     const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
@@ -1073,38 +1315,15 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
             const int i = L - Q + q;
             const int y = ys + m * Q + i;
             if (y >= H) {
-#pragma unroll
-              for (int k = 0; k < NOUT; ++k) win[i][k] = win[i - 1][k];
+              RM::copy(win[i], win[i - 1]);
             } else {
               hrow_regs(sb + r * Cl::BOXB, win[i]);
             }
             if (q == Q - 1) {
               // the window holds block m's pattern: its P output rows
-              if (active) {
-                const int rr = rb0 + m;
+              if (active) RM::v(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
 #pragma unroll
-                for (int jv = 0; jv < P; ++jv) {
-                  const int oy = rr * P + jv;
-                  if (oy < jd.OH) {
-                    float acc[NOUT];
-#pragma unroll
-                    for (int k = 0; k < NOUT; ++k) acc[k] = 0.0f;
-#pragma unroll
-                    for (int tt = 0; tt < K; ++tt) {
-                      const float wt = taps[jv * K + tt];
-#pragma unroll
-                      for (int k = 0; k < NOUT; ++k) acc[k] = fmaf(wt, win[Cl::b(jv) - Cl::BMIN + tt][k], acc[k]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < NOUT; ++k) acc[k] = pass_round<T>(acc[k]);
-                    store_run<T, NOUT>(obase + (long long)oy * rowe, acc, n_valid);
-                  }
-                }
-              }
-#pragma unroll
-              for (int i2 = 0; i2 < L - Q; ++i2)
-#pragma unroll
-                for (int k = 0; k < NOUT; ++k) win[i2][k] = win[i2 + Q][k];
+              for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
             }
           }
         }
@@ -1157,7 +1376,7 @@ bool has_rows_kernel(int cls) {
   switch (cls) {
     case kFcF32_38: case kFcF32_12: case kFcF32_23:
     case kFcF16_38: case kFcF16_12: case kFcF16_23:
-    case kFcU8C3_12: return true;
+    case kFcU8C3_38: case kFcU8C3_12: case kFcU8C3_23: return true;
     default: return false;
   }
 }
@@ -1171,9 +1390,9 @@ HostGeom geom_of(int cls) {
     case kFcF16_38: return host_geom_rows<RF16_38>();
     case kFcF16_12: return host_geom_rows<RF16_12>();
     case kFcF16_23: return host_geom_rows<RF16_23>();
-    case kFcU8C3_38: return host_geom<CU8_38>();
+    case kFcU8C3_38: return host_geom_rows<RU8_38>();
     case kFcU8C3_12: return host_geom_rows<RU8_12>();
-    default: return host_geom<CU8_23>();
+    default: return host_geom_rows<RU8_23>();
   }
 }
 
@@ -1222,9 +1441,9 @@ KernelInfo kernel_for(int cls) {
     case kFcF16_38: return rows_info<RF16_38>();
     case kFcF16_12: return rows_info<RF16_12>();
     case kFcF16_23: return rows_info<RF16_23>();
-    case kFcU8C3_38: return kernel_info<8, CU8_38>();
+    case kFcU8C3_38: return rows_info<RU8_38>();
     case kFcU8C3_12: return rows_info<RU8_12>();
-    default: return kernel_info<4, CU8_23>();
+    default: return rows_info<RU8_23>();
   }
 }
 
@@ -1269,14 +1488,27 @@ void fill_taps(FastParams& prm) {
         const int cls = pl->fast_class;
         for (int i = 0; i < pl->p * pl->K; ++i)
           taps_only.taps[cls][i] = (dts[d] == DS_U8_RGB) ? (float)pl->q14[i] : pl->w32[i];
+        if (dts[d] == DS_U8_RGB) {
+          const int u = cls - kFcU8C3_38;
+          for (int par = 0; par < 2; ++par)
+            for (int j = 0; j < pl->p; ++j)
+              for (int i = 0; i < kMaxPairs; ++i) {
+                const int ta = 2 * i - par, tb = 2 * i + 1 - par;
+                const int qa = (ta >= 0 && ta < pl->K) ? pl->q14[j * pl->K + ta] : 0;
+                const int qb = (tb >= 0 && tb < pl->K) ? pl->q14[j * pl->K + tb] : 0;
+                taps_only.tap2[u][par][j][i] = (uint32_t)(uint16_t)(int16_t)qa | ((uint32_t)(uint16_t)(int16_t)qb << 16);
+              }
+        }
         ds_destroy(pl);
       }
   });
   std::memcpy(prm.taps, taps_only.taps, sizeof(prm.taps));
+  std::memcpy(prm.tap2, taps_only.tap2, sizeof(prm.tap2));
 }
 
-// Tile geometry of a job (everything but the tensor map).
-void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames) {
+// Tile geometry of a job (everything but the tensor map).  `band`: output
+// row blocks per tile, 0 = the plan's.
+void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, int band = 0) {
   const HostGeom hg = geom_of(pl->fast_class);
   jd.out = out;
   jd.out_frame = (long long)pl->out_frame_elems();
@@ -1289,13 +1521,13 @@ void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames) 
   const int nbx = (pl->out_w + hg.p - 1) / hg.p;
   const int nby = (pl->out_h + hg.p - 1) / hg.p;
   jd.strips = (nbx + hg.sblk - 1) / hg.sblk;
-  jd.rbc = std::max(1, std::min(pl->row_blocks, nby));
+  jd.rbc = std::max(1, std::min(band > 0 ? band : pl->row_blocks, nby));
   jd.chunks = (nby + jd.rbc - 1) / jd.rbc;
   jd.tiles = jd.strips * jd.chunks * n_frames;
   jd.out_vec = (((uintptr_t)out & 3u) == 0 && ((size_t)pl->out_w * pl->channels) % 4 == 0) ? 1 : 0;
 }
 
-ds_status encode_job(JobDesc& jd, const FastJob& job) {
+ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
   const ds_plan* pl = job.plan;
   const HostGeom hg = geom_of(pl->fast_class);
   auto enc = encode_fn();
@@ -1315,8 +1547,28 @@ ds_status encode_job(JobDesc& jd, const FastJob& job) {
     set_error("cuTensorMapEncodeTiled failed (%d) for a %dx%d frame", (int)r, pl->in_h, pl->in_w);
     return DS_ERR_CUDA;
   }
-  fill_job_geometry(jd, pl, job.out, job.n_frames);
+  fill_job_geometry(jd, pl, job.out, job.n_frames, band);
   return DS_OK;
+}
+
+// Band height for the jobs of one launch.  A tile is processed serially by
+// one warp (row kernel) or CTA, so a launch with fewer band-rows of work than
+// the GPU has pipelines finishes sooner with shorter bands: the band is cut
+// to ceil(block rows of work / pipelines), never above the plans' own value.
+// Plans with a caller-set (or autotuned) schedule keep theirs.
+int launch_band(const FastJob* jobs, int n, int pipelines) {
+  long long units = 0;
+  int cap = 0;
+  for (int i = 0; i < n; ++i) {
+    const ds_plan* pl = jobs[i].plan;
+    if (pl->schedule_set) return 0;
+    const HostGeom hg = geom_of(pl->fast_class);
+    const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.p - 1) / hg.p;
+    units += (nbx + hg.sblk - 1) / hg.sblk * nby * (long long)jobs[i].n_frames;
+    cap = std::max(cap, pl->row_blocks);
+  }
+  const long long fill = (units + pipelines - 1) / std::max(1, pipelines);
+  return (int)std::max<long long>(1, std::min<long long>(cap, fill));
 }
 
 // ---------------------------------------------------------------------------
@@ -1568,7 +1820,9 @@ std::string check_plan(const ds_plan* pl) {
       case kFcF16_38: return check_rows<RF16_38, kRowsWPC>(jd);
       case kFcF16_12: return check_rows<RF16_12, kRowsWPC>(jd);
       case kFcF16_23: return check_rows<RF16_23, kRowsWPC>(jd);
-      default: return check_rows<RU8_12, kRowsWPC>(jd);
+      case kFcU8C3_38: return check_rows<RU8_38, kRowsWPC>(jd);
+      case kFcU8C3_12: return check_rows<RU8_12, kRowsWPC>(jd);
+      default: return check_rows<RU8_23, kRowsWPC>(jd);
     }
   }
   switch (pl->fast_class) {
@@ -1592,19 +1846,7 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   fill_taps(prm);
   const int cls = jobs[0].plan->fast_class;  // launch_fast groups jobs by class
   int want_ctas = jobs[0].plan->ctas_per_sm;
-  int tiles = 0;
-  for (int i = 0; i < n; ++i) {
-    ds_status s = encode_job(prm.jobs[i], jobs[i]);
-    if (s != DS_OK) return s;
-    prm.jobs[i].tile_begin = tiles;
-    tiles += prm.jobs[i].tiles;
-    want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
-  }
-  prm.n_jobs = n;
-  prm.total_tiles = tiles;
-  static std::atomic<unsigned> slot_counter{0};
-  prm.sched_slot = (int)(slot_counter.fetch_add(1) % kSchedSlots);
-  if (tiles == 0) return DS_OK;
+  for (int i = 0; i < n; ++i) want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
   const KernelInfo ki = kernel_for(cls);
   int occ = ctas_per_sm(ki);
   if (occ <= 0) {
@@ -1614,6 +1856,19 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   if (want_ctas > 0) occ = std::min(occ, want_ctas);
   // the row-streaming kernel runs one tile per warp, the other one per CTA
   const int per_cta = has_rows_kernel(cls) ? ki.threads / 32 : 1;
+  const int band = launch_band(jobs, n, sm_count() * occ * per_cta);
+  int tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    ds_status s = encode_job(prm.jobs[i], jobs[i], band);
+    if (s != DS_OK) return s;
+    prm.jobs[i].tile_begin = tiles;
+    tiles += prm.jobs[i].tiles;
+  }
+  prm.n_jobs = n;
+  prm.total_tiles = tiles;
+  static std::atomic<unsigned> slot_counter{0};
+  prm.sched_slot = (int)(slot_counter.fetch_add(1) % kSchedSlots);
+  if (tiles == 0) return DS_OK;
   const int grid = std::min((tiles + per_cta - 1) / per_cta, sm_count() * occ);
   void* args[] = {&prm};
   cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, (size_t)ki.smem, st);

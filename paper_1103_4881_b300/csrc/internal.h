@@ -48,6 +48,9 @@ struct ds_plan {
   int fast_class = ds::kFcNone;              // -1: general kernels only
   int row_blocks = 0;                        // fused tile: output row blocks per tile
   int ctas_per_sm = 0;                       // persistent grid: 0 = occupancy
+  bool schedule_set = false;                 // row_blocks fixed by the caller or the autotuner;
+                                             // else a launch too small to fill the GPU uses
+                                             // shorter bands (more tiles)
   bool force_general = false;                // DS_NO_TMA or unsupported alignment
 
   size_t in_frame_elems() const { return (size_t)in_h * in_w * channels; }

@@ -266,6 +266,7 @@ ds_status ds_plan_set_schedule(ds_plan* pl, int row_blocks, int ctas_per_sm) {
   }
   pl->row_blocks = row_blocks;
   pl->ctas_per_sm = ctas_per_sm;
+  pl->schedule_set = true;
   return DS_OK;
 }
 

@@ -35,6 +35,8 @@ ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frame
     return cuda_fail(cudaGetLastError(), "ds_plan_autotune: events");
   }
   const int keep_rb = plan->row_blocks, keep_ctas = plan->ctas_per_sm;
+  const bool keep_set = plan->schedule_set;
+  plan->schedule_set = true;  // time each candidate as given
   int best = keep_rb;
   float best_t = 1e30f;
   ds_status s = DS_OK;
@@ -63,9 +65,11 @@ ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frame
   plan->ctas_per_sm = keep_ctas;
   if (s != DS_OK) {
     plan->row_blocks = keep_rb;
+    plan->schedule_set = keep_set;
     return s;
   }
   plan->row_blocks = best;
+  plan->schedule_set = true;
   if (best_row_blocks) *best_row_blocks = best;
   if (best_us) *best_us = best_t * 1000.0f / iters;
   return DS_OK;
