@@ -1,35 +1,33 @@
 // fused_fast.cu -- the fused horizontal + vertical decimating FIR for B300.
 //
-// One persistent kernel runs the whole filter stage of the paper's
+// One persistent kernel per class runs the whole filter stage of the paper's
 // downscaler (Sec. 3: horizontal filter, then vertical filter, packets of q
-// pixels -> p outputs).  Work is cut into tiles: a strip of output columns
-// x a band of output row blocks of one frame.  Per CTA:
+// pixels -> p outputs).  Work is cut into tiles: a strip of output columns x
+// a band of output row blocks of one frame; tiles are handed to warps from a
+// per-launch counter.  Each warp runs its tile by itself:
 //
-//   producer warp (one elected lane): TMA tensor loads
-//     (cp.async.bulk.tensor.3d) of SR input rows of the strip plus its left
-//     and right halo into an NSTAGE-deep shared-memory ring, completion
-//     tracked by mbarrier transaction counts;
-//   4 consumer warps:
-//     H pass -- every thread loads one contiguous chunk of a row (NB packets
-//       of q pixels) with conflict-free vector ld.shared, takes the halo
-//       pixels from its neighbour lanes with warp shuffles, and computes
-//       NB*p outputs per channel with the phase taps (kernel parameters, so
-//       FFMA operands come from the constant bank);
-//     the horizontal results go to an on-chip ring of intermediate rows
-//       (the intermediate never reaches HBM -- the paper's Sec. 3.B.4 removes
-//       host round trips between the two filters; this removes the device
-//       memory round trip as well);
-//     V pass -- as soon as the rows of an output block are in the ring,
-//       threads read them column-wise and write the p output rows.
+//   lane 0 issues TMA tensor loads (cp.async.bulk.tensor.3d) of SR input rows
+//     of the strip plus its left and right halo into the warp's private ring
+//     of NST shared-memory stages, completion tracked by one mbarrier each;
+//   every input row goes through the horizontal pass in registers: each lane
+//     reads one contiguous chunk of the row (NB packets of q pixels plus the
+//     halo) with vector ld.shared and computes NB*p outputs per channel with
+//     the phase taps (kernel parameters, i.e. constant-bank operands);
+//   the results enter a sliding window of the last L filtered rows, also in
+//     registers, so the intermediate never leaves the SM (the paper's
+//     Sec. 3.B.4 removes host round trips between the two filters; this
+//     removes the device-memory round trip as well);
+//   each time q new rows have entered the window, the warp computes the p
+//     output rows of one block from it and stores them.
 //
-// The H and V dot products accumulate in tap order t = 0..K-1 with fmaf from
-// 0, the same sequence as the general kernels, so results are identical bit
-// for bit whatever kernel, tile or batch computes them.
+// Float data accumulate in FP32 with fmaf in tap order t = 0..K-1 from 0, the
+// same sequence as the general kernels; uint8 data use exact integer dot
+// products (dp2a) whose rounding is the same integer formula; so results are
+// identical bit for bit whatever kernel, tile or batch computes them.
 //
-// Every wait on an mbarrier is bounded (2e9 SM clock cycles, about 1 s).  On expiry the
-// kernel records DS_ERR_TIMEOUT in a device status word, the consumers agree
-// on leaving through a barrier with OR-reduction, and the producer waits
-// (bounded) for the copies it issued before it returns.
+// Every wait on an mbarrier is bounded (2e9 SM clock cycles, about 1 s).  On
+// expiry the warp records DS_ERR_TIMEOUT in a device status word, waits
+// (bounded) for the copies it issued and leaves.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -57,17 +55,11 @@ __device__ unsigned int g_warps_done[kSchedSlots];
 
 namespace {
 
-constexpr int kNH = 8;                        // horizontal-pass warps
-constexpr int kNV = 4;                        // vertical-pass warps
-constexpr int kNWC = kNH + kNV;               // consumer warps
-constexpr int kThreads = (kNWC + 1) * 32;     // + one producer warp
-constexpr int kNRS = 4;                       // intermediate ring capacity, in stages
 constexpr int kMaxJobs = 64;                  // job descriptors per launch
 constexpr int kMaxTaps = 24;                  // p*K of the fast classes
 constexpr long long kWaitLimitCycles = 2000000000ll;  // ~1 s at the B300's 2.03 GHz
 constexpr uint32_t kSuspendHintNs = 20000;             // a waiting thread sleeps up to 20 us per poll
 constexpr int kStatusTimeout = 1;
-constexpr int kStatusBadClass = 2;
 
 // ---------------------------------------------------------------------------
 // compile-time geometry
@@ -79,10 +71,7 @@ __host__ __device__ constexpr int rup(int a, int m) { return cdiv(a, m) * m; }
 __host__ __device__ constexpr int phase_b(int P, int Q, int K, int j) {
   return cfloordiv((2 * j + 1) * Q - P, 2 * P) - K / 2 + 1;
 }
-__host__ __device__ constexpr int pow2_at_least(int a) { return a <= 1 ? 1 : 2 * pow2_at_least((a + 1) / 2); }
-constexpr int cmax(int a) { return a; }
-template <typename... R>
-constexpr int cmax(int a, int b, R... r) { return cmax(a > b ? a : b, r...); }
+__host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
 template <typename T>
 struct TmaType;
@@ -93,84 +82,77 @@ struct TmaType<__half> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_
 template <>
 struct TmaType<uint8_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_UINT8; };
 
-// Intermediate type in the on-chip ring: FP32 for float data; FP16 for uint8
-// data, whose intermediate values are integers 0..255 (exact in FP16).
-template <typename T>
-struct RingOf { using type = float; };
-template <>
-struct RingOf<uint8_t> { using type = __half; };
-
 // A fast-path class: data type, channels, ratio P/Q, taps K, and the tile
-// shape -- NB packets per thread and row, WX warps across a strip, SR input
-// rows per pipeline stage, VE columns per thread in the V pass.
-template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int WX_, int SR_, int VE_>
+// shape -- NB packets (of Q input pixels) per lane and row, so a warp's strip
+// is 32*NB packets wide; SR input rows per pipeline stage, NST stages per warp.
+template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_>
 struct Cls {
   using T = T_;
-  using R = typename RingOf<T_>::type;
-  static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_, WX = WX_, SR = SR_, VE = VE_;
-  static constexpr int WY = kNH / WX;
+  static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
+  static constexpr int SRR = SR_;                   // input rows per stage
+  static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
   static constexpr int BMIN = phase_b(P, Q, K, 0);
   static constexpr int BMAX = phase_b(P, Q, K, P - 1);
-  static constexpr int L = BMAX - BMIN + K;   // pattern length (rows or pixels per block window)
-  static constexpr int LH = -BMIN;            // halo pixels left of a block
-  static constexpr int RH = BMAX + K - Q;     // halo pixels right of a block
-  static constexpr int E = NB * Q * C;        // elements per thread and row
+  static constexpr int L = BMAX - BMIN + K;         // pattern length (rows or pixels per block window)
+  static constexpr int LH = -BMIN;                  // halo pixels left of a block
+  static constexpr int RH = BMAX + K - Q;           // halo pixels right of a block
+  static constexpr int E = NB * Q * C;              // elements per lane and row
   static constexpr int EB = E * SZ;
-  static constexpr int EW = EB / 4;
   static constexpr int HLB = rup(LH * C * SZ, 16);  // left halo bytes in the window (TMA x alignment)
   static constexpr int RHB = rup(RH * C * SZ, 16);
-  static constexpr int SBLK = 32 * NB * WX;         // packets (blocks) per strip
+  static constexpr int SBLK = 32 * NB;              // packets (blocks) per strip
   static constexpr int SPX = SBLK * Q;              // input pixels per strip
   static constexpr int WINB = HLB + SPX * C * SZ + RHB;
   static constexpr int NBOX = cdiv(WINB / SZ, 256);
   static constexpr int BOXB = rup(cdiv(WINB, NBOX), 16);
   static constexpr int BOXE = BOXB / SZ;
-  static constexpr int BOXSTR = rup(SR * BOXB, 128);  // each box lands 128-B aligned
-  static constexpr int STAGE_BYTES = NBOX * BOXSTR;
-  static constexpr int TX_BYTES = NBOX * SR * BOXB;
-  static constexpr int SOE = SBLK * P * C;            // intermediate elements per ring row
-  static constexpr int RING = kNRS * SR;              // ring rows: kNRS stages of SR rows
-  static constexpr int RING_MASK = RING - 1;
-  static constexpr int D = cdiv(L - 1, SR);           // V of stage k reads rows of stages k-D..k
-  static constexpr int RING_BYTES = rup(RING * SOE * (int)sizeof(R), 16);
-  static constexpr int NX = (LH + NB * Q + RH) * C;   // elements one thread reads per row
+  static constexpr int BOXSTR = rup(SR_ * BOXB, 128);  // each box lands 128-B aligned
+  static constexpr int RSTAGE = NBOX * BOXSTR;
+  static constexpr int RTX = NBOX * SR_ * BOXB;        // TMA bytes per stage
+  static constexpr int WARP_BYTES = NST_ * RSTAGE;
+  static constexpr int NX = (LH + NB * Q + RH) * C;    // elements one lane reads per row
   static constexpr int VB = (EB % 16 == 0) ? 16 : ((EB % 8 == 0) ? 8 : 4);
   static constexpr int NV = EB / VB;
-  static constexpr int HB = cdiv(LH * C * SZ, VB);   // halo vectors a thread loads before its chunk
-  static constexpr int HA = cdiv(RH * C * SZ, VB);   // ... and after it
-  static constexpr int NVT = HB + NV + HA;           // vectors per thread and row
-  static constexpr int NWT = NVT * VB / 4;           // words per thread and row
-  // With 16-byte vectors and a 32-byte lane stride, the lanes of one
-  // 8-lane shared-memory phase cover only half the 16-byte bank groups for a
-  // fixed vector index (2-way conflicts).  Lanes 4-7 of each phase then load
-  // their 4 vectors in the order 1,2,3,0, which makes every phase hit 8
-  // distinct bank groups; the vectors are put back in order with selects.
-  static constexpr bool ROT = (VB == 16 && EB == 32 && NVT == 4);
-  static constexpr int NOUT = NB * P * C;             // H outputs per thread and row
+  static constexpr int HB = cdiv(LH * C * SZ, VB);     // halo vectors a lane loads before its chunk
+  static constexpr int HA = cdiv(RH * C * SZ, VB);     // ... and after it
+  static constexpr int NVT = HB + NV + HA;             // vectors per lane and row
+  static constexpr int NWT = NVT * VB / 4;             // words per lane and row
+  static constexpr int NOUT = NB * P * C;              // H outputs per lane and row
+  // The stream of a tile is cut so that the window prologue (the first L-Q
+  // pattern rows) fills whole stages, EXTRA rows being loaded before the first
+  // pattern row; after it, every group of U = lcm(SR, Q) rows is USTG stages
+  // and UBLK block steps, so each row's stage offset and window slot are
+  // compile-time constants.
+  static constexpr int PRE = L - Q;
+  static constexpr int NPS = cdiv(PRE, SR_);
+  static constexpr int EXTRA = NPS * SR_ - PRE;
+  static constexpr int U = SR_ / cgcd(SR_, Q) * Q;
+  static constexpr int USTG = U / SR_;
+  static constexpr int UBLK = U / Q;
   __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
-  static_assert(EB % 4 == 0, "a thread's chunk must be whole words");
+  static_assert(EB % 4 == 0, "a lane's chunk must be whole words");
   static_assert(HB * VB <= HLB && HA * VB <= RHB, "halo vectors must lie in the loaded window");
   static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
   static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
-  static_assert(SR % WY == 0 && kNH % WX == 0, "stage rows must split over warp rows");
-  static_assert((SR & (SR - 1)) == 0 && kNRS >= D + 1, "ring of kNRS power-of-two stages");
-  static_assert(SOE % 4 == 0 && VE == 4, "V pass works on groups of 4 columns");
-  static_assert((RING & RING_MASK) == 0, "ring size");
   static_assert(P * K <= kMaxTaps, "tap table size");
   static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
+  static_assert(PRE > LH, "the window prologue must reach frame row 0");
+  static_assert(L * (SZ == 1 ? (NOUT + 3) / 4 : NOUT) <= 48, "register window too large");
+  static_assert(U <= 16, "iteration unit too long to unroll");
 };
 
-//                 id        T     C  P  Q  K  NB WX  SR VE
-using CF32_38 = Cls<kFcF32_38, float, 1, 3, 8, 8, 1, 1, 16, 4>;
-using CF32_12 = Cls<kFcF32_12, float, 1, 1, 2, 6, 4, 1, 16, 4>;
-using CF32_23 = Cls<kFcF32_23, float, 1, 2, 3, 6, 2, 1, 16, 4>;
-using CF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 1, 16, 4>;
-using CF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 1, 16, 4>;
-using CF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 1, 16, 4>;
-using CU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 1, 8, 4>;
-using CU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 2, 2, 8, 4>;
-using CU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 1, 8, 4>;
+//                 id          T       C  P  Q  K  NB SR NST
+using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 4, 3>;
+using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3>;
+using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3>;
+using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 4, 3>;
+using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 4, 3>;
+using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3>;
+// uint8 RGB (integer row math)
+using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3>;
+using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3>;
+using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3>;
 
 // ---------------------------------------------------------------------------
 // launch parameters
@@ -212,9 +194,6 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr32(bar)), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr32(bar)) : "memory");
-}
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -227,19 +206,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 // Wait for the phase of `parity` to complete; false after about a second
-// (kWaitLimitCycles SM clock cycles, counted from the 4th failed poll), or at
-// once when *abort_flag becomes non-zero (if given).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+// (kWaitLimitCycles SM clock cycles, counted from the 4th failed poll).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
 #pragma unroll 1
   for (int it = 0; it < 4; ++it)
     if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 3u) == 0) {
-      if (abort_flag && *abort_flag) return false;
-      if (clock64() - t0 > kWaitLimitCycles) return false;
-    }
+    if ((it & 3u) == 0 && clock64() - t0 > kWaitLimitCycles) return false;
   }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
@@ -275,30 +250,6 @@ __host__ __device__ __forceinline__ Tile decode_tile(const FastParams& prm, int 
   return r;
 }
 
-struct Geo {
-  int rb0;   // first output row block of the tile
-  int nblk;  // row blocks in the tile
-  int ys;    // first input row of the tile's pattern (may be < 0)
-  int rows;  // input rows the tile needs
-  int nst;   // pipeline stages of the tile
-  int xw;    // first element (x coordinate) of the loaded window
-  int ox0;   // first output pixel of the strip
-};
-
-template <class Cl>
-__host__ __device__ __forceinline__ Geo tile_geo(const JobDesc& jd, const Tile& tl) {
-  Geo g;
-  g.rb0 = tl.chunk * jd.rbc;
-  const int nby = (jd.OH + Cl::P - 1) / Cl::P;
-  g.nblk = jd.rbc < nby - g.rb0 ? jd.rbc : nby - g.rb0;
-  g.ys = g.rb0 * Cl::Q + Cl::BMIN;
-  g.rows = (g.nblk - 1) * Cl::Q + Cl::L;
-  g.nst = (g.rows + Cl::SR - 1) / Cl::SR;
-  g.xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
-  g.ox0 = tl.strip * Cl::SBLK * Cl::P;
-  return g;
-}
-
 // Offset of byte `byte` of window row 0 inside a stage: boxes are stored one
 // after the other, each as SR rows of BOXB bytes (BOXSTR bytes apart), so row
 // r of the window starts r * BOXB bytes further in every box.
@@ -306,25 +257,6 @@ template <class Cl>
 __host__ __device__ __forceinline__ int win_off(int byte) {
   const int box = byte / Cl::BOXB;
   return byte + box * (Cl::BOXSTR - Cl::BOXB);
-}
-
-// ---------------------------------------------------------------------------
-// producer
-// ---------------------------------------------------------------------------
-template <class Cl, int NSTAGE, int STAGE_MAX>
-__device__ bool produce_tile(const JobDesc& jd, const Tile& tl, uint8_t* stages, uint64_t* full, uint64_t* empty,
-                             uint32_t& g, const volatile int* abort_flag) {
-  const Geo G = tile_geo<Cl>(jd, tl);
-  for (int k = 0; k < G.nst; ++k, ++g) {
-    const uint32_t slot = g % NSTAGE, round = g / NSTAGE;
-    if (round > 0 && !mbar_wait(&empty[slot], (round - 1) & 1u, abort_flag)) return false;
-    uint8_t* dst = stages + slot * STAGE_MAX;
-    mbar_expect_tx(&full[slot], Cl::TX_BYTES);
-#pragma unroll
-    for (int bx = 0; bx < Cl::NBOX; ++bx)
-      tma_load_3d(dst + bx * Cl::BOXSTR, &jd.tmap, &full[slot], G.xw + bx * Cl::BOXE, G.ys + k * Cl::SR, tl.frame);
-  }
-  return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -340,65 +272,40 @@ __device__ __forceinline__ float word_elem<__half>(const uint32_t* w, int byte) 
   const unsigned short h = (byte & 2) ? (unsigned short)(v >> 16) : (unsigned short)(v & 0xffffu);
   return __half2float(__ushort_as_half(h));
 }
-template <>
-__device__ __forceinline__ float word_elem<uint8_t>(const uint32_t* w, int byte) {
-  // byte -> float through the bit pattern of 2^23 + byte
-  return __uint_as_float(__byte_perm(w[byte >> 2], 0x4B000000u, 0x7540u | (unsigned)(byte & 3))) - 8388608.0f;
-}
 
-template <typename T>
-__device__ __forceinline__ float smem_elem(const uint8_t* p) { return px_to_f(*reinterpret_cast<const T*>(p)); }
 
-// Per-thread shared-memory offsets (row 0 of a stage) of the vectors the H
-// pass loads: HB halo vectors, the thread's own NV vectors, HA halo vectors,
-// consecutive in the window, in the (possibly rotated) order they are loaded.
-// They depend only on the lane: computed once.
+// Per-lane shared-memory offsets (row 0 of a stage) of the vectors the H
+// pass loads: HB halo vectors, the lane's own NV vectors, HA halo vectors,
+// consecutive in the window.  They depend only on the lane: computed once.
 template <class Cl>
 struct Offs {
   int v[Cl::NVT];
-  bool rot;
 };
 
 template <class Cl>
-__device__ __forceinline__ Offs<Cl> thread_offs(int lg) {
+__device__ __forceinline__ Offs<Cl> thread_offs(int lane) {
   Offs<Cl> o;
-  const int first = Cl::HLB + lg * Cl::EB - Cl::HB * Cl::VB;
-  o.rot = Cl::ROT && ((lg >> 2) & 1);
+  const int first = Cl::HLB + lane * Cl::EB - Cl::HB * Cl::VB;
 #pragma unroll
-  for (int v = 0; v < Cl::NVT; ++v) {
-    const int pv = o.rot ? (v + 1) % Cl::NVT : v;
-    o.v[v] = win_off<Cl>(first + pv * Cl::VB);
-  }
+  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = win_off<Cl>(first + v * Cl::VB);
   return o;
 }
 
-// Load the thread's vectors of one window row into words w[0..NWT).
+// Load the lane's vectors of one window row into words w[0..NWT).
 template <class Cl>
 __device__ __forceinline__ void load_row(const uint8_t* rowbase, const Offs<Cl>& o, uint32_t* w) {
   constexpr int WPV = Cl::VB / 4;
-  if constexpr (Cl::ROT) {
-    uint4 r[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) r[v] = *reinterpret_cast<const uint4*>(rowbase + o.v[v]);
-    // r[v] holds vector (v + rot) mod 4
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const uint4 x = o.rot ? r[(v + 3) & 3] : r[v];
-      w[v * 4] = x.x; w[v * 4 + 1] = x.y; w[v * 4 + 2] = x.z; w[v * 4 + 3] = x.w;
-    }
-  } else {
-#pragma unroll
-    for (int v = 0; v < Cl::NVT; ++v) {
-      const uint8_t* p = rowbase + o.v[v];
-      if constexpr (Cl::VB == 16) {
-        const uint4 x = *reinterpret_cast<const uint4*>(p);
-        w[v * WPV] = x.x; w[v * WPV + 1] = x.y; w[v * WPV + 2] = x.z; w[v * WPV + 3] = x.w;
-      } else if constexpr (Cl::VB == 8) {
-        const uint2 x = *reinterpret_cast<const uint2*>(p);
-        w[v * WPV] = x.x; w[v * WPV + 1] = x.y;
-      } else {
-        w[v] = *reinterpret_cast<const uint32_t*>(p);
-      }
+  for (int v = 0; v < Cl::NVT; ++v) {
+    const uint8_t* p = rowbase + o.v[v];
+    if constexpr (Cl::VB == 16) {
+      const uint4 x = *reinterpret_cast<const uint4*>(p);
+      w[v * WPV] = x.x; w[v * WPV + 1] = x.y; w[v * WPV + 2] = x.z; w[v * WPV + 3] = x.w;
+    } else if constexpr (Cl::VB == 8) {
+      const uint2 x = *reinterpret_cast<const uint2*>(p);
+      w[v * WPV] = x.x; w[v * WPV + 1] = x.y;
+    } else {
+      w[v] = *reinterpret_cast<const uint32_t*>(p);
     }
   }
 }
@@ -411,9 +318,9 @@ struct EdgeFix {
 };
 
 template <class Cl>
-__host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int wx, int W) {
-  const int seg0 = strip * Cl::SPX + wx * 32 * Cl::NB * Cl::Q - Cl::LH;       // first pixel the warp reads
-  const int seg1 = strip * Cl::SPX + (wx + 1) * 32 * Cl::NB * Cl::Q + Cl::RH;  // one past the last
+__host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int W) {
+  const int seg0 = strip * Cl::SPX - Cl::LH;             // first pixel the warp reads
+  const int seg1 = (strip + 1) * Cl::SPX + Cl::RH;       // one past the last
   EdgeFix f;
   f.l_lo = seg0;
   f.nl = seg0 < 0 ? ((seg1 < 0 ? seg1 : 0) - seg0) * Cl::C : 0;
@@ -439,49 +346,6 @@ __device__ __forceinline__ void apply_edge_fix(uint8_t* rowbase, const EdgeFix& 
   // these generic-proxy writes must land before the TMA refills the stage
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncwarp();
-}
-
-// Store a thread's NOUT horizontal results into its slice of a ring row with
-// the widest aligned vector stores (the slice starts at lg * NOUT elements).
-template <class Cl>
-__device__ __forceinline__ void ring_store(typename Cl::R* dst, const float* o) {
-  constexpr int N = Cl::NOUT;
-  if constexpr (sizeof(typename Cl::R) == 4) {
-    if constexpr (N % 4 == 0) {
-#pragma unroll
-      for (int i = 0; i < N / 4; ++i)
-        reinterpret_cast<float4*>(dst)[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
-    } else if constexpr (N % 2 == 0) {
-#pragma unroll
-      for (int i = 0; i < N / 2; ++i) reinterpret_cast<float2*>(dst)[i] = make_float2(o[2 * i], o[2 * i + 1]);
-    } else {
-#pragma unroll
-      for (int i = 0; i < N; ++i) dst[i] = o[i];
-    }
-  } else {
-    if constexpr (N % 2 == 0) {
-      uint32_t hw[N / 2];
-#pragma unroll
-      for (int i = 0; i < N / 2; ++i) {
-        const __half2 h2 = __floats2half2_rn(o[2 * i], o[2 * i + 1]);
-        hw[i] = *reinterpret_cast<const uint32_t*>(&h2);
-      }
-      if constexpr (N % 8 == 0) {
-#pragma unroll
-        for (int i = 0; i < N / 8; ++i)
-          reinterpret_cast<uint4*>(dst)[i] = make_uint4(hw[4 * i], hw[4 * i + 1], hw[4 * i + 2], hw[4 * i + 3]);
-      } else if constexpr (N % 4 == 0) {
-#pragma unroll
-        for (int i = 0; i < N / 4; ++i) reinterpret_cast<uint2*>(dst)[i] = make_uint2(hw[2 * i], hw[2 * i + 1]);
-      } else {
-#pragma unroll
-        for (int i = 0; i < N / 2; ++i) reinterpret_cast<uint32_t*>(dst)[i] = hw[i];
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < N; ++i) dst[i] = __float2half_rn(o[i]);
-    }
-  }
 }
 
 // Horizontal pass of one window row whose words the thread has loaded (see
@@ -510,398 +374,13 @@ __device__ __forceinline__ void hcompute(const uint32_t* w, const float* __restr
   }
 }
 
-// ... and stored to the thread's slice of a ring row.
-template <class Cl>
-__device__ __forceinline__ void hrow(const uint32_t* w, const float* __restrict__ taps,
-                                     typename Cl::R* __restrict__ dst) {
-  float o[Cl::NOUT];
-  hcompute<Cl>(w, taps, o);
-  ring_store<Cl>(dst, o);
-}
-
-// ---------------------------------------------------------------------------
-// consumer: vertical pass of the blocks that became ready at stage k
-// ---------------------------------------------------------------------------
-// Row blocks (tile-relative) whose V pass runs at stage k: block m is ready
-// once its last pattern row m*Q + L - 1 has been loaded.
-template <class Cl>
-__host__ __device__ __forceinline__ void ready_blocks(const Geo& G, int k, int& m_lo, int& m_hi) {
-  m_lo = k * Cl::SR - Cl::L + 1;
-  m_lo = m_lo <= 0 ? 0 : (m_lo + Cl::Q - 1) / Cl::Q;
-  m_hi = (k + 1) * Cl::SR - Cl::L;
-  m_hi = m_hi < 0 ? -1 : m_hi / Cl::Q;
-  if (m_hi > G.nblk - 1 || k == G.nst - 1) m_hi = G.nblk - 1;
-}
-
-// Four consecutive intermediate values of one ring row.
-template <class Cl>
-__device__ __forceinline__ void ring_load4(const typename Cl::R* p, float* h) {
-  if constexpr (sizeof(typename Cl::R) == 4) {
-    const float4 v = *reinterpret_cast<const float4*>(p);
-    h[0] = v.x; h[1] = v.y; h[2] = v.z; h[3] = v.w;
-  } else {
-    const uint2 v = *reinterpret_cast<const uint2*>(p);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-    h[0] = a.x; h[1] = a.y; h[2] = b.x; h[3] = b.y;
-  }
-}
-
-// Store four output values (vector store when aligned and complete).
-template <typename T>
-__device__ __forceinline__ void store4(T* o, const float* v, bool vec, int n_valid) {
-  if (vec && n_valid >= 4) {
-    if constexpr (sizeof(T) == 4) {
-      *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
-    } else if constexpr (sizeof(T) == 2) {
-      const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
-      *reinterpret_cast<uint2*>(o) = make_uint2(*reinterpret_cast<const uint32_t*>(&a), *reinterpret_cast<const uint32_t*>(&b));
-    } else {
-      uint32_t pk = 0;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) pk |= (uint32_t)f_to_px<T>(v[i]) << (8 * i);
-      *reinterpret_cast<uint32_t*>(o) = pk;
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-      if (i < n_valid) o[i] = f_to_px<T>(v[i]);
-  }
-}
-
-// Output row r*P + J, columns e0..e0+3 of the strip: the K taps of phase J
-// over the ring rows of its window, in tap order.  `rbase` is the ring row of
-// the tile's relative row 0.
-template <class Cl, int J>
-__device__ __forceinline__ void vtask(const JobDesc& jd, const Geo& G, const float* __restrict__ taps,
-                                      const typename Cl::R* __restrict__ ring, int rbase, int r, int e0,
-                                      typename Cl::T* o, int n_valid) {
-  using T = typename Cl::T;
-  const int row0 = r * Cl::Q + Cl::b(J);  // first input row of the window
-  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  float h[4];
-  if (row0 >= 0 && row0 + Cl::K - 1 < jd.H) {
-    const int q0 = rbase + row0 - G.ys;
-    const int s0 = q0 & Cl::RING_MASK;
-    if (s0 + Cl::K <= Cl::RING) {
-      const typename Cl::R* p = ring + s0 * Cl::SOE + e0;  // K consecutive ring rows
-#pragma unroll
-      for (int t = 0; t < Cl::K; ++t) {
-        ring_load4<Cl>(p + t * Cl::SOE, h);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = fmaf(taps[J * Cl::K + t], h[v], acc[v]);
-      }
-    } else {
-#pragma unroll
-      for (int t = 0; t < Cl::K; ++t) {
-        ring_load4<Cl>(ring + ((q0 + t) & Cl::RING_MASK) * Cl::SOE + e0, h);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] = fmaf(taps[J * Cl::K + t], h[v], acc[v]);
-      }
-    }
-  } else {
-    // frame top / bottom: clamp-to-edge rows
-#pragma unroll
-    for (int t = 0; t < Cl::K; ++t) {
-      const int yc = clampi(row0 + t, 0, jd.H - 1);
-      ring_load4<Cl>(ring + ((rbase + yc - G.ys) & Cl::RING_MASK) * Cl::SOE + e0, h);
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[v] = fmaf(taps[J * Cl::K + t], h[v], acc[v]);
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < 4; ++v) acc[v] = pass_round<T>(acc[v]);
-  store4<T>(o, acc, jd.out_vec != 0, n_valid);
-}
-
-template <class Cl, int J>
-__device__ __forceinline__ void vtask_phase(int j, const JobDesc& jd, const Geo& G, const float* taps,
-                                            const typename Cl::R* ring, int rbase, int r, int e0,
-                                            typename Cl::T* o, int n_valid) {
-  if constexpr (J < Cl::P) {
-    if (j == J) vtask<Cl, J>(jd, G, taps, ring, rbase, r, e0, o, n_valid);
-    else vtask_phase<Cl, J + 1>(j, jd, G, taps, ring, rbase, r, e0, o, n_valid);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// consumers: one tile
-// ---------------------------------------------------------------------------
-// Three pipelines meet here.  TMA -> H warps through full/empty (one stage
-// of input rows each).  H warps -> V warps through hdone/vdone over the ring
-// of intermediate rows, which holds kNRS stages: the rows of stage g live in
-// ring rows (g*SR .. g*SR+SR-1) mod RING.  The V pass of stage g reads rows of
-// stages g-D..g only (its blocks' windows are L <= D*SR+1 rows tall), so the
-// H pass of stage g may overwrite stage g-kNRS once the V pass of stage
-// g-kNRS+D is done.  When the class changes between tiles (the all-class
-// kernel), the ring layout changes with it and the H pass waits for every
-// earlier V pass instead.
-template <class Cl, int NSTAGE, int STAGE_MAX>
-__device__ bool h_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl, uint8_t* stages,
-                       uint8_t* ring_raw, uint64_t* full, uint64_t* empty, uint64_t* hdone, uint64_t* vdone,
-                       uint32_t& g, bool class_changed, const volatile int* abort_flag) {
-  using R = typename Cl::R;
-  R* ring = reinterpret_cast<R*>(ring_raw);
-  const float* taps = prm.taps[Cl::id];
-  const Geo G = tile_geo<Cl>(jd, tl);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int wx = warp % Cl::WX, wy = warp / Cl::WX;
-  const int lg = wx * 32 + lane;                         // chunk index across the strip
-  const int blk0 = tl.strip * Cl::SBLK + lg * Cl::NB;   // first packet of the chunk (frame coords)
-  const int px0 = blk0 * Cl::Q;
-  const bool active = blk0 * Cl::P < jd.OW;
-  (void)px0;
-  const Offs<Cl> of = thread_offs<Cl>(lg);
-  const EdgeFix fix = edge_fix<Cl>(tl.strip, wx, jd.W);
-  R* const ring_mine = ring + lg * Cl::NOUT;
-  for (int k = 0; k < G.nst; ++k, ++g) {
-    const uint32_t slot = g % NSTAGE;
-    // wait results are made warp-uniform, so a timeout takes the whole warp out
-    bool ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (g / NSTAGE) & 1u, abort_flag));
-    const int dep = (class_changed && k == 0) ? (int)g - 1 : (int)g - kNRS + Cl::D;
-    if (ok && dep >= 0)
-      ok = __all_sync(0xffffffffu, mbar_wait(&vdone[dep % kNRS], (uint32_t)(dep / kNRS) & 1u, abort_flag));
-    if (!ok) return false;
-    uint8_t* stage = stages + slot * STAGE_MAX;
-    // the warp's rows of this stage: border fix-ups, then all loads, then the
-    // arithmetic (so the loads of every row are in flight together)
-    constexpr int NR = Cl::SR / Cl::WY;
-    bool valid[NR];
-    uint32_t w[NR][Cl::NWT];
-#pragma unroll
-    for (int s = 0; s < NR; ++s) {
-      const int i = wy + s * Cl::WY;
-      const int rel = k * Cl::SR + i;
-      const int y = G.ys + rel;
-      valid[s] = y >= 0 && y < jd.H && rel < G.rows;  // other rows are never read by the V pass
-      if (valid[s] && fix.nl + fix.nr > 0) apply_edge_fix<Cl>(stage + i * Cl::BOXB, fix, lane, jd.W, G.xw);
-    }
-#pragma unroll
-    for (int s = 0; s < NR; ++s)
-      if (valid[s]) load_row<Cl>(stage + (wy + s * Cl::WY) * Cl::BOXB, of, w[s]);
-    if (active) {
-#pragma unroll
-      for (int s = 0; s < NR; ++s)
-        if (valid[s])
-          hrow<Cl>(w[s], taps, ring_mine + ((g * Cl::SR + wy + s * Cl::WY) & Cl::RING_MASK) * Cl::SOE);
-    }
-    __syncwarp();
-    if (lane == 0) {
-      mbar_arrive(&empty[slot]);
-      mbar_arrive(&hdone[g % kNRS]);
-    }
-  }
-  return true;
-}
-
-template <class Cl>
-__device__ bool v_tile(const FastParams& prm, const JobDesc& jd, const Tile& tl, const uint8_t* ring_raw,
-                       uint64_t* hdone, uint64_t* vdone, uint32_t& g, const volatile int* abort_flag) {
-  using T = typename Cl::T;
-  using R = typename Cl::R;
-  const R* ring = reinterpret_cast<const R*>(ring_raw);
-  const float* taps = prm.taps[Cl::id];
-  const Geo G = tile_geo<Cl>(jd, tl);
-  const int vw = (threadIdx.x >> 5) - kNH, lane = threadIdx.x & 31;
-  const int ncols = min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
-  const int rowe = jd.OW * Cl::C;
-  T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)G.ox0 * Cl::C;
-  const int rbase = (int)((g * Cl::SR) & Cl::RING_MASK);  // ring row of the tile's first row
-  for (int k = 0; k < G.nst; ++k, ++g) {
-    if (!__all_sync(0xffffffffu, mbar_wait(&hdone[g % kNRS], (g / kNRS) & 1u, abort_flag))) return false;
-    int m_lo, m_hi;
-    ready_blocks<Cl>(G, k, m_lo, m_hi);
-    // one (block, phase) pair per warp at a time, so the phase -- and with it
-    // the compiled tap sequence -- is uniform across the warp; lanes take
-    // groups of 4 columns (groups past the frame's right edge are skipped)
-    constexpr int TPR = Cl::SOE / 4;
-    const int npairs = (m_hi - m_lo + 1) * Cl::P;
-    for (int pair = vw; pair < npairs; pair += kNV) {
-      const int mb = pair / Cl::P, j = pair - mb * Cl::P;
-      const int r = G.rb0 + m_lo + mb;
-      const int oy = r * Cl::P + j;
-      if (oy >= jd.OH) continue;
-      T* const orow = obase + (long long)oy * rowe;
-      for (int grp = lane; grp < TPR; grp += 32) {
-        const int e0 = grp * 4;
-        if (e0 >= ncols) break;
-        vtask_phase<Cl, 0>(j, jd, G, taps, ring, rbase, r, e0, orow + e0, ncols - e0);
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&vdone[g % kNRS]);
-  }
-  return true;
-}
-
-// ---------------------------------------------------------------------------
-// class dispatch and the kernel
-// ---------------------------------------------------------------------------
-template <class... Cs>
-struct Dispatch;
-template <>
-struct Dispatch<> {
-  template <class F>
-  __device__ static bool run(int, F&&) { return false; }
-};
-template <class C0, class... Rest>
-struct Dispatch<C0, Rest...> {
-  template <class F>
-  __device__ static bool run(int cls, F&& f) {
-    if (cls == C0::id) return f(C0{});
-    return Dispatch<Rest...>::run(cls, f);
-  }
-};
-
-template <int NSTAGE, class... Cs>
-struct KernelShape {
-  static constexpr int STAGE_MAX = cmax(Cs::STAGE_BYTES...);
-  static constexpr int RING_MAX = cmax(Cs::RING_BYTES...);
-  static constexpr int BAR_OFF = NSTAGE * STAGE_MAX + RING_MAX;
-  static constexpr int SMEM = 128 + BAR_OFF + (2 * NSTAGE + 2 * kNRS) * 8 + 16;
-};
-
-// MINB: resident CTAs per SM the registers are budgeted for (2 for the
-// single-class kernels; 1 for the all-class kernel, whose union of code paths
-// needs more registers).
-template <int NSTAGE, int MINB, class... Cs>
-__global__ void __launch_bounds__(kThreads, MINB) k_fused_tma(const __grid_constant__ FastParams prm) {
-  using KS = KernelShape<NSTAGE, Cs...>;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint8_t* stages = smem;
-  uint8_t* ring = smem + NSTAGE * KS::STAGE_MAX;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + KS::BAR_OFF);
-  uint64_t* empty = full + NSTAGE;
-  uint64_t* hdone = empty + NSTAGE;
-  uint64_t* vdone = hdone + kNRS;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(vdone + kNRS);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kNH);
-    }
-    for (int s = 0; s < kNRS; ++s) {
-      mbar_init(&hdone[s], kNH);
-      mbar_init(&vdone[s], kNV);
-    }
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
-
-  if (warp == kNWC) {
-    // ------------------------------- producer
-    if (lane != 0) return;
-    uint32_t g = 0;
-    bool ok = true;
-    for (int t = blockIdx.x; ok && t < prm.total_tiles; t += gridDim.x) {
-      const Tile tl = decode_tile(prm, t);
-      const JobDesc& jd = prm.jobs[tl.job];
-      ok = Dispatch<Cs...>::run(jd.cls, [&](auto cl) {
-        return produce_tile<decltype(cl), NSTAGE, KS::STAGE_MAX>(jd, tl, stages, full, empty, g, abort_flag);
-      });
-    }
-    if (!ok) {
-      // leave no copy in flight: wait (bounded) for the last round of each slot
-      *abort_flag = 1;
-      atomicCAS(&g_fast_status, 0, kStatusTimeout);
-      for (uint32_t s = 0; s < NSTAGE && s < g; ++s) {
-        const uint32_t last = g - 1 - s;
-        mbar_wait(&full[last % NSTAGE], (last / NSTAGE) & 1u, nullptr);
-      }
-    }
-    return;
-  }
-
-  // --------------------------------- consumers: H warps and V warps
-  uint32_t g = 0;
-  int prev_cls = -1;
-  for (int t = blockIdx.x; t < prm.total_tiles; t += gridDim.x) {
-    const Tile tl = decode_tile(prm, t);
-    const JobDesc& jd = prm.jobs[tl.job];
-    int code = kStatusBadClass;
-    const bool changed = prev_cls >= 0 && prev_cls != jd.cls;
-    prev_cls = jd.cls;
-    const bool ok = Dispatch<Cs...>::run(jd.cls, [&](auto cl) {
-      code = kStatusTimeout;
-      if (warp < kNH)
-        return h_tile<decltype(cl), NSTAGE, KS::STAGE_MAX>(prm, jd, tl, stages, ring, full, empty, hdone, vdone, g,
-                                                         changed, abort_flag);
-      return v_tile<decltype(cl)>(prm, jd, tl, ring, hdone, vdone, g, abort_flag);
-    });
-    if (!ok) {
-      if (lane == 0) {
-        *abort_flag = 1;
-        atomicCAS(&g_fast_status, 0, code);
-      }
-      return;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
 // row-streaming kernel: one self-contained pipeline per warp
 // ---------------------------------------------------------------------------
-// Each warp owns a tile (a strip of 32*NB packets x a band of output row
-// blocks of one frame) and runs the whole filter on it by itself:
-//   lane 0 issues TMA loads of SR input rows (plus the strip's halo) into the
-//   warp's private ring of NST stages, each stage with its own mbarrier;
-//   every input row goes through the horizontal pass in registers and lands
-//   in a sliding window of the last L filtered rows, also in registers
-//   (L rows x NOUT values per lane: the intermediate never leaves the SM);
-//   each time Q new rows have entered the window, the warp computes the P
-//   output rows of one block from the window and stores them.
 // Rows above / below the frame are never loaded: their window slots take a
 // copy of the first / last filtered row (clamp-to-edge); columns outside the
-// frame are fixed up in shared memory as in the other kernel.  Warps
-// synchronise with nothing but their own TMA completions.
-__host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
-
-template <class B, int SR_, int NST_>
-struct RCls : B {
-  static constexpr int SRR = SR_;                          // input rows per stage
-  static constexpr int NST = NST_;                         // stages per warp
-  static constexpr int BOXSTR = rup(SR_ * B::BOXB, 128);   // (hides the base's stage layout)
-  static constexpr int RSTAGE = B::NBOX * BOXSTR;
-  static constexpr int RTX = B::NBOX * SR_ * B::BOXB;      // TMA bytes per stage
-  static constexpr int WARP_BYTES = NST_ * RSTAGE;
-  static constexpr bool ROT = false;                       // bank rotation off: the selects cost more here
-  // The stream of a tile is cut so that the window prologue (the first L-Q
-  // pattern rows) fills whole stages, EXTRA rows being loaded before the first
-  // pattern row; after it, every group of U = lcm(SR, Q) rows is USTG stages
-  // and UBLK block steps, so each row's stage offset and window slot are
-  // compile-time constants.
-  static constexpr int PRE = B::L - B::Q;
-  static constexpr int NPS = cdiv(PRE, SR_);
-  static constexpr int EXTRA = NPS * SR_ - PRE;
-  static constexpr int U = SR_ / cgcd(SR_, B::Q) * B::Q;
-  static constexpr int USTG = U / SR_;
-  static constexpr int UBLK = U / B::Q;
-  static_assert(B::WX == 1, "one warp per strip");
-  static_assert(PRE > B::LH, "the window prologue must reach frame row 0");
-  static_assert(B::L * (sizeof(typename B::T) == 1 ? (B::NOUT + 3) / 4 : B::NOUT) <= 48,
-                "register window too large");
-  static_assert(U <= 16, "iteration unit too long to unroll");
-};
-
-//                 base class   SR NST
-using RF32_38 = RCls<CF32_38, 4, 3>;
-using RF32_12 = RCls<CF32_12, 4, 3>;
-using RF32_23 = RCls<CF32_23, 6, 3>;
-using RF16_38 = RCls<CF16_38, 4, 3>;
-using RF16_12 = RCls<CF16_12, 4, 3>;
-using RF16_23 = RCls<CF16_23, 6, 3>;
-// uint8 RGB (integer row math): one warp per strip, chunks of whole words
-using CU8_38r = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 1, 8, 4>;
-using CU8_12r = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 1, 8, 4>;
-using CU8_23r = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 1, 8, 4>;
-using RU8_38 = RCls<CU8_38r, 4, 3>;
-using RU8_12 = RCls<CU8_12r, 4, 3>;
-using RU8_23 = RCls<CU8_23r, 3, 3>;
+// frame are fixed up in shared memory.  Warps synchronise with nothing but
+// their own TMA completions.
 
 // Store n_valid (<= N) consecutive output values with the widest aligned stores.
 template <typename T, int N>
@@ -1200,15 +679,18 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
   const Offs<Cl> of = thread_offs<Cl>(lane);
   const unsigned nwarps = gridDim.x * WPC;
   unsigned* const next = &g_tile_next[prm.sched_slot];
+  // the first tile of every warp is its warp index (so the launch does not
+  // start with every warp hitting one counter); later ones come from the
+  // counter, offset by the number of warps
   auto next_tile = [&]() -> int {
     unsigned t = 0;
-    if (lane == 0) t = atomicAdd(next, 1u);
+    if (lane == 0) t = nwarps + atomicAdd(next, 1u);
     return (int)__shfl_sync(0xffffffffu, t, 0);
   };
   uint32_t g = 0;       // this warp's stage counter over all its tiles (mbarrier phases)
   uint32_t issued = 0;  // one past the last stage issued
   bool ok = true;
-  for (int t = next_tile(); ok && t < prm.total_tiles; t = next_tile()) {
+  for (int t = (int)(blockIdx.x * WPC + warp); ok && t < prm.total_tiles; t = next_tile()) {
     const Tile tl = decode_tile(prm, t);
     const JobDesc& jd = prm.jobs[tl.job];
     if (jd.cls != Cl::id) {
@@ -1223,7 +705,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     const int nst = Cl::NPS + (nblk * Q + SR - 1) / SR;
     const int ystream = ys - Cl::EXTRA;  // frame row of stage 0's first row
     const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
-    const EdgeFix fix = edge_fix<Cl>(tl.strip, 0, jd.W);
+    const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
     const bool fixing = fix.nl + fix.nr > 0;
     const int blk0 = tl.strip * Cl::SBLK + lane * Cl::NB;
     const bool active = blk0 * P < jd.OW;
@@ -1245,7 +727,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     // wait for stage s; returns the stage's row-0 base, or nullptr on timeout
     auto stage_wait = [&](int s) -> uint8_t* {
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (G / NST) & 1u, nullptr))) return nullptr;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (G / NST) & 1u))) return nullptr;
       return ring + slot * Cl::RSTAGE;
     };
     // stage s fully read: refill its slot with stage s + NST
@@ -1338,7 +820,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     if (lane == 0) {
       atomicCAS(&g_fast_status, 0, kStatusTimeout);
       for (uint32_t G = (issued > (uint32_t)NST ? issued - NST : 0); G < issued; ++G)
-        mbar_wait(&full[G % NST], (G / NST) & 1u, nullptr);
+        mbar_wait(&full[G % NST], (G / NST) & 1u);
     }
   }
   // the last warp out resets the slot for its next launch
@@ -1356,43 +838,27 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
 // host side
 // ---------------------------------------------------------------------------
 struct HostGeom {
-  int sblk, spx, p, q, boxe, sr, sz, c, ve;
+  int sblk, spx, p, q, boxe, sr, sz, c;
   CUtensorMapDataType dt;
 };
 
 template <class Cl>
 HostGeom host_geom() {
-  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::BOXE, Cl::SR, Cl::SZ, Cl::C, Cl::VE, TmaType<typename Cl::T>::v};
-}
-template <class Cl>
-HostGeom host_geom_rows() {
-  HostGeom g = host_geom<Cl>();
-  g.sr = Cl::SRR;
-  return g;
-}
-
-// Classes with a row-streaming kernel (their register window fits).
-bool has_rows_kernel(int cls) {
-  switch (cls) {
-    case kFcF32_38: case kFcF32_12: case kFcF32_23:
-    case kFcF16_38: case kFcF16_12: case kFcF16_23:
-    case kFcU8C3_38: case kFcU8C3_12: case kFcU8C3_23: return true;
-    default: return false;
-  }
+  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, TmaType<typename Cl::T>::v};
 }
 
 // Geometry of the kernel that runs class `cls`.
 HostGeom geom_of(int cls) {
   switch (cls) {
-    case kFcF32_38: return host_geom_rows<RF32_38>();
-    case kFcF32_12: return host_geom_rows<RF32_12>();
-    case kFcF32_23: return host_geom_rows<RF32_23>();
-    case kFcF16_38: return host_geom_rows<RF16_38>();
-    case kFcF16_12: return host_geom_rows<RF16_12>();
-    case kFcF16_23: return host_geom_rows<RF16_23>();
-    case kFcU8C3_38: return host_geom_rows<RU8_38>();
-    case kFcU8C3_12: return host_geom_rows<RU8_12>();
-    default: return host_geom_rows<RU8_23>();
+    case kFcF32_38: return host_geom<RF32_38>();
+    case kFcF32_12: return host_geom<RF32_12>();
+    case kFcF32_23: return host_geom<RF32_23>();
+    case kFcF16_38: return host_geom<RF16_38>();
+    case kFcF16_12: return host_geom<RF16_12>();
+    case kFcF16_23: return host_geom<RF16_23>();
+    case kFcU8C3_38: return host_geom<RU8_38>();
+    case kFcU8C3_12: return host_geom<RU8_12>();
+    default: return host_geom<RU8_23>();
   }
 }
 
@@ -1414,13 +880,6 @@ struct KernelInfo {
   int smem;
   int threads;
 };
-
-template <int NSTAGE, class... Cs>
-KernelInfo kernel_info() {
-  constexpr int minb = sizeof...(Cs) == 1 ? 2 : 1;
-  return KernelInfo{reinterpret_cast<const void*>(&k_fused_tma<NSTAGE, minb, Cs...>), KernelShape<NSTAGE, Cs...>::SMEM,
-                    kThreads};
-}
 
 constexpr int kRowsWPC = 4;  // warps (independent pipelines) per CTA of the row-streaming kernel
 
@@ -1551,130 +1010,81 @@ ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
   return DS_OK;
 }
 
-// Band height for the jobs of one launch.  A tile is processed serially by
-// one warp (row kernel) or CTA, so a launch with fewer band-rows of work than
-// the GPU has pipelines finishes sooner with shorter bands: the band is cut
-// to ceil(block rows of work / pipelines), never above the plans' own value.
-// Plans with a caller-set (or autotuned) schedule keep theirs.
-int launch_band(const FastJob* jobs, int n, int pipelines) {
+// Band heights (output row blocks per tile) of the jobs of one launch.  A
+// tile is processed serially by one warp, and tiles are handed out in job
+// order, so:
+//  - a launch with fewer block rows of work than the GPU has pipelines
+//    finishes sooner with shorter bands: the band is cut to
+//    ceil(block rows / pipelines), never above the plans' own value;
+//  - the launch ends when the last warp finishes its last tile, so the work
+//    at the end (about two tiles per pipeline) runs at a quarter of the band,
+//    the last job being split by frames where the boundary falls inside it.
+// Plans with a caller-set (or autotuned) schedule keep theirs, unsplit.
+struct BandedJob {
+  FastJob job;
+  int band;  // 0 = the plan's
+};
+
+int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
+  std::vector<long long> per_frame(n);
   long long units = 0;
   int cap = 0;
+  bool fixed = false;
   for (int i = 0; i < n; ++i) {
     const ds_plan* pl = jobs[i].plan;
-    if (pl->schedule_set) return 0;
+    fixed = fixed || pl->schedule_set;
     const HostGeom hg = geom_of(pl->fast_class);
     const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.p - 1) / hg.p;
-    units += (nbx + hg.sblk - 1) / hg.sblk * nby * (long long)jobs[i].n_frames;
+    per_frame[i] = (nbx + hg.sblk - 1) / hg.sblk * nby;
+    units += per_frame[i] * jobs[i].n_frames;
     cap = std::max(cap, pl->row_blocks);
   }
-  const long long fill = (units + pipelines - 1) / std::max(1, pipelines);
-  return (int)std::max<long long>(1, std::min<long long>(cap, fill));
+  if (fixed) {
+    for (int i = 0; i < n; ++i) out[i] = BandedJob{jobs[i], 0};
+    return n;
+  }
+  pipelines = std::max(1, pipelines);
+  const int band = (int)std::max<long long>(1, std::min<long long>(cap, (units + pipelines - 1) / pipelines));
+  const int tail_band = std::max(1, band / 4);
+  for (int i = 0; i < n; ++i) out[i] = BandedJob{jobs[i], band};
+  if (band < 4) return n;
+  const long long target = 2ll * pipelines * tail_band;
+  long long acc = 0;
+  int count = n;
+  for (int i = n - 1; i >= 0 && acc < target; --i) {
+    const long long whole = per_frame[i] * jobs[i].n_frames;
+    if (acc + whole <= target || jobs[i].n_frames < 2) {
+      out[i].band = tail_band;
+      acc += whole;
+      continue;
+    }
+    const int k = (int)std::min<long long>(jobs[i].n_frames - 1, (target - acc + per_frame[i] - 1) / per_frame[i]);
+    if (count + 1 > kMaxJobs) break;
+    size_t fin = 0, fout = 0;
+    ds_plan_frame_bytes(jobs[i].plan, &fin, &fout);
+    const int head = jobs[i].n_frames - k;
+    for (int m = count; m > i + 1; --m) out[m] = out[m - 1];
+    out[i] = BandedJob{FastJob{jobs[i].plan, jobs[i].in, jobs[i].out, head}, band};
+    out[i + 1] = BandedJob{FastJob{jobs[i].plan, static_cast<const uint8_t*>(jobs[i].in) + (size_t)head * fin,
+                                   static_cast<uint8_t*>(jobs[i].out) + (size_t)head * fout, k},
+                           tail_band};
+    ++count;
+    break;
+  }
+  return count;
 }
 
 // ---------------------------------------------------------------------------
 // host-side check of the kernel's index arithmetic
 // ---------------------------------------------------------------------------
-// Walks every tile of one frame the way the kernel does and checks: TMA x
-// coordinates are 16-byte aligned; every shared-memory read of the H pass
-// (vector chunks, halo words, clamped border reads) stays inside the loaded
-// window and never straddles a box; ring writes stay inside a ring row;
-// every ring row the V pass reads was written by the H pass of an earlier or
-// the same stage and is not overwritten by the next stage's H pass; every
-// output element is written exactly once; the shared-memory footprint fits.
-template <class Cl, int STAGE_MAX, int SMEM>
-std::string check_class(const JobDesc& jd) {
-  char buf[256];
-  auto fail = [&](const char* what, int a, int b) {
-    std::snprintf(buf, sizeof(buf), "class %d: %s (%d, %d)", Cl::id, what, a, b);
-    return std::string(buf);
-  };
-  if (SMEM > 227 * 1024) return fail("shared memory above 227 KB", SMEM, 0);
-  if (Cl::STAGE_BYTES > STAGE_MAX || Cl::BOXSTR < Cl::SR * Cl::BOXB) return fail("stage layout", Cl::STAGE_BYTES, STAGE_MAX);
-  const int win = Cl::NBOX * Cl::BOXB;
-  std::vector<int> written((size_t)jd.OH * jd.OW * Cl::C, 0);
-  for (int chunk = 0; chunk < jd.chunks; ++chunk) {
-    for (int strip = 0; strip < jd.strips; ++strip) {
-      const Tile tl{0, 0, strip, chunk};
-      const Geo G = tile_geo<Cl>(jd, tl);
-      if (G.nblk < 1 || G.ox0 >= jd.OW) return fail("empty tile", chunk, strip);
-      for (int bx = 0; bx < Cl::NBOX; ++bx) {
-        const long long xb = (long long)(G.xw + bx * Cl::BOXE) * Cl::SZ;
-        if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", G.xw, bx);
-      }
-      for (int wx = 0; wx < Cl::WX; ++wx) {
-        const EdgeFix fx = edge_fix<Cl>(strip, wx, jd.W);
-        // fix-up sources and destinations stay in the window
-        for (int e = 0; e < fx.nl + fx.nr; ++e) {
-          const bool left = e < fx.nl;
-          const int k2 = left ? e : e - fx.nl;
-          const int px = (left ? fx.l_lo : fx.r_lo) + k2 / Cl::C, c = k2 % Cl::C;
-          const int src = (left ? 0 : jd.W - 1) * Cl::C + c - G.xw, dst = px * Cl::C + c - G.xw;
-          if (src < 0 || (src + 1) * Cl::SZ > win || dst < 0 || (dst + 1) * Cl::SZ > win)
-            return fail("edge fix outside the window", src, dst);
-          if (px >= 0 && px < jd.W) return fail("edge fix inside the frame", px, jd.W);
-        }
-        for (int lane = 0; lane < 32; ++lane) {
-          const int lg = wx * 32 + lane;
-          const int first = Cl::HLB + lg * Cl::EB - Cl::HB * Cl::VB;
-          for (int v = 0; v < Cl::NVT; ++v) {
-            const int b0 = first + v * Cl::VB;
-            if (b0 < 0 || b0 + Cl::VB > win || b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB)
-              return fail("vector read", lg, b0);
-          }
-          const int blk0 = strip * Cl::SBLK + lg * Cl::NB;
-          const int px0 = blk0 * Cl::Q;
-          if (blk0 * Cl::P >= jd.OW) continue;  // inactive lane: loads only
-          // element e of the thread (pixel px0 - LH + e/C) sits at window element px*C + c - xw
-          const int el0 = (px0 - Cl::LH) * Cl::C - G.xw;
-          if (el0 * Cl::SZ != first + Cl::HB * Cl::VB - Cl::LH * Cl::C * Cl::SZ) return fail("chunk not at its pixels", lg, el0);
-          for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
-            if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lg, px);
-            if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lg, px);
-          }
-          if (lg * Cl::NOUT + Cl::NOUT > Cl::SOE) return fail("ring write", lg, Cl::SOE);
-        }
-      }
-      // ring rule: the V pass of stage k may read only rows the H pass wrote in
-      // stages k-D..k (the H pass of stage k+kNRS-D overwrites stage k-D)
-      std::vector<int> done(G.nblk, 0);
-      for (int k = 0; k < G.nst; ++k) {
-        int m_lo, m_hi;
-        ready_blocks<Cl>(G, k, m_lo, m_hi);
-        for (int m = m_lo; m <= m_hi; ++m) {
-          if (m < 0 || m >= G.nblk || done[m]) return fail("block scheduled twice or out of range", m, k);
-          done[m] = 1;
-          const int r = G.rb0 + m;
-          for (int i = 0; i < Cl::L; ++i) {
-            int yc = r * Cl::Q + Cl::BMIN + i;
-            yc = yc < 0 ? 0 : (yc > jd.H - 1 ? jd.H - 1 : yc);
-            const int rel = yc - G.ys;
-            if (rel < 0 || rel >= G.rows) return fail("V row outside the tile", rel, G.rows);
-            const int st = rel / Cl::SR;
-            if (st > k) return fail("V row not yet written", rel, k);
-            if (k - st > Cl::D) return fail("V row older than the ring keeps", rel, k);
-          }
-          const int ncols = std::min(Cl::SOE, (jd.OW - G.ox0) * Cl::C);
-          for (int j = 0; j < Cl::P; ++j) {
-            const int oy = r * Cl::P + j;
-            if (oy >= jd.OH) break;
-            for (int e = 0; e < ncols; ++e) written[((size_t)oy * jd.OW + G.ox0) * Cl::C + e]++;
-          }
-        }
-      }
-      for (int m = 0; m < G.nblk; ++m)
-        if (!done[m]) return fail("block never scheduled", m, chunk);
-    }
-  }
-  for (size_t i = 0; i < written.size(); ++i)
-    if (written[i] != 1) return fail("output element written != 1 times", (int)i, written[i]);
-  return std::string();
-}
-
-// Host-side walk of the row-streaming kernel: the same TMA / window / edge
-// checks as above, plus a replay of its stream and register-window logic on
-// frame-row indices -- every V block must see exactly the clamped rows of
-// its window, every stream row must be the next frame row in order, every
-// output element is written once.
+// Host-side walk of the row-streaming kernel over every tile of one frame:
+// TMA x coordinates are 16-byte aligned; every shared-memory read of the H
+// pass (vector chunks, halo words, clamped border pixels) stays inside the
+// loaded window and never straddles a box; the shared-memory footprint fits;
+// a replay of the stream and register-window logic on frame-row indices --
+// every V block must see exactly the clamped rows of its window, every
+// stream row must be the next frame row in order, every output element is
+// written once.
 template <class Cl, int WPC>
 std::string check_rows(const JobDesc& jd) {
   char buf[256];
@@ -1704,7 +1114,7 @@ std::string check_rows(const JobDesc& jd) {
         const long long xb = (long long)(xw + bx * Cl::BOXE) * Cl::SZ;
         if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", xw, bx);
       }
-      const EdgeFix fx = edge_fix<Cl>(strip, 0, jd.W);
+      const EdgeFix fx = edge_fix<Cl>(strip, jd.W);
       for (int e = 0; e < fx.nl + fx.nr; ++e) {
         const bool left = e < fx.nl;
         const int k2 = left ? e : e - fx.nl;
@@ -1795,49 +1205,22 @@ std::string check_rows(const JobDesc& jd) {
   return std::string();
 }
 
-template <int NSTAGE, class Cl>
-std::string check_single(const JobDesc& jd) {
-  using KS = KernelShape<NSTAGE, Cl>;
-  return check_class<Cl, KS::STAGE_MAX, KS::SMEM>(jd);
-}
-
-template <class Cl>
-std::string check_mixed(const JobDesc& jd) {
-  using KS = KernelShape<3, CF32_38, CF32_12, CF32_23, CF16_38, CF16_12, CF16_23, CU8_38, CU8_12, CU8_23>;
-  return check_class<Cl, KS::STAGE_MAX, KS::SMEM>(jd);
-}
-
 std::string check_plan(const ds_plan* pl) {
   JobDesc jd;
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);
-  std::string a, b;
-  if (has_rows_kernel(pl->fast_class)) {
-    switch (pl->fast_class) {
-      case kFcF32_38: return check_rows<RF32_38, kRowsWPC>(jd);
-      case kFcF32_12: return check_rows<RF32_12, kRowsWPC>(jd);
-      case kFcF32_23: return check_rows<RF32_23, kRowsWPC>(jd);
-      case kFcF16_38: return check_rows<RF16_38, kRowsWPC>(jd);
-      case kFcF16_12: return check_rows<RF16_12, kRowsWPC>(jd);
-      case kFcF16_23: return check_rows<RF16_23, kRowsWPC>(jd);
-      case kFcU8C3_38: return check_rows<RU8_38, kRowsWPC>(jd);
-      case kFcU8C3_12: return check_rows<RU8_12, kRowsWPC>(jd);
-      default: return check_rows<RU8_23, kRowsWPC>(jd);
-    }
-  }
   switch (pl->fast_class) {
-    case kFcF32_38: a = check_single<4, CF32_38>(jd); b = check_mixed<CF32_38>(jd); break;
-    case kFcF32_12: a = check_single<4, CF32_12>(jd); b = check_mixed<CF32_12>(jd); break;
-    case kFcF32_23: a = check_single<4, CF32_23>(jd); b = check_mixed<CF32_23>(jd); break;
-    case kFcF16_38: a = check_single<6, CF16_38>(jd); b = check_mixed<CF16_38>(jd); break;
-    case kFcF16_12: a = check_single<6, CF16_12>(jd); b = check_mixed<CF16_12>(jd); break;
-    case kFcF16_23: a = check_single<6, CF16_23>(jd); b = check_mixed<CF16_23>(jd); break;
-    case kFcU8C3_38: a = check_single<8, CU8_38>(jd); b = check_mixed<CU8_38>(jd); break;
-    case kFcU8C3_12: a = check_single<8, CU8_12>(jd); b = check_mixed<CU8_12>(jd); break;
-    case kFcU8C3_23: a = check_single<4, CU8_23>(jd); b = check_mixed<CU8_23>(jd); break;
+    case kFcF32_38: return check_rows<RF32_38, kRowsWPC>(jd);
+    case kFcF32_12: return check_rows<RF32_12, kRowsWPC>(jd);
+    case kFcF32_23: return check_rows<RF32_23, kRowsWPC>(jd);
+    case kFcF16_38: return check_rows<RF16_38, kRowsWPC>(jd);
+    case kFcF16_12: return check_rows<RF16_12, kRowsWPC>(jd);
+    case kFcF16_23: return check_rows<RF16_23, kRowsWPC>(jd);
+    case kFcU8C3_38: return check_rows<RU8_38, kRowsWPC>(jd);
+    case kFcU8C3_12: return check_rows<RU8_12, kRowsWPC>(jd);
+    case kFcU8C3_23: return check_rows<RU8_23, kRowsWPC>(jd);
     default: return std::string();
   }
-  return a.empty() ? b : a;
 }
 
 ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
@@ -1854,17 +1237,17 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
     return DS_ERR_UNSUPPORTED;
   }
   if (want_ctas > 0) occ = std::min(occ, want_ctas);
-  // the row-streaming kernel runs one tile per warp, the other one per CTA
-  const int per_cta = has_rows_kernel(cls) ? ki.threads / 32 : 1;
-  const int band = launch_band(jobs, n, sm_count() * occ * per_cta);
+  const int per_cta = ki.threads / 32;  // one tile per warp
+  BandedJob banded[kMaxJobs];
+  const int nb = plan_bands(jobs, n, sm_count() * occ * per_cta, banded);
   int tiles = 0;
-  for (int i = 0; i < n; ++i) {
-    ds_status s = encode_job(prm.jobs[i], jobs[i], band);
+  for (int i = 0; i < nb; ++i) {
+    ds_status s = encode_job(prm.jobs[i], banded[i].job, banded[i].band);
     if (s != DS_OK) return s;
     prm.jobs[i].tile_begin = tiles;
     tiles += prm.jobs[i].tiles;
   }
-  prm.n_jobs = n;
+  prm.n_jobs = nb;
   prm.total_tiles = tiles;
   static std::atomic<unsigned> slot_counter{0};
   prm.sched_slot = (int)(slot_counter.fetch_add(1) % kSchedSlots);
@@ -1872,7 +1255,7 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   const int grid = std::min((tiles + per_cta - 1) / per_cta, sm_count() * occ);
   void* args[] = {&prm};
   cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, (size_t)ki.smem, st);
-  if (e != cudaSuccess) return cuda_fail(e, "k_fused_tma launch");
+  if (e != cudaSuccess) return cuda_fail(e, "k_rows launch");
   count_launches(1);
   return DS_OK;
 }

@@ -81,11 +81,9 @@ int default_row_blocks(int fast_class) {
   switch (fast_class) {
     case kFcF32_38: return 8;
     case kFcF16_38: return 10;
-    case kFcU8C3_38: return 12;
-    case kFcF32_12: case kFcF16_12: return 24;
-    case kFcU8C3_12: return 34;
-    case kFcF32_23: case kFcF16_23: return 16;
-    case kFcU8C3_23: return 24;
+    case kFcU8C3_38: return 16;
+    case kFcF32_12: case kFcF16_12: case kFcU8C3_12: return 24;
+    case kFcF32_23: case kFcF16_23: case kFcU8C3_23: return 20;
     default: return 0;
   }
 }
