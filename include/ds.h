@@ -235,7 +235,12 @@ typedef struct ds_graph ds_graph;
 /*
  * Capture ds_batch_run(jobs, n, .) into a CUDA graph and instantiate it; the
  * job pointers are baked in.  NULL on error.  ds_graph_launch replays it on
- * `stream` (one graph launch for the whole batch).
+ * `stream` (one graph launch for the whole batch; replays of one graph are
+ * serialised by CUDA).  Each captured fused launch holds one of 512 tile-
+ * scheduling slots until ds_graph_destroy, which must be called after the
+ * graph's launches have completed; DS_ERR_UNSUPPORTED (NULL) when live graphs
+ * hold all of them.  Direct launches share the other 512 slots round robin,
+ * so at most 512 fused launches may be in flight at once.
  */
 ds_graph* ds_graph_create(const ds_job* jobs, int n);
 ds_status ds_graph_launch(ds_graph* graph, void* stream);

@@ -59,6 +59,7 @@ struct ds_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long launches = 0;
+  std::vector<int> slots;  // tile-scheduling slots of the captured fused launches
 };
 
 struct ds_pipeline {
@@ -165,7 +166,9 @@ ds_graph* ds_graph_create(const ds_job* jobs, int n) {
   }
   ds_launch_count();  // the nodes captured below are counted for the graph
   e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  g_capture_slots = &g->slots;
   ds_status s = (e == cudaSuccess) ? run_jobs(jobs, n, st) : cuda_fail(e, "begin capture");
+  g_capture_slots = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(st, &g->graph);
   g->launches = ds_launch_count();
   cudaStreamDestroy(st);
@@ -196,6 +199,7 @@ void ds_graph_destroy(ds_graph* g) {
   if (!g) return;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  release_graph_slots(g->slots);
   delete g;
 }
 

@@ -47,9 +47,13 @@ __device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out; 2 = bad clas
 
 // Dynamic tile scheduling of the row-streaming kernel: launch slot s hands out
 // tiles from g_tile_next[s]; the last warp to finish puts both counters of
-// its slot back to zero.  Launches take slots in turn, so launches that can
-// overlap (different streams) use different counters.
+// its slot back to zero.  Direct launches take the slots below kGraphSlot0 in
+// turn, so launches that overlap (different streams) use different counters
+// unless kGraphSlot0 launches were issued while one of them ran; launches
+// captured into a CUDA graph own a slot above it until the graph is
+// destroyed (replays of one graph are serialised by CUDA).
 constexpr int kSchedSlots = 1024;
+constexpr int kGraphSlot0 = 512;
 __device__ unsigned int g_tile_next[kSchedSlots];
 __device__ unsigned int g_warps_done[kSchedSlots];
 
@@ -1223,6 +1227,20 @@ std::string check_plan(const ds_plan* pl) {
   }
 }
 
+// Scheduling slots owned by live graphs.
+std::mutex g_slot_mu;
+bool g_slot_used[kSchedSlots - kGraphSlot0] = {};
+
+int take_graph_slot() {
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  for (int i = 0; i < kSchedSlots - kGraphSlot0; ++i)
+    if (!g_slot_used[i]) {
+      g_slot_used[i] = true;
+      return kGraphSlot0 + i;
+    }
+  return -1;
+}
+
 ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   static thread_local FastParams prm;  // ~13 KB, too large for the stack of some callers
   std::memset(&prm, 0, sizeof(prm));
@@ -1249,9 +1267,19 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   }
   prm.n_jobs = nb;
   prm.total_tiles = tiles;
-  static std::atomic<unsigned> slot_counter{0};
-  prm.sched_slot = (int)(slot_counter.fetch_add(1) % kSchedSlots);
   if (tiles == 0) return DS_OK;
+  if (g_capture_slots) {
+    const int slot = take_graph_slot();
+    if (slot < 0) {
+      set_error("more than %d fused launches held by live CUDA graphs", kSchedSlots - kGraphSlot0);
+      return DS_ERR_UNSUPPORTED;
+    }
+    g_capture_slots->push_back(slot);
+    prm.sched_slot = slot;
+  } else {
+    static std::atomic<unsigned> slot_counter{0};
+    prm.sched_slot = (int)(slot_counter.fetch_add(1) % kGraphSlot0);
+  }
   const int grid = std::min((tiles + per_cta - 1) / per_cta, sm_count() * occ);
   void* args[] = {&prm};
   cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, (size_t)ki.smem, st);
@@ -1263,6 +1291,14 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
 }  // namespace
 
 int fast_max_jobs_per_launch() { return kMaxJobs; }
+
+thread_local std::vector<int>* g_capture_slots = nullptr;
+
+void release_graph_slots(const std::vector<int>& slots) {
+  std::lock_guard<std::mutex> lock(g_slot_mu);
+  for (int s : slots)
+    if (s >= kGraphSlot0 && s < kSchedSlots) g_slot_used[s - kGraphSlot0] = false;
+}
 
 // One launch per class present (each kernel is specialised for its class),
 // at most kMaxJobs descriptors per launch.

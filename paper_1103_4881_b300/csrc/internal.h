@@ -80,6 +80,11 @@ struct FastJob {
   int n_frames;
 };
 ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t stream);
+// While non-null (on this thread), fused launches are being captured into a
+// CUDA graph: each takes a scheduling slot of its own and records it here, to
+// be given back with release_graph_slots when the graph is destroyed.
+extern thread_local std::vector<int>* g_capture_slots;
+void release_graph_slots(const std::vector<int>& slots);
 int fast_max_jobs_per_launch();
 ds_status read_device_status(int* status);  // reads and clears the status word
 ds_status debug_check_plan(const ds_plan* plan, std::string& msg);

@@ -226,3 +226,34 @@ def test_zero_frames_and_stream_check():
         ds.ds_stream_check(stream())
     finally:
         ds.ds_destroy(pl)
+
+
+def test_graphs_and_direct_launches_on_several_streams(oracle):
+    """Replays of two graphs and direct launches on three streams at once: each
+    captured launch owns its tile-scheduling slot, so none disturbs another."""
+    import torch
+
+    H, W = 270, 480
+    pl = ds.ds_plan_create(H, W, (3, 8), 8, ds.DS_F32)
+    try:
+        xs = [frames((H, W), ds.DS_F32, 3, 40 + k) for k in range(3)]
+        want = [run_fused(pl, x) for x in xs]
+        ins = [to_dev(x) for x in xs]
+        outs = [out_buffer(pl, 3) for _ in xs]
+        graphs = [ds.ds_graph_create([(pl, ins[k].data_ptr(), outs[k].data_ptr(), 3)]) for k in range(2)]
+        streams = [torch.cuda.Stream() for _ in range(3)]
+        torch.cuda.synchronize()
+        try:
+            for _ in range(20):
+                ds.ds_graph_launch(graphs[0], streams[0].cuda_stream)
+                ds.ds_graph_launch(graphs[1], streams[1].cuda_stream)
+                ds.ds_run_frames(pl, ins[2].data_ptr(), outs[2].data_ptr(), 3, streams[2].cuda_stream)
+            finish()
+        finally:
+            for g in graphs:
+                ds.ds_graph_destroy(g)
+        for k in range(3):
+            np.testing.assert_array_equal(outs[k].cpu().numpy(), want[k], err_msg="stream %d" % k)
+        assert_parity(want[0], oracle_out(oracle, xs[0], 3, 8, 8, ds.DS_F32), ds.DS_F32)
+    finally:
+        ds.ds_destroy(pl)
