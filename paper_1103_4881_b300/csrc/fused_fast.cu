@@ -15,7 +15,7 @@
 //     the phase taps (kernel parameters, i.e. constant-bank operands);
 //   the results enter a sliding window of the last L filtered rows, also in
 //     registers, so the intermediate never leaves the SM (the paper's
-//     Sec. 3.B.4 removes host round trips between the two filters; this
+//     Sec. 3.B.3 removes host round trips between the two filters; this
 //     removes the device-memory round trip as well);
 //   each time q new rows have entered the window, the warp computes the p
 //     output rows of one block from it and stores them.

@@ -4,7 +4,7 @@
 //  * k_fused_general: one CTA per output tile; the horizontal pass of the
 //    tile's input rows (plus the vertical halo) goes to shared memory, the
 //    vertical pass reads it there (paper Sec. 3: horizontal filter, then
-//    vertical filter; Sec. 3.B.4: no round trip for the intermediate).
+//    vertical filter; Sec. 3.B.3: no round trip for the intermediate).
 //  * k_hpass / k_vpass: the unfused two-kernel form with the intermediate in
 //    device memory (FP32 for float dtypes, uint8 for uint8).
 //
