@@ -216,6 +216,16 @@ ds_status ds_run_unfused_static(const ds_plan* plan, const void* in, void* out, 
 ds_status ds_stream_check(void* stream);
 
 /*
+ * Test of the timeout path: launch on `stream` one warp that waits, with the
+ * fused kernel's bounded wait, on an mbarrier that nothing completes (no
+ * copy is issued, no thread arrives).  After limit_cycles SM clock cycles
+ * (2.03e6 per ms at the B300's clock) it gives up and sets the device status
+ * word, so the next ds_stream_check returns DS_ERR_TIMEOUT and the context
+ * stays usable.  DS_ERR_ARG for a limit outside [0, 4e9].
+ */
+ds_status ds_debug_timeout_probe(long long limit_cycles, void* stream);
+
+/*
  * Host-only self-check of the fused kernel's tile schedule for this plan:
  * walks every tile of a frame with the kernel's own index arithmetic and
  * verifies that TMA coordinates are aligned, every shared-memory access

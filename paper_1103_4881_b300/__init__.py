@@ -33,6 +33,7 @@ ABI_SYMBOLS = (
     "ds_stream_check", "ds_debug_check_plan", "ds_graph_create", "ds_graph_launch", "ds_graph_destroy",
     "ds_pipeline_create", "ds_pipeline_run", "ds_pipeline_destroy", "ds_last_error", "ds_version",
     "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static", "ds_plan_autotune",
+    "ds_debug_timeout_probe",
 )
 
 
@@ -93,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "ds_static_workspace_bytes": (sz, []),
         "ds_plan_autotune": (i, [vp, vp, vp, i, vp, i, ip, ctypes.POINTER(ctypes.c_float)]),
         "ds_run_unfused_static": (i, [vp, vp, vp, i, vp]),
+        "ds_debug_timeout_probe": (i, [ctypes.c_longlong, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -190,6 +192,12 @@ def ds_plan_autotune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream
     _check(lib().ds_plan_autotune(_ptr(plan), _ptr(in_ptr), _ptr(out_ptr), n_frames, _ptr(stream), iters,
                                   ctypes.byref(rb), ctypes.byref(us)))
     return rb.value, us.value
+
+
+def ds_debug_timeout_probe(limit_cycles: int, stream: int = 0) -> None:
+    """Launch a warp whose bounded wait runs out after limit_cycles (nothing
+    completes its barrier); the next ds_stream_check raises DS_ERR_TIMEOUT."""
+    _check(lib().ds_debug_timeout_probe(limit_cycles, _ptr(stream)))
 
 
 # ---------------------------------------------------------------------- running

@@ -144,6 +144,15 @@ ds_status ds_stream_check(void* stream) {
   return DS_OK;
 }
 
+ds_status ds_debug_timeout_probe(long long limit_cycles, void* stream) {
+  clear_error();
+  if (limit_cycles < 0 || limit_cycles > 4000000000ll) {
+    set_error("ds_debug_timeout_probe: limit of %lld cycles outside [0, 4e9]", limit_cycles);
+    return DS_ERR_ARG;
+  }
+  return launch_timeout_probe(limit_cycles, (cudaStream_t)stream);
+}
+
 // ------------------------------------------------------------------ graphs
 
 ds_graph* ds_graph_create(const ds_job* jobs, int n) {

@@ -209,16 +209,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase of `parity` to complete; false after about a second
-// (kWaitLimitCycles SM clock cycles, counted from the 4th failed poll).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete; false after `limit` SM clock
+// cycles (about a second by default), counted from the 4th failed poll.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitLimitCycles) {
 #pragma unroll 1
   for (int it = 0; it < 4; ++it)
     if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try(bar, parity)) return true;
-    if ((it & 3u) == 0 && clock64() - t0 > kWaitLimitCycles) return false;
+    if ((it & 3u) == 0 && clock64() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
@@ -838,6 +838,21 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
   }
 }
 
+// Exercise of the timeout path: one warp waits, with the kernels' bounded
+// wait, on an mbarrier that nothing will ever complete (no copy is issued
+// and no thread arrives), gives up after `limit` cycles and records the
+// timeout in the status word exactly as k_rows does.
+__global__ void k_timeout_probe(long long limit) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar, 0u, limit));
+  if (!ok && threadIdx.x == 0) atomicCAS(&g_fast_status, 0, kStatusTimeout);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1313,6 +1328,14 @@ ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
       if (s != DS_OK) return s;
     }
   }
+  return DS_OK;
+}
+
+ds_status launch_timeout_probe(long long limit_cycles, cudaStream_t st) {
+  k_timeout_probe<<<1, 32, 0, st>>>(limit_cycles);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "timeout probe launch");
+  count_launches(1);
   return DS_OK;
 }
 

@@ -87,6 +87,7 @@ extern thread_local std::vector<int>* g_capture_slots;
 void release_graph_slots(const std::vector<int>& slots);
 int fast_max_jobs_per_launch();
 ds_status read_device_status(int* status);  // reads and clears the status word
+ds_status launch_timeout_probe(long long limit_cycles, cudaStream_t stream);
 ds_status debug_check_plan(const ds_plan* plan, std::string& msg);
 
 // general.cu: any plan, any alignment.
