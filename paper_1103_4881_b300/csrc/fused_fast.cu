@@ -150,8 +150,8 @@ struct Cls {
 using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 4, 3>;
 using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3>;
 using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3>;
-using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 4, 3>;
-using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 4, 3>;
+using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3>;
+using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3>;
 using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3>;
 // uint8 RGB (integer row math)
 using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3>;
@@ -670,7 +670,10 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
   using Row = typename RM::Row;
   constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P, SR = Cl::SRR, NST = Cl::NST;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  // 128-byte aligned start, derived from the __shared__ array by an offset
+  // (not through an integer cast) so that every access stays a shared-memory
+  // access (ld.shared / st.shared), not a generic one
+  uint8_t* smem = smem_raw + ((128u - (saddr32(smem_raw) & 127u)) & 127u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* const ring = smem + warp * Cl::WARP_BYTES;
   uint64_t* const full = reinterpret_cast<uint64_t*>(smem + WPC * Cl::WARP_BYTES) + warp * NST;
