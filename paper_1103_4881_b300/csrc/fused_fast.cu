@@ -36,6 +36,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -88,11 +89,15 @@ struct TmaType<uint8_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP
 
 // A fast-path class: data type, channels, ratio P/Q, taps K, and the tile
 // shape -- NB packets (of Q input pixels) per lane and row, so a warp's strip
-// is 32*NB packets wide; SR input rows per pipeline stage, NST stages per warp.
-template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_>
+// is 32*NB packets wide; SR input rows per pipeline stage, NST stages per warp;
+// FP: whether interior units run a second, check-free copy of the loop body
+// (faster for some classes, slower where the larger code costs more than the
+// checks, measured per class).
+template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_, bool FP_>
 struct Cls {
   using T = T_;
   static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
+  static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
@@ -146,17 +151,17 @@ struct Cls {
   static_assert(U <= 16, "iteration unit too long to unroll");
 };
 
-//                 id          T       C  P  Q  K  NB SR NST
-using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 4, 3>;
-using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3>;
-using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3>;
-using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3>;
-using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3>;
-using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3>;
+//                 id          T       C  P  Q  K  NB SR NST FP
+using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 4, 3, false>;
+using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3, true>;
+using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3, true>;
+using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, false>;
+using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
+using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3, true>;
 // uint8 RGB (integer row math)
-using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3>;
-using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3>;
-using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3>;
+using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3, false>;
+using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, false>;
+using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false>;
 
 // ---------------------------------------------------------------------------
 // launch parameters
@@ -457,14 +462,16 @@ struct RowMath<Cl, false> {
 #pragma unroll
     for (int k = 0; k < N; ++k) d.v[k] = s.v[k];
   }
-  // the P output rows of block rr from the window
+  // the P output rows of block rr from the window (CHECK: rows past OH are
+  // skipped; without it the caller knows they are all inside)
+  template <bool CHECK>
   __device__ static __forceinline__ void v(const Row (&win)[Cl::L], const FastParams& prm, T* obase,
                                            long long rowe, int rr, int OH, int n_valid) {
     const float* taps = prm.taps[Cl::id];
 #pragma unroll
     for (int jv = 0; jv < Cl::P; ++jv) {
       const int oy = rr * Cl::P + jv;
-      if (oy < OH) {
+      if (!CHECK || oy < OH) {
         float acc[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) acc[k] = 0.0f;
@@ -623,6 +630,7 @@ struct RowMath<Cl, true> {
       r.w[k] = pack4(v[e], e + 1 < N ? v[e + 1] : 0, e + 2 < N ? v[e + 2] : 0, e + 3 < N ? v[e + 3] : 0);
     }
   }
+  template <bool CHECK>
   __device__ static __forceinline__ void v(const Row (&win)[L], const FastParams& prm, T* obase, long long rowe,
                                            int rr, int OH, int n_valid) {
     // one word column g (4 output columns) at a time: row-pair words
@@ -658,7 +666,7 @@ struct RowMath<Cl, true> {
 #pragma unroll
     for (int jv = 0; jv < P; ++jv) {
       const int oy = rr * P + jv;
-      if (oy < OH) store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
+      if (!CHECK || oy < OH) store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
     }
   }
 };
@@ -781,36 +789,42 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
 #pragma unroll
       for (int i = 0; i < Cl::LH; ++i) RM::copy(win[i], win[Cl::LH]);
     }
-    // ---- block steps, U rows (USTG stages, UBLK blocks) at a time
-    const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
-    for (int u = 0; ok && u < nunits; ++u) {
+    // ---- block steps, U rows (USTG stages, UBLK blocks) at a time.  A unit
+    // whose blocks are all inside the tile, whose rows are all above the
+    // frame's last row and whose outputs are all inside the frame, in a strip
+    // that needs no border fix-up and has every lane active, runs a copy of
+    // the body without any of those checks.
+    auto unit = [&](auto fast, int u) {
+      constexpr bool FAST = decltype(fast)::value;
 #pragma unroll
       for (int st = 0; st < Cl::USTG; ++st) {
         const int s = Cl::NPS + u * Cl::USTG + st;
-        if (s >= nst) break;
+        if (!FAST && s >= nst) break;
         uint8_t* sb = stage_wait(s);
         if (!sb) {
           ok = false;
-          break;
+          return;
         }
 #pragma unroll
         for (int r = 0; r < SR; ++r) {
-          constexpr int dummy = 0;
-          (void)dummy;
           const int ru = st * SR + r;       // row within the unit
           const int bq = ru / Q, q = ru - bq * Q;
           const int m = u * Cl::UBLK + bq;  // block step
-          if (m < nblk) {
+          if (FAST || m < nblk) {
             const int i = L - Q + q;
-            const int y = ys + m * Q + i;
-            if (y >= H) {
-              RM::copy(win[i], win[i - 1]);
+            if constexpr (FAST) {
+              uint32_t w[Cl::NWT];
+              load_row<Cl>(sb + r * Cl::BOXB, of, w);
+              RM::h(w, prm, win[i]);
             } else {
-              hrow_regs(sb + r * Cl::BOXB, win[i]);
+              const int y = ys + m * Q + i;
+              if (y >= H) RM::copy(win[i], win[i - 1]);
+              else hrow_regs(sb + r * Cl::BOXB, win[i]);
             }
             if (q == Q - 1) {
               // the window holds block m's pattern: its P output rows
-              if (active) RM::v(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+              if constexpr (FAST) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+              else if (active) RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
 #pragma unroll
               for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
             }
@@ -818,6 +832,18 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
         }
         stage_release(s);
       }
+    };
+    const bool x_inside = !fixing && (tl.strip * Cl::SBLK + 32 * Cl::NB) * P <= jd.OW;  // every lane complete
+    const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
+    for (int u = 0; ok && u < nunits; ++u) {
+      if constexpr (Cl::FASTPATH) {
+        const int mend = (u + 1) * Cl::UBLK;  // one past the unit's last block
+        if (x_inside && mend <= nblk && ys + (mend - 1) * Q + L - 1 < H && (rb0 + mend) * P <= jd.OH) {
+          unit(std::true_type{}, u);
+          continue;
+        }
+      }
+      unit(std::false_type{}, u);
     }
     g += (uint32_t)nst;
   }
