@@ -98,6 +98,9 @@ struct Cls {
   using T = T_;
   static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
   static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
+  // resident CTAs per SM the registers are budgeted for (4 x 4 warps; the
+  // uint8 1/2 class fits in the tighter budget of 5, which measures faster)
+  static constexpr int MINB = (ID == kFcU8C3_12) ? 5 : 4;
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
@@ -931,12 +934,12 @@ struct KernelInfo {
 
 constexpr int kRowsWPC = 4;  // warps (independent pipelines) per CTA of the row-streaming kernel
 
-// Registers are budgeted for 4 resident CTAs (16 warps) per SM, which the
-// shared-memory footprint of the stage rings also allows.
+// Registers are budgeted for Cl::MINB resident CTAs (4 warps each) per SM,
+// which the shared-memory footprint of the stage rings also allows.
 template <class Cl>
 KernelInfo rows_info() {
   constexpr int smem = 128 + kRowsWPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  return KernelInfo{reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, 4>), smem, kRowsWPC * 32};
+  return KernelInfo{reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, Cl::MINB>), smem, kRowsWPC * 32};
 }
 
 // The kernel that runs class `cls` (all jobs of a launch share the class).
