@@ -38,6 +38,12 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _Axes(ctypes.Structure):
+    _fields_ = [("ph", ctypes.c_int), ("qh", ctypes.c_int), ("Kh", ctypes.c_int),
+                ("pv", ctypes.c_int), ("qv", ctypes.c_int), ("Kv", ctypes.c_int),
+                ("boundary", ctypes.c_int), ("taps_h", ctypes.c_void_p), ("taps_v", ctypes.c_void_p)]
+
+
 def _load():
     global _lib
     if _lib is None:
@@ -53,6 +59,10 @@ def _load():
         lib.dso_filter_f64.argtypes = sig
         lib.dso_filter_u8.argtypes = sig
         lib.dso_max_threads.argtypes = []
+        lib.dso_quantize_q14.argtypes = [c_void, c_int, c_int, c_void]
+        sig_ex = [c_void, c_void, c_long, c_int, c_int, c_int, ctypes.POINTER(_Axes), c_int]
+        lib.dso_filter_ex_f64.argtypes = sig_ex
+        lib.dso_filter_ex_u8.argtypes = sig_ex
         _lib = lib
     return _lib
 
@@ -122,6 +132,37 @@ def filter_u8(x: np.ndarray, p: int, q: int, K: int, threads: int = 0) -> np.nda
     OH, OW = out_extent(H, p, q), out_extent(W, p, q)
     y = np.empty((n, OH, OW, C), np.uint8)
     if _load().dso_filter_u8(x4.ctypes.data, y.ctypes.data, n, H, W, C, p, q, K, threads):
+        raise ValueError("bad filter arguments")
+    return back(y)
+
+
+def quantize_q14(w: np.ndarray) -> np.ndarray:
+    """Q14 of a tap table (p, K): round half up, residual on the largest tap."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    p, K = w.shape
+    qt = np.zeros((p, K), np.int32)
+    if _load().dso_quantize_q14(w.ctypes.data, p, K, qt.ctypes.data):
+        raise ValueError("bad tap table")
+    return qt
+
+
+def filter_ex(x: np.ndarray, ratio_h, taps_h: int, ratio_v, taps_v: int, wrap: bool = False,
+              weights_h=None, weights_v=None, threads: int = 0) -> np.ndarray:
+    """Separable filter with its own ratio, tap count and (optionally) FP64 tap
+    table (p, K) per axis, and clamp-to-edge or modular (wrap) tilers.  uint8
+    input takes the Q14 integer path, anything else FP64."""
+    x4, back = _as_nhwc(np.asarray(x))
+    u8 = x4.dtype == np.uint8
+    x4 = np.ascontiguousarray(x4, dtype=np.uint8 if u8 else np.float64)
+    n, H, W, C = x4.shape
+    wh = None if weights_h is None else np.ascontiguousarray(weights_h, dtype=np.float64)
+    wv = None if weights_v is None else np.ascontiguousarray(weights_v, dtype=np.float64)
+    ax = _Axes(ratio_h[0], ratio_h[1], taps_h, ratio_v[0], ratio_v[1], taps_v, 1 if wrap else 0,
+               None if wh is None else wh.ctypes.data, None if wv is None else wv.ctypes.data)
+    OH, OW = out_extent(H, ratio_v[0], ratio_v[1]), out_extent(W, ratio_h[0], ratio_h[1])
+    y = np.empty((n, OH, OW, C), np.uint8 if u8 else np.float64)
+    fn = _load().dso_filter_ex_u8 if u8 else _load().dso_filter_ex_f64
+    if fn(x4.ctypes.data, y.ctypes.data, n, H, W, C, ctypes.byref(ax), threads):
         raise ValueError("bad filter arguments")
     return back(y)
 

@@ -117,15 +117,28 @@ int dso_taps_q14(int p, int q, int K, int32_t* qt) {
     if (p > 64) return -1;
     double w[64 * 16];
     dso_taps_f64(p, q, K, w);
+    return dso_quantize_q14(w, p, K, qt);
+}
+
+/*
+ * Q14 of any tap table w[p][K]: q = floor(w * 16384 + 1/2), then the
+ * residual floor(16384 * sum(w) + 1/2) - sum(q) goes to the tap with the
+ * largest w (lowest index on ties).  For rows that sum to 1 this is the
+ * rule above: each row of q sums to 16384 exactly.
+ */
+int dso_quantize_q14(const double* w, int p, int K, int32_t* qt) {
+    if (!w || !qt || p < 1 || K < 1) return -1;
     for (int j = 0; j < p; ++j) {
         long sum = 0;
+        double wsum = 0.0;
         int big = 0;
         for (int t = 0; t < K; ++t) {
             qt[j * K + t] = (int32_t)floor(w[j * K + t] * 16384.0 + 0.5);
             sum += qt[j * K + t];
+            wsum += w[j * K + t];
             if (w[j * K + t] > w[j * K + big]) big = t;
         }
-        qt[j * K + big] += (int32_t)(16384 - sum);
+        qt[j * K + big] += (int32_t)((long)floor(wsum * 16384.0 + 0.5) - sum);
     }
     return 0;
 }
@@ -148,9 +161,10 @@ typedef struct {
     long repetition; /* ceil(n_out / p): tasks along the axis           */
     long n_in;
     long n_out;
+    int wrap;        /* 0: clamp to the array; 1: modulo its extent     */
 } dso_tiler;
 
-static void make_tiler(dso_tiler* tl, long n_in, int p, int q, int K, const int* b) {
+static void make_tiler(dso_tiler* tl, long n_in, int p, int q, int K, const int* b, int wrap) {
     tl->origin = b[0];
     tl->paving = q;
     tl->fitting = 1;
@@ -158,6 +172,7 @@ static void make_tiler(dso_tiler* tl, long n_in, int p, int q, int K, const int*
     tl->n_in = n_in;
     tl->n_out = dso_out_extent(n_in, p, q);
     tl->repetition = (tl->n_out + p - 1) / p;
+    tl->wrap = wrap;
 }
 
 static long clamp_index(long i, long n) {
@@ -166,8 +181,15 @@ static long clamp_index(long i, long n) {
     return i;
 }
 
+/* Array-OL tilers index modulo the array's shape (the toroidal reading). */
+static long wrap_index(long i, long n) {
+    long m = i % n;
+    return m < 0 ? m + n : m;
+}
+
 static long tiler_index(const dso_tiler* tl, long r, int i) {
-    return clamp_index((long)tl->origin + (long)tl->paving * r + (long)tl->fitting * i, tl->n_in);
+    long k = (long)tl->origin + (long)tl->paving * r + (long)tl->fitting * i;
+    return tl->wrap ? wrap_index(k, tl->n_in) : clamp_index(k, tl->n_in);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -217,8 +239,8 @@ int dso_filter_f64(const double* x, double* y, long n_frames, int H, int W, int 
     dso_phase_windows(p, q, K, b, NULL);
     dso_taps_f64(p, q, K, w);
     dso_tiler th, tv;
-    make_tiler(&th, W, p, q, K, b);
-    make_tiler(&tv, H, p, q, K, b);
+    make_tiler(&th, W, p, q, K, b, 0);
+    make_tiler(&tv, H, p, q, K, b, 0);
     long OW = th.n_out, OH = tv.n_out;
     if (OW < 1 || OH < 1) return -1;
 #ifdef _OPENMP
@@ -286,8 +308,8 @@ int dso_filter_u8(const uint8_t* x, uint8_t* y, long n_frames, int H, int W, int
     dso_phase_windows(p, q, K, b, NULL);
     dso_taps_q14(p, q, K, qt);
     dso_tiler th, tv;
-    make_tiler(&th, W, p, q, K, b);
-    make_tiler(&tv, H, p, q, K, b);
+    make_tiler(&th, W, p, q, K, b, 0);
+    make_tiler(&tv, H, p, q, K, b, 0);
     long OW = th.n_out, OH = tv.n_out;
     if (OW < 1 || OH < 1) return -1;
 #ifdef _OPENMP
@@ -301,6 +323,94 @@ int dso_filter_u8(const uint8_t* x, uint8_t* y, long n_frames, int H, int W, int
         pass_u8(xf, h, H, W, C, 1, p, K, b, qt, &th);   /* horizontal filter */
         pass_u8(h, yf, H, OW, C, 0, p, K, b, qt, &tv);  /* vertical filter   */
         free(h);
+    }
+    (void)n_threads;
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Extended filter: each axis its own ratio, taps and tap table; boundary   */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+    int p, K;
+    int b[64];
+    double w[64 * 16];
+    int32_t qt[64 * 16];
+} dso_axis;
+
+/* Windows of one axis and its taps: Lanczos-3 (the reading above) when
+ * `user` is NULL, else the given FP64 table [p][K] as it is. */
+static int make_axis(dso_axis* a, int p, int q, int K, const double* user) {
+    if (check_filter_args(p, q, K) || p > 64) return -1;
+    a->p = p;
+    a->K = K;
+    dso_phase_windows(p, q, K, a->b, NULL);
+    if (user) {
+        for (int i = 0; i < p * K; ++i) {
+            if (!isfinite(user[i])) return -1;
+            a->w[i] = user[i];
+        }
+    } else {
+        dso_taps_f64(p, q, K, a->w);
+    }
+    return dso_quantize_q14(a->w, p, K, a->qt);
+}
+
+static int check_ex(const dso_axes* ax, dso_axis* h, dso_axis* v) {
+    if (!ax || (ax->boundary != 0 && ax->boundary != 1)) return -1;
+    if (make_axis(h, ax->ph, ax->qh, ax->Kh, ax->taps_h)) return -1;
+    if (make_axis(v, ax->pv, ax->qv, ax->Kv, ax->taps_v)) return -1;
+    return 0;
+}
+
+int dso_filter_ex_f64(const double* x, double* y, long n_frames, int H, int W, int C, const dso_axes* ax,
+                      int n_threads) {
+    dso_axis ah, av;
+    if (!x || !y || check_ex(ax, &ah, &av)) return -1;
+    if (n_frames < 0 || H < 1 || W < 1 || C < 1) return -1;
+    dso_tiler th, tv;
+    make_tiler(&th, W, ah.p, ax->qh, ah.K, ah.b, ax->boundary);
+    make_tiler(&tv, H, av.p, ax->qv, av.K, av.b, ax->boundary);
+    long OW = th.n_out, OH = tv.n_out;
+    if (OW < 1 || OH < 1) return -1;
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (long f = 0; f < n_frames; ++f) {
+        const double* xf = x + f * (long)H * W * C;
+        double* yf = y + f * OH * OW * C;
+        double* hbuf = (double*)malloc(sizeof(double) * (size_t)H * (size_t)OW * (size_t)C);
+        pass_f64(xf, hbuf, H, W, C, 1, ah.p, ah.K, ah.b, ah.w, &th);   /* horizontal filter */
+        pass_f64(hbuf, yf, H, OW, C, 0, av.p, av.K, av.b, av.w, &tv);  /* vertical filter   */
+        free(hbuf);
+    }
+    (void)n_threads;
+    return 0;
+}
+
+int dso_filter_ex_u8(const uint8_t* x, uint8_t* y, long n_frames, int H, int W, int C, const dso_axes* ax,
+                     int n_threads) {
+    dso_axis ah, av;
+    if (!x || !y || check_ex(ax, &ah, &av)) return -1;
+    if (n_frames < 0 || H < 1 || W < 1 || C < 1) return -1;
+    dso_tiler th, tv;
+    make_tiler(&th, W, ah.p, ax->qh, ah.K, ah.b, ax->boundary);
+    make_tiler(&tv, H, av.p, ax->qv, av.K, av.b, ax->boundary);
+    long OW = th.n_out, OH = tv.n_out;
+    if (OW < 1 || OH < 1) return -1;
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+#endif
+    for (long f = 0; f < n_frames; ++f) {
+        const uint8_t* xf = x + f * (long)H * W * C;
+        uint8_t* yf = y + f * OH * OW * C;
+        uint8_t* hbuf = (uint8_t*)malloc((size_t)H * (size_t)OW * (size_t)C);
+        pass_u8(xf, hbuf, H, W, C, 1, ah.p, ah.K, ah.b, ah.qt, &th);   /* horizontal filter */
+        pass_u8(hbuf, yf, H, OW, C, 0, av.p, av.K, av.b, av.qt, &tv);  /* vertical filter   */
+        free(hbuf);
     }
     (void)n_threads;
     return 0;

@@ -65,6 +65,27 @@ int dso_filter_f64(const double* x, double* y, long n_frames, int H, int W, int 
 int dso_filter_u8(const uint8_t* x, uint8_t* y, long n_frames, int H, int W, int C,
                   int p, int q, int K, int n_threads);
 
+/* Q14 of any tap table w[p][K]: round half up, the residual
+ * floor(16384 * row sum + 1/2) - sum(q) on the largest tap of the row. */
+int dso_quantize_q14(const double* w, int p, int K, int32_t* qt);
+
+/* Extended filter: a ratio, tap count and (optionally) tap table per axis,
+ * and the boundary of the tilers: 0 = clamp-to-edge, 1 = modular (Array-OL
+ * tilers index modulo the array's shape).  taps_h / taps_v NULL: the
+ * Lanczos-3 taps above; else FP64 tables [p][K] used as given. */
+typedef struct {
+    int ph, qh, Kh;
+    int pv, qv, Kv;
+    int boundary;
+    const double* taps_h;
+    const double* taps_v;
+} dso_axes;
+
+int dso_filter_ex_f64(const double* x, double* y, long n_frames, int H, int W, int C,
+                      const dso_axes* ax, int n_threads);
+int dso_filter_ex_u8(const uint8_t* x, uint8_t* y, long n_frames, int H, int W, int C,
+                     const dso_axes* ax, int n_threads);
+
 /* Number of OpenMP threads a parallel region would use (0 if built without). */
 int dso_max_threads(void);
 
