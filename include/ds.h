@@ -85,13 +85,57 @@ typedef enum {
  */
 ds_plan* ds_plan_create(int in_h, int in_w, ds_ratio ratio, int taps, ds_dtype dtype);
 
+/* Boundary of the tilers: clamp-to-edge (the default reading), or modular
+ * indexing, the Array-OL reading of tilers (Sec. 3.A: pattern elements are
+ * taken modulo the array's shape). */
+typedef enum {
+    DS_CLAMP = 0,
+    DS_WRAP = 1
+} ds_boundary;
+
+/*
+ * Extended plan: each axis has its own ratio and tap count, for instance
+ * the paper's CIF case, 352 -> 132 per line (3/8) and 288 -> 128 lines
+ * (4/9) (Sec. 3).  The tap tables may be given.
+ *   weights_h / weights_v: NULL = the Lanczos-3 taps of ds_plan_create;
+ *     else a row-major [p][taps] FP64 table of that axis, copied into the
+ *     plan and used as given (rows need not sum to 1).  uint8 plans use its
+ *     Q14 rounding: q = floor(w * 16384 + 1/2), with the residual
+ *     floor(16384 * row sum + 1/2) - sum(q) added to the largest tap of
+ *     the row.
+ * Axes with equal ratio and taps, DS_CLAMP and no given taps run on the
+ * fast fused kernel; every other plan runs on the general kernels.
+ * Errors (NULL + ds_last_error): those of ds_plan_create per axis; an
+ * unknown boundary; a given tap that is not finite; for uint8, a Q14 tap
+ * outside the int16 range or a row whose Q14 magnitudes sum past 65535
+ * (sums must stay exact in FP32).
+ */
+typedef struct {
+    int in_h, in_w;
+    ds_ratio ratio_h;          /* along a row: packets of q pixels -> p */
+    int taps_h;
+    ds_ratio ratio_v;          /* along a column                        */
+    int taps_v;
+    ds_dtype dtype;
+    ds_boundary boundary;
+    const double* weights_h;   /* NULL or [ratio_h.p][taps_h]           */
+    const double* weights_v;   /* NULL or [ratio_v.p][taps_v]           */
+} ds_plan_desc;
+
+ds_plan* ds_plan_create_ex(const ds_plan_desc* desc);
+
 /* Release a plan.  The caller must make sure no launch using it is still
  * running (synchronise the streams it was used on first).  NULL is ignored. */
 void ds_destroy(ds_plan* plan);
 
-/* The arguments the plan was created with (any pointer may be NULL). */
+/* The arguments the plan was created with (any pointer may be NULL); p, q
+ * and taps are those of the horizontal axis (ds_plan_get_axes has both). */
 ds_status ds_plan_get_params(const ds_plan* plan, int* in_h, int* in_w, int* p, int* q, int* taps,
                              int* dtype);
+
+/* Ratio and taps of both axes and the boundary (any pointer may be NULL). */
+ds_status ds_plan_get_axes(const ds_plan* plan, int* p_h, int* q_h, int* taps_h, int* p_v, int* q_v,
+                           int* taps_v, int* boundary);
 
 /* Output extent floor(in*p/q) per axis and the channel count. */
 ds_status ds_plan_out_shape(const ds_plan* plan, int* out_h, int* out_w, int* channels);
@@ -107,6 +151,11 @@ ds_status ds_plan_frame_bytes(const ds_plan* plan, size_t* in_bytes, size_t* out
  */
 ds_status ds_plan_get_taps(const ds_plan* plan, double* fp64, float* fp32, short* q14,
                            int* window_start);
+
+/* The same for one axis: axis 0 = horizontal (as ds_plan_get_taps), 1 =
+ * vertical.  DS_ERR_ARG for another axis. */
+ds_status ds_plan_get_axis_taps(const ds_plan* plan, int axis, double* fp64, float* fp32, short* q14,
+                                int* window_start);
 
 /*
  * Describe the execution choice as a short JSON object written into buf

@@ -21,6 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libds.so")
 
 DS_F32, DS_F16, DS_U8, DS_U8_RGB = 0, 1, 2, 3
+DS_CLAMP, DS_WRAP = 0, 1
 DS_OK, DS_ERR_ARG, DS_ERR_NOMEM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 _STATUS_NAMES = {0: "DS_OK", -1: "DS_ERR_ARG", -2: "DS_ERR_NOMEM", -3: "DS_ERR_CUDA",
                  -4: "DS_ERR_TIMEOUT", -5: "DS_ERR_UNSUPPORTED"}
@@ -33,7 +34,7 @@ ABI_SYMBOLS = (
     "ds_stream_check", "ds_debug_check_plan", "ds_graph_create", "ds_graph_launch", "ds_graph_destroy",
     "ds_pipeline_create", "ds_pipeline_run", "ds_pipeline_destroy", "ds_last_error", "ds_version",
     "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static", "ds_plan_autotune",
-    "ds_debug_timeout_probe",
+    "ds_debug_timeout_probe", "ds_plan_create_ex", "ds_plan_get_axes", "ds_plan_get_axis_taps",
 )
 
 
@@ -45,6 +46,12 @@ class DsError(RuntimeError):
 
 class ds_ratio(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("q", ctypes.c_int)]
+
+
+class ds_plan_desc(ctypes.Structure):
+    _fields_ = [("in_h", ctypes.c_int), ("in_w", ctypes.c_int), ("ratio_h", ds_ratio), ("taps_h", ctypes.c_int),
+                ("ratio_v", ds_ratio), ("taps_v", ctypes.c_int), ("dtype", ctypes.c_int), ("boundary", ctypes.c_int),
+                ("weights_h", ctypes.c_void_p), ("weights_v", ctypes.c_void_p)]
 
 
 class ds_job(ctypes.Structure):
@@ -95,6 +102,9 @@ def lib() -> ctypes.CDLL:
         "ds_plan_autotune": (i, [vp, vp, vp, i, vp, i, ip, ctypes.POINTER(ctypes.c_float)]),
         "ds_run_unfused_static": (i, [vp, vp, vp, i, vp]),
         "ds_debug_timeout_probe": (i, [ctypes.c_longlong, vp]),
+        "ds_plan_create_ex": (vp, [ctypes.POINTER(ds_plan_desc)]),
+        "ds_plan_get_axes": (i, [vp, ip, ip, ip, ip, ip, ip, ip]),
+        "ds_plan_get_axis_taps": (i, [vp, i, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -132,6 +142,41 @@ def ds_plan_create(in_h: int, in_w: int, ratio: Sequence[int], taps: int, dtype:
     if not h:
         raise DsError(DS_ERR_ARG, ds_last_error())
     return h
+
+
+def ds_plan_create_ex(in_h: int, in_w: int, ratio_h: Sequence[int], taps_h: int, ratio_v: Sequence[int],
+                      taps_v: int, dtype: int, boundary: int = DS_CLAMP, weights_h=None, weights_v=None) -> int:
+    """Plan with a ratio and tap count per axis, a boundary (DS_CLAMP / DS_WRAP)
+    and optional FP64 tap tables (p, K) per axis (copied by the library)."""
+    wh = None if weights_h is None else np.ascontiguousarray(weights_h, dtype=np.float64)
+    wv = None if weights_v is None else np.ascontiguousarray(weights_v, dtype=np.float64)
+    d = ds_plan_desc(in_h, in_w, ds_ratio(int(ratio_h[0]), int(ratio_h[1])), taps_h,
+                     ds_ratio(int(ratio_v[0]), int(ratio_v[1])), taps_v, dtype, boundary,
+                     None if wh is None else wh.ctypes.data, None if wv is None else wv.ctypes.data)
+    h = lib().ds_plan_create_ex(ctypes.byref(d))
+    if not h:
+        raise DsError(DS_ERR_ARG, ds_last_error())
+    return h
+
+
+def ds_plan_get_axes(plan: int):
+    """((p_h, q_h, taps_h), (p_v, q_v, taps_v), boundary)"""
+    v = [ctypes.c_int() for _ in range(7)]
+    _check(lib().ds_plan_get_axes(_ptr(plan), *[ctypes.byref(x) for x in v]))
+    return (v[0].value, v[1].value, v[2].value), (v[3].value, v[4].value, v[5].value), v[6].value
+
+
+def ds_plan_get_axis_taps(plan: int, axis: int):
+    """ds_plan_get_taps for axis 0 (horizontal) or 1 (vertical)."""
+    (ph, _, Kh), (pv, _, Kv), _ = ds_plan_get_axes(plan)
+    p, K = (ph, Kh) if axis == 0 else (pv, Kv)
+    f64 = np.zeros((p, K), np.float64)
+    f32 = np.zeros((p, K), np.float32)
+    q14 = np.zeros((p, K), np.int16)
+    b = np.zeros(p, np.int32)
+    _check(lib().ds_plan_get_axis_taps(_ptr(plan), axis, f64.ctypes.data, f32.ctypes.data, q14.ctypes.data,
+                                       b.ctypes.data))
+    return {"fp64": f64, "fp32": f32, "q14": q14, "window_start": b}
 
 
 def ds_destroy(plan: int) -> None:

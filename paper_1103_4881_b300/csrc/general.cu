@@ -20,47 +20,71 @@ namespace ds {
 
 namespace {
 
-struct GenParams {
-  float w[kMaxP * kMaxK];  // FP32 taps, or Q14 taps as floats for uint8
-  int b[kMaxP];            // window start of each phase
-  int p, q, K, C;
-  int H, W, OH, OW;
-  int bmin, L;             // first window offset and pattern length
-  int nby;                 // output row blocks: ceil(OH / p)
-  int tob, tox;            // fused tile: row blocks x output pixels
+// One axis of the filter: phase windows and taps (FP32, or Q14 as floats
+// for uint8).
+struct GenAxis {
+  float w[kMaxP * kMaxK];
+  int b[kMaxP];   // window start of each phase
+  int p, q, K;
+  int bmin, L;    // first window offset and pattern length
 };
+
+struct GenParams {
+  GenAxis h, v;   // horizontal (along a row) and vertical (along a column)
+  int C;
+  int H, W, OH, OW;
+  int wrap;       // 0: clamp-to-edge, 1: modular indexing
+  int nby;        // output row blocks: ceil(OH / v.p)
+  int tob, tox;   // fused tile: row blocks x output pixels
+};
+
+GenAxis make_axis(int p, int q, int K, const int* b, const float* w32, const short* q14, bool u8) {
+  GenAxis a{};
+  for (int i = 0; i < p * K; ++i) a.w[i] = u8 ? (float)q14[i] : w32[i];
+  for (int j = 0; j < p; ++j) a.b[j] = b[j];
+  a.p = p;
+  a.q = q;
+  a.K = K;
+  a.bmin = b[0];
+  a.L = b[p - 1] + K - b[0];
+  return a;
+}
 
 GenParams make_params(const ds_plan* pl) {
   GenParams g{};
-  const int n = pl->p * pl->K;
   const bool u8 = pl->dtype == DS_U8 || pl->dtype == DS_U8_RGB;
-  for (int i = 0; i < n; ++i) g.w[i] = u8 ? (float)pl->q14[i] : pl->w32[i];
-  for (int j = 0; j < pl->p; ++j) g.b[j] = pl->b[j];
-  g.p = pl->p;
-  g.q = pl->q;
-  g.K = pl->K;
+  g.h = make_axis(pl->p, pl->q, pl->K, pl->b, pl->w32, pl->q14, u8);
+  g.v = make_axis(pl->pv, pl->qv, pl->Kv, pl->bv, pl->w32v, pl->q14v, u8);
   g.C = pl->channels;
   g.H = pl->in_h;
   g.W = pl->in_w;
   g.OH = pl->out_h;
   g.OW = pl->out_w;
-  g.bmin = pl->b[0];
-  g.L = pl->b[pl->p - 1] + pl->K - pl->b[0];
-  g.nby = (pl->out_h + pl->p - 1) / pl->p;
-  g.tob = std::max(1, 32 / pl->q);
+  g.wrap = pl->boundary == DS_WRAP ? 1 : 0;
+  g.nby = (pl->out_h + pl->pv - 1) / pl->pv;
+  g.tob = std::max(1, 32 / pl->qv);
   g.tox = 32;
   return g;
+}
+
+// Index i of an axis of n elements under the plan's boundary.
+__device__ __forceinline__ int fix_index(int i, int n, int wrap) {
+  if (wrap) {
+    const int m = i % n;
+    return m < 0 ? m + n : m;
+  }
+  return clampi(i, 0, n - 1);
 }
 
 // Horizontal dot product of output pixel o (channel c) on input row `row`.
 template <typename T>
 __device__ __forceinline__ float hdot(const GenParams& g, const T* __restrict__ row, int o, int c) {
-  const int j = o % g.p;
-  const int s = (o / g.p) * g.q + g.b[j];
-  const float* w = g.w + j * g.K;
+  const int j = o % g.h.p;
+  const int s = (o / g.h.p) * g.h.q + g.h.b[j];
+  const float* w = g.h.w + j * g.h.K;
   float acc = 0.0f;
-  for (int t = 0; t < g.K; ++t) {
-    const int x = clampi(s + t, 0, g.W - 1);
+  for (int t = 0; t < g.h.K; ++t) {
+    const int x = fix_index(s + t, g.W, g.wrap);
     acc = fmaf(w[t], px_to_f(row[(size_t)x * g.C + c]), acc);
   }
   return pass_round<T>(acc);
@@ -77,29 +101,30 @@ __global__ void __launch_bounds__(256) k_fused_general(const T* __restrict__ in,
   const int npx = min(g.tox, g.OW - ox0);
   const int ne = npx * g.C;         // elements per tile row
   const int te = g.tox * g.C;       // shared row stride
-  const int ys = rb0 * g.q + g.bmin;
-  const int nr = (nb - 1) * g.q + g.L;
+  const int ys = rb0 * g.v.q + g.v.bmin;
+  const int nr = (nb - 1) * g.v.q + g.v.L;
   const T* src = in + (size_t)f * g.H * g.W * g.C;
   T* dst = out + (size_t)f * g.OH * g.OW * g.C;
 
-  // horizontal pass: shared row i holds the filtered input row clamp(ys + i)
+  // horizontal pass: shared row i holds the filtered input row ys + i
+  // (clamped or wrapped)
   for (int idx = threadIdx.x; idx < nr * ne; idx += blockDim.x) {
     const int i = idx / ne, e = idx - i * ne;
-    const int y = clampi(ys + i, 0, g.H - 1);
+    const int y = fix_index(ys + i, g.H, g.wrap);
     const int o = ox0 + e / g.C, c = e % g.C;
     sh[i * te + e] = hdot<T>(g, src + (size_t)y * g.W * g.C, o, c);
   }
   __syncthreads();
   // vertical pass over the shared rows
-  for (int idx = threadIdx.x; idx < nb * g.p * ne; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < nb * g.v.p * ne; idx += blockDim.x) {
     const int orow = idx / ne, e = idx - orow * ne;
-    const int r = rb0 + orow / g.p, j = orow % g.p;
-    const int oy = r * g.p + j;
+    const int r = rb0 + orow / g.v.p, j = orow % g.v.p;
+    const int oy = r * g.v.p + j;
     if (oy >= g.OH) continue;
-    const int base = r * g.q + g.b[j] - ys;
-    const float* w = g.w + j * g.K;
+    const int base = r * g.v.q + g.v.b[j] - ys;
+    const float* w = g.v.w + j * g.v.K;
     float acc = 0.0f;
-    for (int t = 0; t < g.K; ++t) acc = fmaf(w[t], sh[(base + t) * te + e], acc);
+    for (int t = 0; t < g.v.K; ++t) acc = fmaf(w[t], sh[(base + t) * te + e], acc);
     dst[(size_t)oy * g.OW * g.C + (size_t)ox0 * g.C + e] = f_to_px<T>(pass_round<T>(acc));
   }
 }
@@ -128,13 +153,13 @@ __global__ void __launch_bounds__(256) k_vpass(const I* __restrict__ inter, T* _
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int ne = g.OW * g.C;
   if (e >= ne) return;
-  const int j = oy % g.p;
-  const int s = (oy / g.p) * g.q + g.b[j];
-  const float* w = g.w + j * g.K;
+  const int j = oy % g.v.p;
+  const int s = (oy / g.v.p) * g.v.q + g.v.b[j];
+  const float* w = g.v.w + j * g.v.K;
   const I* col = inter + (size_t)f * g.H * ne + e;
   float acc = 0.0f;
-  for (int t = 0; t < g.K; ++t) {
-    const int y = clampi(s + t, 0, g.H - 1);
+  for (int t = 0; t < g.v.K; ++t) {
+    const int y = fix_index(s + t, g.H, g.wrap);
     acc = fmaf(w[t], (float)col[(size_t)y * ne], acc);
   }
   out[((size_t)f * g.OH + oy) * ne + e] = f_to_px<T>(pass_round<T>(acc));
@@ -145,7 +170,7 @@ constexpr int kMaxGridZ = 65535;
 template <typename T>
 ds_status fused_general_t(const ds_plan* pl, const void* in, void* out, int n_frames, cudaStream_t st) {
   const GenParams g = make_params(pl);
-  const int nr_max = (g.tob - 1) * g.q + g.L;
+  const int nr_max = (g.tob - 1) * g.v.q + g.v.L;
   const size_t smem = (size_t)nr_max * g.tox * g.C * sizeof(float);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_fused_general<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -38,6 +38,7 @@ enum FastClass : int {
 
 struct ds_plan {
   int in_h = 0, in_w = 0, channels = 1, elem_size = 4;
+  // horizontal axis (along a row)
   int p = 1, q = 2, K = 2;
   ds_dtype dtype = DS_F32;
   int out_h = 0, out_w = 0;
@@ -45,6 +46,14 @@ struct ds_plan {
   double w64[ds::kMaxP * ds::kMaxK] = {};    // FP64 taps [p][K]
   float w32[ds::kMaxP * ds::kMaxK] = {};     // (float) of w64
   short q14[ds::kMaxP * ds::kMaxK] = {};     // Q14 taps
+  // vertical axis (along a column), the same tables
+  int pv = 1, qv = 2, Kv = 2;
+  int bv[ds::kMaxP] = {};
+  double w64v[ds::kMaxP * ds::kMaxK] = {};
+  float w32v[ds::kMaxP * ds::kMaxK] = {};
+  short q14v[ds::kMaxP * ds::kMaxK] = {};
+  ds_boundary boundary = DS_CLAMP;
+  bool given_taps = false;                   // a tap table came from the caller
   int fast_class = ds::kFcNone;              // -1: general kernels only
   int row_blocks = 0;                        // fused tile: output row blocks per tile
   int ctas_per_sm = 0;                       // persistent grid: 0 = occupancy

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 
 #include "internal.h"
 
@@ -44,35 +45,80 @@ double lanczos_a3(double x) {
   return 3.0 * std::sin(px) * std::sin(px / 3.0) / (px * px);
 }
 
-// Phase windows and taps of a p/q, K-tap plan.
-void build_taps(ds_plan* pl) {
-  const int p = pl->p, q = pl->q, K = pl->K;
+// Phase windows and taps of one axis: p/q with K taps.  `given`: NULL for
+// the Lanczos-3 taps, else the caller's FP64 table [p][K].  The Q14 table
+// rounds half up and puts the residual floor(16384 * row sum + 1/2) - sum(q)
+// on the row's largest tap (16384 - sum(q) for rows summing to 1).
+// Returns false, with the reason in `why`, if a given tap is not finite or
+// (for uint8, `u8`) the Q14 table cannot be used exactly.
+bool build_axis(int p, int q, int K, const double* given, bool u8, int* b, double* w64, float* w32, short* q14,
+                char* why, size_t why_len) {
   const double stretch = 6.0 / K;  // Lanczos-3 support spread over K taps
   for (int j = 0; j < p; ++j) {
     // centre of phase j relative to the block start, as num / den
     const long long num = (long long)(2 * j + 1) * q - p;
     const long long den = 2LL * p;
     const double centre = (double)num / (double)den;
-    pl->b[j] = (int)(floor_div(num, den) - K / 2 + 1);
-    double* row = pl->w64 + j * K;
-    double total = 0.0;
-    for (int t = 0; t < K; ++t) {
-      row[t] = lanczos_a3(stretch * ((double)(pl->b[j] + t) - centre));
-      total += row[t];
+    b[j] = (int)(floor_div(num, den) - K / 2 + 1);
+    double* row = w64 + j * K;
+    if (given) {
+      for (int t = 0; t < K; ++t) {
+        row[t] = given[j * K + t];
+        if (!std::isfinite(row[t])) {
+          std::snprintf(why, why_len, "tap [%d][%d] is not finite", j, t);
+          return false;
+        }
+      }
+    } else {
+      double total = 0.0;
+      for (int t = 0; t < K; ++t) {
+        row[t] = lanczos_a3(stretch * ((double)(b[j] + t) - centre));
+        total += row[t];
+      }
+      for (int t = 0; t < K; ++t) row[t] /= total;
     }
     int largest = 0;
     long long qsum = 0;
+    double wsum = 0.0;
+    long long qv[kMaxK];
     for (int t = 0; t < K; ++t) {
-      row[t] /= total;
-      pl->w32[j * K + t] = (float)row[t];
-      const long long qv = (long long)std::floor(row[t] * 16384.0 + 0.5);
-      pl->q14[j * K + t] = (short)qv;
-      qsum += qv;
+      w32[j * K + t] = (float)row[t];
+      qv[t] = (long long)std::floor(row[t] * 16384.0 + 0.5);
+      qsum += qv[t];
+      wsum += row[t];
       if (row[t] > row[largest]) largest = t;
     }
-    // the rounding residual goes to the largest tap so each row sums to 2^14
-    pl->q14[j * K + largest] = (short)(pl->q14[j * K + largest] + (16384 - qsum));
+    // the rounding residual goes to the largest tap (so rows summing to 1
+    // give Q14 rows summing to 2^14 exactly)
+    qv[largest] += (long long)std::floor(wsum * 16384.0 + 0.5) - qsum;
+    long long mag = 0;
+    for (int t = 0; t < K; ++t) {
+      if (u8 && (qv[t] < -32768 || qv[t] > 32767)) {
+        std::snprintf(why, why_len, "Q14 tap [%d][%d] = %lld outside int16", j, t, qv[t]);
+        return false;
+      }
+      mag += qv[t] < 0 ? -qv[t] : qv[t];
+      q14[j * K + t] = (short)(qv[t] < -32768 ? -32768 : (qv[t] > 32767 ? 32767 : qv[t]));
+    }
+    if (u8 && mag > 65535) {
+      std::snprintf(why, why_len, "Q14 row %d magnitudes sum to %lld > 65535", j, mag);
+      return false;
+    }
   }
+  return true;
+}
+
+bool axis_ok(const char* who, const char* axis, int p, int q, int K) {
+  if (p < 1 || q <= p || gcd(p, q) != 1 || p > kMaxP || q > kMaxQ) {
+    set_error("%s: %sratio %d/%d must be in lowest terms, 0 < p < q, p <= %d, q <= %d", who, axis, p, q, kMaxP,
+              kMaxQ);
+    return false;
+  }
+  if (K < 2 || K > kMaxK || (K % 2) != 0) {
+    set_error("%s: %staps %d must be even and in [2,%d]", who, axis, K, kMaxK);
+    return false;
+  }
+  return true;
 }
 
 // Default band of output row blocks per tile (measured on a B300 over the
@@ -147,63 +193,102 @@ long long ds_launch_count(void) {
   return n;
 }
 
-ds_plan* ds_plan_create(int in_h, int in_w, ds_ratio ratio, int taps, ds_dtype dtype) {
-  clear_error();
-  if (in_h < 1 || in_w < 1) {
-    set_error("ds_plan_create: frame %dx%d must be at least 1x1", in_h, in_w);
+namespace {
+
+ds_plan* create_plan(const ds_plan_desc& d, const char* who) {
+  if (d.in_h < 1 || d.in_w < 1) {
+    set_error("%s: frame %dx%d must be at least 1x1", who, d.in_h, d.in_w);
     return nullptr;
   }
-  const int p = ratio.p, q = ratio.q;
-  if (p < 1 || q <= p || gcd(p, q) != 1 || p > kMaxP || q > kMaxQ) {
-    set_error("ds_plan_create: ratio %d/%d must be in lowest terms, 0 < p < q, p <= %d, q <= %d",
-              p, q, kMaxP, kMaxQ);
-    return nullptr;
-  }
-  if (taps < 2 || taps > kMaxK || (taps % 2) != 0) {
-    set_error("ds_plan_create: taps %d must be even and in [2,%d]", taps, kMaxK);
-    return nullptr;
-  }
+  const bool same = d.ratio_h.p == d.ratio_v.p && d.ratio_h.q == d.ratio_v.q && d.taps_h == d.taps_v;
+  if (!axis_ok(who, same ? "" : "horizontal ", d.ratio_h.p, d.ratio_h.q, d.taps_h)) return nullptr;
+  if (!axis_ok(who, same ? "" : "vertical ", d.ratio_v.p, d.ratio_v.q, d.taps_v)) return nullptr;
   int channels = 1, elem = 4;
-  switch (dtype) {
+  switch (d.dtype) {
     case DS_F32: channels = 1; elem = 4; break;
     case DS_F16: channels = 1; elem = 2; break;
     case DS_U8: channels = 1; elem = 1; break;
     case DS_U8_RGB: channels = 3; elem = 1; break;
     default:
-      set_error("ds_plan_create: unknown dtype %d", (int)dtype);
+      set_error("%s: unknown dtype %d", who, (int)d.dtype);
       return nullptr;
   }
-  const long long oh = (long long)in_h * p / q, ow = (long long)in_w * p / q;
-  if (oh < 1 || ow < 1) {
-    set_error("ds_plan_create: %dx%d at %d/%d gives an empty output", in_h, in_w, p, q);
+  if (d.boundary != DS_CLAMP && d.boundary != DS_WRAP) {
+    set_error("%s: unknown boundary %d", who, (int)d.boundary);
     return nullptr;
   }
-  if ((long long)in_h * in_w * channels >= (1LL << 40)) {
-    set_error("ds_plan_create: frame too large");
+  const long long oh = (long long)d.in_h * d.ratio_v.p / d.ratio_v.q;
+  const long long ow = (long long)d.in_w * d.ratio_h.p / d.ratio_h.q;
+  if (oh < 1 || ow < 1) {
+    set_error("%s: %dx%d at %d/%d x %d/%d gives an empty output", who, d.in_h, d.in_w, d.ratio_v.p, d.ratio_v.q,
+              d.ratio_h.p, d.ratio_h.q);
+    return nullptr;
+  }
+  if ((long long)d.in_h * d.in_w * channels >= (1LL << 40)) {
+    set_error("%s: frame too large", who);
     return nullptr;
   }
   ds_plan* pl = new (std::nothrow) ds_plan();
   if (!pl) {
-    set_error("ds_plan_create: out of host memory");
+    set_error("%s: out of host memory", who);
     return nullptr;
   }
-  pl->in_h = in_h;
-  pl->in_w = in_w;
+  pl->in_h = d.in_h;
+  pl->in_w = d.in_w;
   pl->channels = channels;
   pl->elem_size = elem;
-  pl->p = p;
-  pl->q = q;
-  pl->K = taps;
-  pl->dtype = dtype;
+  pl->p = d.ratio_h.p;
+  pl->q = d.ratio_h.q;
+  pl->K = d.taps_h;
+  pl->pv = d.ratio_v.p;
+  pl->qv = d.ratio_v.q;
+  pl->Kv = d.taps_v;
+  pl->dtype = d.dtype;
+  pl->boundary = d.boundary;
+  pl->given_taps = d.weights_h || d.weights_v;
   pl->out_h = (int)oh;
   pl->out_w = (int)ow;
-  build_taps(pl);
-  pl->fast_class = fast_class_of(p, q, taps, dtype);
+  const bool u8 = d.dtype == DS_U8 || d.dtype == DS_U8_RGB;
+  char why[160];
+  if (!build_axis(pl->p, pl->q, pl->K, d.weights_h, u8, pl->b, pl->w64, pl->w32, pl->q14, why, sizeof(why)) ||
+      !build_axis(pl->pv, pl->qv, pl->Kv, d.weights_v, u8, pl->bv, pl->w64v, pl->w32v, pl->q14v, why,
+                  sizeof(why))) {
+    set_error("%s: %s", who, why);
+    delete pl;
+    return nullptr;
+  }
+  // the fast kernels take one ratio for both axes, clamp-to-edge and the
+  // library's own taps
+  pl->fast_class = (same && d.boundary == DS_CLAMP && !pl->given_taps)
+                       ? fast_class_of(pl->p, pl->q, pl->K, d.dtype) : kFcNone;
   pl->row_blocks = default_row_blocks(pl->fast_class);
   if (pl->row_blocks == 0) pl->row_blocks = 8;
   const char* no_tma = std::getenv("DS_NO_TMA");
   pl->force_general = (no_tma && no_tma[0] && no_tma[0] != '0');
   return pl;
+}
+
+}  // namespace
+
+ds_plan* ds_plan_create(int in_h, int in_w, ds_ratio ratio, int taps, ds_dtype dtype) {
+  clear_error();
+  ds_plan_desc d{};
+  d.in_h = in_h;
+  d.in_w = in_w;
+  d.ratio_h = d.ratio_v = ratio;
+  d.taps_h = d.taps_v = taps;
+  d.dtype = dtype;
+  d.boundary = DS_CLAMP;
+  return create_plan(d, "ds_plan_create");
+}
+
+ds_plan* ds_plan_create_ex(const ds_plan_desc* desc) {
+  clear_error();
+  if (!desc) {
+    set_error("ds_plan_create_ex: NULL descriptor");
+    return nullptr;
+  }
+  return create_plan(*desc, "ds_plan_create_ex");
 }
 
 void ds_destroy(ds_plan* plan) { delete plan; }
@@ -245,15 +330,37 @@ ds_status ds_plan_frame_bytes(const ds_plan* pl, size_t* in_bytes, size_t* out_b
 
 ds_status ds_plan_get_taps(const ds_plan* pl, double* fp64, float* fp32, short* q14,
                            int* window_start) {
-  if (!pl) {
-    set_error("ds_plan_get_taps: NULL plan");
+  return ds_plan_get_axis_taps(pl, 0, fp64, fp32, q14, window_start);
+}
+
+ds_status ds_plan_get_axis_taps(const ds_plan* pl, int axis, double* fp64, float* fp32, short* q14,
+                                int* window_start) {
+  if (!pl || (axis != 0 && axis != 1)) {
+    set_error("ds_plan_get_axis_taps: NULL plan or axis not 0 / 1");
     return DS_ERR_ARG;
   }
-  const int n = pl->p * pl->K;
-  if (fp64) std::memcpy(fp64, pl->w64, sizeof(double) * n);
-  if (fp32) std::memcpy(fp32, pl->w32, sizeof(float) * n);
-  if (q14) std::memcpy(q14, pl->q14, sizeof(short) * n);
-  if (window_start) std::memcpy(window_start, pl->b, sizeof(int) * pl->p);
+  const bool v = axis == 1;
+  const int p = v ? pl->pv : pl->p, n = p * (v ? pl->Kv : pl->K);
+  if (fp64) std::memcpy(fp64, v ? pl->w64v : pl->w64, sizeof(double) * n);
+  if (fp32) std::memcpy(fp32, v ? pl->w32v : pl->w32, sizeof(float) * n);
+  if (q14) std::memcpy(q14, v ? pl->q14v : pl->q14, sizeof(short) * n);
+  if (window_start) std::memcpy(window_start, v ? pl->bv : pl->b, sizeof(int) * p);
+  return DS_OK;
+}
+
+ds_status ds_plan_get_axes(const ds_plan* pl, int* p_h, int* q_h, int* taps_h, int* p_v, int* q_v, int* taps_v,
+                           int* boundary) {
+  if (!pl) {
+    set_error("ds_plan_get_axes: NULL plan");
+    return DS_ERR_ARG;
+  }
+  if (p_h) *p_h = pl->p;
+  if (q_h) *q_h = pl->q;
+  if (taps_h) *taps_h = pl->K;
+  if (p_v) *p_v = pl->pv;
+  if (q_v) *q_v = pl->qv;
+  if (taps_v) *taps_v = pl->Kv;
+  if (boundary) *boundary = (int)pl->boundary;
   return DS_OK;
 }
 
@@ -288,9 +395,11 @@ ds_status ds_plan_describe(const ds_plan* pl, char* buf, size_t len) {
   const bool fast = pl->fast_class >= 0 && !pl->force_general;
   std::snprintf(buf, len,
                 "{\"kernel\": \"%s\", \"class\": \"%s\", \"in\": [%d, %d, %d], \"out\": [%d, %d, %d], "
-                "\"ratio\": [%d, %d], \"taps\": %d, \"row_blocks\": %d, \"ctas_per_sm\": %d}",
+                "\"ratio\": [%d, %d], \"taps\": %d, \"ratio_v\": [%d, %d], \"taps_v\": %d, "
+                "\"boundary\": \"%s\", \"given_taps\": %s, \"row_blocks\": %d, \"ctas_per_sm\": %d}",
                 fast ? "fused_tma" : "fused_general", pl->fast_class >= 0 ? names[pl->fast_class] : "general",
-                pl->in_h, pl->in_w, pl->channels, pl->out_h, pl->out_w, pl->channels, pl->p, pl->q, pl->K,
+                pl->in_h, pl->in_w, pl->channels, pl->out_h, pl->out_w, pl->channels, pl->p, pl->q, pl->K, pl->pv,
+                pl->qv, pl->Kv, pl->boundary == DS_WRAP ? "wrap" : "clamp", pl->given_taps ? "true" : "false",
                 pl->row_blocks, pl->ctas_per_sm);
   return DS_OK;
 }

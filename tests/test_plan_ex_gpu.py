@@ -1,0 +1,81 @@
+"""GPU parity of extended plans: a ratio per axis (the paper's CIF case,
+352x288 -> 132x128 with H 3/8 and V 4/9), modular tilers and caller-given
+taps, against the oracle; the general fused kernel and the unfused form
+agree bit for bit."""
+import numpy as np
+import pytest
+
+import paper_1103_4881_b300 as ds
+from tests.gpu_util import TOL, assert_parity, frames, run_fused, run_unfused
+
+pytestmark = pytest.mark.gpu
+
+RNG = np.random.default_rng(11)
+W_H = RNG.normal(0, 0.3, (3, 8))
+W_V = RNG.normal(0, 0.3, (4, 8))
+
+CASES = [
+    # (H, W, rh, Kh, rv, Kv, dtype, boundary, given)
+    (288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8_RGB, ds.DS_CLAMP, False),   # the paper's CIF case
+    (288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8, ds.DS_CLAMP, False),       # one plane
+    (144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8, ds.DS_WRAP, False),        # a chroma plane, modular
+    (97, 130, (1, 2), 6, (2, 3), 6, ds.DS_F32, ds.DS_CLAMP, False),
+    (97, 130, (2, 3), 6, (1, 2), 6, ds.DS_F16, ds.DS_WRAP, False),
+    (5, 7, (3, 8), 8, (4, 9), 8, ds.DS_F32, ds.DS_WRAP, False),           # windows wrap more than once
+    (3, 16, (1, 2), 6, (1, 3), 6, ds.DS_U8_RGB, ds.DS_WRAP, False),
+    (200, 256, (3, 8), 8, (3, 8), 8, ds.DS_F32, ds.DS_WRAP, False),       # equal axes, modular
+    (120, 160, (3, 8), 8, (4, 9), 8, ds.DS_F32, ds.DS_CLAMP, True),       # given taps
+    (120, 160, (3, 8), 8, (4, 9), 8, ds.DS_U8_RGB, ds.DS_WRAP, True),
+    (64, 96, (3, 8), 8, (3, 8), 8, ds.DS_F16, ds.DS_CLAMP, True),
+]
+
+
+def _plan(H, W, rh, Kh, rv, Kv, dt, bnd, given):
+    wh = W_H[: rh[0], :Kh] if given else None
+    wv = W_V[: rv[0], :Kv] if given else None
+    return ds.ds_plan_create_ex(H, W, rh, Kh, rv, Kv, dt, bnd, wh, wv), wh, wv
+
+
+def _oracle(oracle, x, rh, Kh, rv, Kv, dt, bnd, wh, wv):
+    if dt in (ds.DS_U8, ds.DS_U8_RGB):
+        return oracle.filter_ex(x, rh, Kh, rv, Kv, wrap=bnd == ds.DS_WRAP, weights_h=wh, weights_v=wv)
+    return oracle.filter_ex(x.astype(np.float64), rh, Kh, rv, Kv, wrap=bnd == ds.DS_WRAP, weights_h=wh,
+                            weights_v=wv)
+
+
+@pytest.mark.parametrize("H,W,rh,Kh,rv,Kv,dt,bnd,given", CASES)
+def test_extended_plan_parity(oracle, H, W, rh, Kh, rv, Kv, dt, bnd, given):
+    pl, wh, wv = _plan(H, W, rh, Kh, rv, Kv, dt, bnd, given)
+    try:
+        x = frames((H, W), dt, 3, H * 5 + W)
+        got = run_fused(pl, x)
+        want = _oracle(oracle, x, rh, Kh, rv, Kv, dt, bnd, wh, wv)
+        assert got.shape == want.shape
+        assert_parity(got, want, dt, "ex %dx%d %s/%s dt=%d bnd=%d given=%s" % (H, W, rh, rv, dt, bnd, given))
+        np.testing.assert_array_equal(run_unfused(pl, x), got)
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_cif_frames_in_one_batch_with_yuv_planes(oracle):
+    """The paper's CIF workload as 4:2:0 planes: Y 352x288 and U, V 176x144,
+    each H 3/8 and V 4/9 (outputs 132x128 and 66x64), one ds_batch_run."""
+    import torch
+
+    from tests.gpu_util import out_buffer, stream, to_dev, finish
+    py = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    pc = ds.ds_plan_create_ex(144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        assert ds.ds_plan_out_shape(py) == (128, 132, 1) and ds.ds_plan_out_shape(pc) == (64, 66, 1)
+        n = 4
+        ys, us, vs = frames((288, 352), ds.DS_U8, n, 1), frames((144, 176), ds.DS_U8, n, 2), frames((144, 176), ds.DS_U8, n, 3)
+        ins = [to_dev(a) for a in (ys, us, vs)]
+        outs = [out_buffer(py, n), out_buffer(pc, n), out_buffer(pc, n)]
+        ds.ds_batch_run([(py, ins[0].data_ptr(), outs[0].data_ptr(), n), (pc, ins[1].data_ptr(), outs[1].data_ptr(), n),
+                         (pc, ins[2].data_ptr(), outs[2].data_ptr(), n)], stream())
+        finish()
+        for o, x in zip(outs, (ys, us, vs)):
+            assert_parity(o.cpu().numpy(), oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8)
+    finally:
+        ds.ds_destroy(py)
+        ds.ds_destroy(pc)
