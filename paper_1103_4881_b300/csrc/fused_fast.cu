@@ -61,7 +61,7 @@ __device__ unsigned int g_warps_done[kSchedSlots];
 namespace {
 
 constexpr int kMaxJobs = 64;                  // job descriptors per launch
-constexpr int kMaxTaps = 24;                  // p*K of the fast classes
+constexpr int kMaxTaps = 32;                  // p*K of the fast classes (per axis)
 constexpr long long kWaitLimitCycles = 2000000000ll;  // ~1 s at the B300's 2.03 GHz
 constexpr uint32_t kSuspendHintNs = 20000;             // a waiting thread sleeps up to 20 us per poll
 constexpr int kStatusTimeout = 1;
@@ -87,16 +87,20 @@ struct TmaType<__half> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_
 template <>
 struct TmaType<uint8_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_UINT8; };
 
-// A fast-path class: data type, channels, ratio P/Q, taps K, and the tile
-// shape -- NB packets (of Q input pixels) per lane and row, so a warp's strip
-// is 32*NB packets wide; SR input rows per pipeline stage, NST stages per warp;
+// A fast-path class: data type, channels, horizontal ratio P/Q and taps K,
+// vertical ratio PV/QV and taps KV (by default those of the horizontal axis),
+// and the tile shape -- NB packets (of Q input pixels) per lane and row, so a
+// warp's strip is 32*NB packets wide; SR input rows per pipeline stage, NST
+// stages per warp;
 // FP: whether interior units run a second, check-free copy of the loop body
 // (faster for some classes, slower where the larger code costs more than the
 // checks, measured per class).
-template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_, bool FP_>
+template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_, bool FP_, int PV_ = P_,
+          int QV_ = Q_, int KV_ = K_>
 struct Cls {
   using T = T_;
   static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
+  static constexpr int PV = PV_, QV = QV_, KV = KV_;
   static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
   // resident CTAs per SM the registers are budgeted for (4 x 4 warps; the
   // uint8 1/2 class fits in the tighter budget of 5, which measures faster)
@@ -104,9 +108,10 @@ struct Cls {
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
+  // horizontal axis: the strip, its halo columns and the lane chunks
   static constexpr int BMIN = phase_b(P, Q, K, 0);
   static constexpr int BMAX = phase_b(P, Q, K, P - 1);
-  static constexpr int L = BMAX - BMIN + K;         // pattern length (rows or pixels per block window)
+  static constexpr int L = BMAX - BMIN + K;         // pattern length (pixels per block window)
   static constexpr int LH = -BMIN;                  // halo pixels left of a block
   static constexpr int RH = BMAX + K - Q;           // halo pixels right of a block
   static constexpr int E = NB * Q * C;              // elements per lane and row
@@ -131,26 +136,32 @@ struct Cls {
   static constexpr int NVT = HB + NV + HA;             // vectors per lane and row
   static constexpr int NWT = NVT * VB / 4;             // words per lane and row
   static constexpr int NOUT = NB * P * C;              // H outputs per lane and row
-  // The stream of a tile is cut so that the window prologue (the first L-Q
+  // vertical axis: the row stream and the register window
+  static constexpr int BMINV = phase_b(PV, QV, KV, 0);
+  static constexpr int BMAXV = phase_b(PV, QV, KV, PV - 1);
+  static constexpr int LV = BMAXV - BMINV + KV;     // pattern length (rows per block window)
+  static constexpr int LHV = -BMINV;                // halo rows above a block
+  // The stream of a tile is cut so that the window prologue (the first LV-QV
   // pattern rows) fills whole stages, EXTRA rows being loaded before the first
-  // pattern row; after it, every group of U = lcm(SR, Q) rows is USTG stages
+  // pattern row; after it, every group of U = lcm(SR, QV) rows is USTG stages
   // and UBLK block steps, so each row's stage offset and window slot are
   // compile-time constants.
-  static constexpr int PRE = L - Q;
+  static constexpr int PRE = LV - QV;
   static constexpr int NPS = cdiv(PRE, SR_);
   static constexpr int EXTRA = NPS * SR_ - PRE;
-  static constexpr int U = SR_ / cgcd(SR_, Q) * Q;
+  static constexpr int U = SR_ / cgcd(SR_, QV) * QV;
   static constexpr int USTG = U / SR_;
-  static constexpr int UBLK = U / Q;
+  static constexpr int UBLK = U / QV;
   __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
+  __host__ __device__ static constexpr int bv(int j) { return phase_b(PV, QV, KV, j); }
   static_assert(EB % 4 == 0, "a lane's chunk must be whole words");
   static_assert(HB * VB <= HLB && HA * VB <= RHB, "halo vectors must lie in the loaded window");
   static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
   static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
-  static_assert(P * K <= kMaxTaps, "tap table size");
+  static_assert(P * K <= kMaxTaps && PV * KV <= kMaxTaps, "tap table size");
   static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
-  static_assert(PRE > LH, "the window prologue must reach frame row 0");
-  static_assert(L * (SZ == 1 ? (NOUT + 3) / 4 : NOUT) <= 48, "register window too large");
+  static_assert(PRE > LHV, "the window prologue must reach frame row 0");
+  static_assert(LV * (SZ == 1 ? (NOUT + 3) / 4 : NOUT) <= 48, "register window too large");
   static_assert(U <= 16, "iteration unit too long to unroll");
 };
 
@@ -165,6 +176,10 @@ using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3, true>;
 using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3, false>;
 using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, false>;
 using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false>;
+// the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
+//                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV
+using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
+using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
 
 // ---------------------------------------------------------------------------
 // launch parameters
@@ -183,13 +198,16 @@ static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor
 // uint8 class][window-start parity][phase][pair]: for parity a, pair i holds
 // taps 2i - a (low half) and 2i + 1 - a (high half), zero outside 0..K-1, so
 // a window that starts on an odd slot is read from the even slot before it.
-constexpr int kU8Classes = 3;
+constexpr int kU8Classes = kFcCount - kFcU8C3_38;
 constexpr int kMaxPairs = 5;  // (K + 1) / 2 + 1 for K <= 8
+constexpr int kMaxPhases = 4;
 
 struct FastParams {
   JobDesc jobs[kMaxJobs];
-  float taps[kFcCount][kMaxTaps];  // FP32 taps, or Q14 taps as floats for uint8
-  uint32_t tap2[kU8Classes][2][3][kMaxPairs];
+  float taps[kFcCount][kMaxTaps];   // horizontal FP32 taps, or Q14 taps as floats for uint8
+  float tapsv[kFcCount][kMaxTaps];  // the same for the vertical axis
+  uint32_t tap2h[kU8Classes][2][kMaxPhases][kMaxPairs];
+  uint32_t tap2v[kU8Classes][2][kMaxPhases][kMaxPairs];
   int n_jobs;
   int total_tiles;
   int sched_slot;                  // row kernel: dynamic scheduling slot
@@ -465,24 +483,24 @@ struct RowMath<Cl, false> {
 #pragma unroll
     for (int k = 0; k < N; ++k) d.v[k] = s.v[k];
   }
-  // the P output rows of block rr from the window (CHECK: rows past OH are
+  // the PV output rows of block rr from the window (CHECK: rows past OH are
   // skipped; without it the caller knows they are all inside)
   template <bool CHECK>
-  __device__ static __forceinline__ void v(const Row (&win)[Cl::L], const FastParams& prm, T* obase,
+  __device__ static __forceinline__ void v(const Row (&win)[Cl::LV], const FastParams& prm, T* obase,
                                            long long rowe, int rr, int OH, int n_valid) {
-    const float* taps = prm.taps[Cl::id];
+    const float* taps = prm.tapsv[Cl::id];
 #pragma unroll
-    for (int jv = 0; jv < Cl::P; ++jv) {
-      const int oy = rr * Cl::P + jv;
+    for (int jv = 0; jv < Cl::PV; ++jv) {
+      const int oy = rr * Cl::PV + jv;
       if (!CHECK || oy < OH) {
         float acc[N];
 #pragma unroll
         for (int k = 0; k < N; ++k) acc[k] = 0.0f;
 #pragma unroll
-        for (int tt = 0; tt < Cl::K; ++tt) {
-          const float wt = taps[jv * Cl::K + tt];
+        for (int tt = 0; tt < Cl::KV; ++tt) {
+          const float wt = taps[jv * Cl::KV + tt];
 #pragma unroll
-          for (int k = 0; k < N; ++k) acc[k] = fmaf(wt, win[Cl::b(jv) - Cl::BMIN + tt].v[k], acc[k]);
+          for (int k = 0; k < N; ++k) acc[k] = fmaf(wt, win[Cl::bv(jv) - Cl::BMINV + tt].v[k], acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < N; ++k) acc[k] = pass_round<T>(acc[k]);
@@ -573,16 +591,18 @@ __device__ __forceinline__ void store_bytes(uint8_t* o, const uint32_t* w, int n
 template <class Cl>
 struct RowMath<Cl, true> {
   using T = uint8_t;
-  static constexpr int C = Cl::C, Q = Cl::Q, P = Cl::P, K = Cl::K, L = Cl::L, BMIN = Cl::BMIN;
+  static constexpr int C = Cl::C, Q = Cl::Q, P = Cl::P, K = Cl::K, BMIN = Cl::BMIN;  // horizontal
+  static constexpr int PV = Cl::PV, KV = Cl::KV, LV = Cl::LV, BMINV = Cl::BMINV;      // vertical
   static constexpr int N = Cl::NOUT;
   static constexpr int NW = (N + 3) / 4;
   static constexpr int NXP = Cl::LH + Cl::NB * Q + Cl::RH;  // window pixels of a lane
   static constexpr int NCW = (NXP + 1 + 3) / 4;             // channel words (+1: odd-start pad)
-  static constexpr int NPR = (L + 2) / 2;                   // window row pairs (+1 slot of pad)
+  static constexpr int NPR = (LV + 2) / 2;                  // window row pairs (+1 slot of pad)
   static constexpr int U8I = Cl::id - kFcU8C3_38;
   static_assert(Cl::HB * Cl::VB >= Cl::LH * C, "pixel slot 0 must be a loaded byte");
   static_assert(Cl::HB * Cl::VB - Cl::LH * C + NXP * C <= Cl::NVT * Cl::VB, "gathered bytes must be loaded");
-  static_assert(U8I >= 0 && U8I < kU8Classes && P <= 3 && (K + 2) / 2 <= kMaxPairs, "tap pair table");
+  static_assert(U8I >= 0 && U8I < kU8Classes && P <= kMaxPhases && PV <= kMaxPhases &&
+                    (K + 2) / 2 <= kMaxPairs && (KV + 2) / 2 <= kMaxPairs, "tap pair table");
   struct Row {
     uint32_t w[NW];
   };
@@ -591,7 +611,10 @@ struct RowMath<Cl, true> {
     for (int k = 0; k < NW; ++k) d.w[k] = s.w[k];
   }
   __device__ static __forceinline__ uint32_t tp(const FastParams& prm, int par, int j, int i) {
-    return prm.tap2[U8I][par][j][i];
+    return prm.tap2h[U8I][par][j][i];
+  }
+  __device__ static __forceinline__ uint32_t tpv(const FastParams& prm, int par, int j, int i) {
+    return prm.tap2v[U8I][par][j][i];
   }
   __device__ static __forceinline__ void h(const uint32_t* w, const FastParams& prm, Row& r) {
     constexpr int first = Cl::HB * Cl::VB - Cl::LH * C;  // byte of pixel slot 0, channel 0
@@ -634,24 +657,24 @@ struct RowMath<Cl, true> {
     }
   }
   template <bool CHECK>
-  __device__ static __forceinline__ void v(const Row (&win)[L], const FastParams& prm, T* obase, long long rowe,
+  __device__ static __forceinline__ void v(const Row (&win)[LV], const FastParams& prm, T* obase, long long rowe,
                                            int rr, int OH, int n_valid) {
     // one word column g (4 output columns) at a time: row-pair words
     // pl = bytes 0,1 of rows 2m and 2m+1 interleaved, ph = bytes 2,3
-    uint32_t o[P][NW];
+    uint32_t o[PV][NW];
 #pragma unroll
     for (int g = 0; g < NW; ++g) {
       uint32_t pl[NPR], ph[NPR];
 #pragma unroll
       for (int m = 0; m < NPR; ++m) {
-        const int r0 = 2 * m < L ? 2 * m : L - 1, r1 = 2 * m + 1 < L ? 2 * m + 1 : L - 1;
+        const int r0 = 2 * m < LV ? 2 * m : LV - 1, r1 = 2 * m + 1 < LV ? 2 * m + 1 : LV - 1;
         pl[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x5140u);
         ph[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x7362u);
       }
 #pragma unroll
-      for (int jv = 0; jv < P; ++jv) {
-        const int s0 = Cl::b(jv) - BMIN;
-        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
+      for (int jv = 0; jv < PV; ++jv) {
+        const int s0 = Cl::bv(jv) - BMINV;
+        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (KV + par + 1) / 2;
         int v[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -659,7 +682,7 @@ struct RowMath<Cl, true> {
 #pragma unroll
           for (int i = 0; i < npair; ++i) {
             const uint32_t word = (e & 2) ? ph[pr0 + i] : pl[pr0 + i];
-            acc = (e & 1) ? dp2a<1>(tp(prm, par, jv, i), word, acc) : dp2a<0>(tp(prm, par, jv, i), word, acc);
+            acc = (e & 1) ? dp2a<1>(tpv(prm, par, jv, i), word, acc) : dp2a<0>(tpv(prm, par, jv, i), word, acc);
           }
           v[e] = u8_round(acc);
         }
@@ -667,8 +690,8 @@ struct RowMath<Cl, true> {
       }
     }
 #pragma unroll
-    for (int jv = 0; jv < P; ++jv) {
-      const int oy = rr * P + jv;
+    for (int jv = 0; jv < PV; ++jv) {
+      const int oy = rr * PV + jv;
       if (!CHECK || oy < OH) store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
     }
   }
@@ -679,7 +702,9 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
   using T = typename Cl::T;
   using RM = RowMath<Cl>;
   using Row = typename RM::Row;
-  constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P, SR = Cl::SRR, NST = Cl::NST;
+  // L, Q, P: the vertical axis (row stream, window, output rows); the
+  // horizontal one is Cl::P / Cl::Q / Cl::K
+  constexpr int L = Cl::LV, Q = Cl::QV, P = Cl::PV, SR = Cl::SRR, NST = Cl::NST;
   extern __shared__ uint8_t smem_raw[];
   // 128-byte aligned start, derived from the __shared__ array by an offset
   // (not through an integer cast) so that every access stays a shared-memory
@@ -719,16 +744,17 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     const int nby = (jd.OH + P - 1) / P;
     const int rb0 = tl.chunk * jd.rbc;
     const int nblk = min(jd.rbc, nby - rb0);
-    const int ys = rb0 * Q + Cl::BMIN;  // first pattern row; < 0 only for the top band (then == BMIN)
+    const int ys = rb0 * Q + Cl::BMINV;  // first pattern row; < 0 only for the top band (then == BMINV)
     const int nst = Cl::NPS + (nblk * Q + SR - 1) / SR;
     const int ystream = ys - Cl::EXTRA;  // frame row of stage 0's first row
     const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
     const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
     const bool fixing = fix.nl + fix.nr > 0;
     const int blk0 = tl.strip * Cl::SBLK + lane * Cl::NB;
-    const bool active = blk0 * P < jd.OW;
-    const int n_valid = jd.OW * Cl::C - blk0 * P * Cl::C;
-    T* const obase = reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)blk0 * P * Cl::C;
+    const bool active = blk0 * Cl::P < jd.OW;
+    const int n_valid = jd.OW * Cl::C - blk0 * Cl::P * Cl::C;
+    T* const obase =
+        reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)blk0 * Cl::P * Cl::C;
     const long long rowe = (long long)jd.OW * Cl::C;
 
     auto issue = [&](int s) {  // stage s of the tile into slot (g + s) mod NST
@@ -788,9 +814,9 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       stage_release(ps);
     }
     if (!ok) break;
-    if (ys < 0) {  // ys == BMIN: slots 0..LH-1 are frame row 0, held in slot LH
+    if (ys < 0) {  // ys == BMINV: slots 0..LHV-1 are frame row 0, held in slot LHV
 #pragma unroll
-      for (int i = 0; i < Cl::LH; ++i) RM::copy(win[i], win[Cl::LH]);
+      for (int i = 0; i < Cl::LHV; ++i) RM::copy(win[i], win[Cl::LHV]);
     }
     // ---- block steps, U rows (USTG stages, UBLK blocks) at a time.  A unit
     // whose blocks are all inside the tile, whose rows are all above the
@@ -836,7 +862,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
         stage_release(s);
       }
     };
-    const bool x_inside = !fixing && (tl.strip * Cl::SBLK + 32 * Cl::NB) * P <= jd.OW;  // every lane complete
+    const bool x_inside = !fixing && (tl.strip * Cl::SBLK + 32 * Cl::NB) * Cl::P <= jd.OW;  // every lane complete
     const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
     for (int u = 0; ok && u < nunits; ++u) {
       if constexpr (Cl::FASTPATH) {
@@ -889,13 +915,14 @@ __global__ void k_timeout_probe(long long limit) {
 // host side
 // ---------------------------------------------------------------------------
 struct HostGeom {
-  int sblk, spx, p, q, boxe, sr, sz, c;
+  int sblk, spx, p, q, pv, boxe, sr, sz, c;
   CUtensorMapDataType dt;
 };
 
 template <class Cl>
 HostGeom host_geom() {
-  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, TmaType<typename Cl::T>::v};
+  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C,
+                  TmaType<typename Cl::T>::v};
 }
 
 // Geometry of the kernel that runs class `cls`.
@@ -909,6 +936,8 @@ HostGeom geom_of(int cls) {
     case kFcF16_23: return host_geom<RF16_23>();
     case kFcU8C3_38: return host_geom<RU8_38>();
     case kFcU8C3_12: return host_geom<RU8_12>();
+    case kFcU8C3_CIF: return host_geom<RU8_CIF>();
+    case kFcU8C1_CIF: return host_geom<RU8P_CIF>();
     default: return host_geom<RU8_23>();
   }
 }
@@ -953,6 +982,8 @@ KernelInfo kernel_for(int cls) {
     case kFcF16_23: return rows_info<RF16_23>();
     case kFcU8C3_38: return rows_info<RU8_38>();
     case kFcU8C3_12: return rows_info<RU8_12>();
+    case kFcU8C3_CIF: return rows_info<RU8_CIF>();
+    case kFcU8C1_CIF: return rows_info<RU8P_CIF>();
     default: return rows_info<RU8_23>();
   }
 }
@@ -982,38 +1013,65 @@ int sm_count() {
   return n;
 }
 
+// int16 tap pairs of one axis for dp2a (see FastParams::tap2h).
+void pair_taps(const short* q14, int p, int K, uint32_t (*out)[kMaxPhases][kMaxPairs]) {
+  for (int par = 0; par < 2; ++par)
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < kMaxPairs; ++i) {
+        const int ta = 2 * i - par, tb = 2 * i + 1 - par;
+        const int qa = (ta >= 0 && ta < K) ? q14[j * K + ta] : 0;
+        const int qb = (tb >= 0 && tb < K) ? q14[j * K + tb] : 0;
+        out[par][j][i] = (uint32_t)(uint16_t)(int16_t)qa | ((uint32_t)(uint16_t)(int16_t)qb << 16);
+      }
+}
+
 void fill_taps(FastParams& prm) {
-  // the fast classes' taps depend only on (p, q, K): build them once with a
-  // throwaway plan of each class
+  // the fast classes' taps depend only on their axes: build them once with
+  // a throwaway plan of each class
   static FastParams taps_only;
   static std::once_flag once;
   std::call_once(once, [] {
     std::memset(&taps_only, 0, sizeof(taps_only));
+    struct Axes {
+      int p, q, K, pv, qv, Kv;
+      ds_dtype dt;
+    };
+    std::vector<Axes> all;
     const int pq[3][3] = {{3, 8, 8}, {1, 2, 6}, {2, 3, 6}};
     const ds_dtype dts[3] = {DS_F32, DS_F16, DS_U8_RGB};
     for (int d = 0; d < 3; ++d)
-      for (int r = 0; r < 3; ++r) {
-        ds_plan* pl = ds_plan_create(64, 64, ds_ratio{pq[r][0], pq[r][1]}, pq[r][2], dts[d]);
-        if (!pl) continue;
-        const int cls = pl->fast_class;
-        for (int i = 0; i < pl->p * pl->K; ++i)
-          taps_only.taps[cls][i] = (dts[d] == DS_U8_RGB) ? (float)pl->q14[i] : pl->w32[i];
-        if (dts[d] == DS_U8_RGB) {
-          const int u = cls - kFcU8C3_38;
-          for (int par = 0; par < 2; ++par)
-            for (int j = 0; j < pl->p; ++j)
-              for (int i = 0; i < kMaxPairs; ++i) {
-                const int ta = 2 * i - par, tb = 2 * i + 1 - par;
-                const int qa = (ta >= 0 && ta < pl->K) ? pl->q14[j * pl->K + ta] : 0;
-                const int qb = (tb >= 0 && tb < pl->K) ? pl->q14[j * pl->K + tb] : 0;
-                taps_only.tap2[u][par][j][i] = (uint32_t)(uint16_t)(int16_t)qa | ((uint32_t)(uint16_t)(int16_t)qb << 16);
-              }
-        }
+      for (int r = 0; r < 3; ++r) all.push_back({pq[r][0], pq[r][1], pq[r][2], pq[r][0], pq[r][1], pq[r][2], dts[d]});
+    all.push_back({3, 8, 8, 4, 9, 8, DS_U8_RGB});
+    all.push_back({3, 8, 8, 4, 9, 8, DS_U8});
+    for (const Axes& a : all) {
+      ds_plan_desc d{};
+      d.in_h = d.in_w = 72;
+      d.ratio_h = ds_ratio{a.p, a.q};
+      d.taps_h = a.K;
+      d.ratio_v = ds_ratio{a.pv, a.qv};
+      d.taps_v = a.Kv;
+      d.dtype = a.dt;
+      d.boundary = DS_CLAMP;
+      ds_plan* pl = ds_plan_create_ex(&d);
+      if (!pl || pl->fast_class < 0) {
         ds_destroy(pl);
+        continue;
       }
+      const int cls = pl->fast_class;
+      const bool u8 = a.dt == DS_U8 || a.dt == DS_U8_RGB;
+      for (int i = 0; i < pl->p * pl->K; ++i) taps_only.taps[cls][i] = u8 ? (float)pl->q14[i] : pl->w32[i];
+      for (int i = 0; i < pl->pv * pl->Kv; ++i) taps_only.tapsv[cls][i] = u8 ? (float)pl->q14v[i] : pl->w32v[i];
+      if (u8) {
+        pair_taps(pl->q14, pl->p, pl->K, taps_only.tap2h[cls - kFcU8C3_38]);
+        pair_taps(pl->q14v, pl->pv, pl->Kv, taps_only.tap2v[cls - kFcU8C3_38]);
+      }
+      ds_destroy(pl);
+    }
   });
   std::memcpy(prm.taps, taps_only.taps, sizeof(prm.taps));
-  std::memcpy(prm.tap2, taps_only.tap2, sizeof(prm.tap2));
+  std::memcpy(prm.tapsv, taps_only.tapsv, sizeof(prm.tapsv));
+  std::memcpy(prm.tap2h, taps_only.tap2h, sizeof(prm.tap2h));
+  std::memcpy(prm.tap2v, taps_only.tap2v, sizeof(prm.tap2v));
 }
 
 // Tile geometry of a job (everything but the tensor map).  `band`: output
@@ -1029,7 +1087,7 @@ void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, 
   jd.nframes = n_frames;
   jd.cls = pl->fast_class;
   const int nbx = (pl->out_w + hg.p - 1) / hg.p;
-  const int nby = (pl->out_h + hg.p - 1) / hg.p;
+  const int nby = (pl->out_h + hg.pv - 1) / hg.pv;
   jd.strips = (nbx + hg.sblk - 1) / hg.sblk;
   jd.rbc = std::max(1, std::min(band > 0 ? band : pl->row_blocks, nby));
   jd.chunks = (nby + jd.rbc - 1) / jd.rbc;
@@ -1085,7 +1143,7 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
     const ds_plan* pl = jobs[i].plan;
     fixed = fixed || pl->schedule_set;
     const HostGeom hg = geom_of(pl->fast_class);
-    const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.p - 1) / hg.p;
+    const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.pv - 1) / hg.pv;
     per_frame[i] = (nbx + hg.sblk - 1) / hg.sblk * nby;
     units += per_frame[i] * jobs[i].n_frames;
     cap = std::max(cap, pl->row_blocks);
@@ -1147,7 +1205,8 @@ std::string check_rows(const JobDesc& jd) {
   if (smem > 227 * 1024) return fail("shared memory above 227 KB", smem, 0);
   if (Cl::BOXSTR < Cl::SRR * Cl::BOXB) return fail("stage layout", Cl::BOXSTR, 0);
   const int win = Cl::NBOX * Cl::BOXB;
-  constexpr int L = Cl::L, Q = Cl::Q, P = Cl::P;
+  // L, Q, P: the vertical axis; PH: the horizontal phases per packet
+  constexpr int L = Cl::LV, Q = Cl::QV, P = Cl::PV, PH = Cl::P;
   std::vector<int> written((size_t)jd.OH * jd.OW * Cl::C, 0);
   const int nby = (jd.OH + P - 1) / P;
   for (int chunk = 0; chunk < jd.chunks; ++chunk) {
@@ -1155,11 +1214,11 @@ std::string check_rows(const JobDesc& jd) {
       const int rb0 = chunk * jd.rbc;
       const int nblk = std::min(jd.rbc, nby - rb0);
       if (nblk < 1) return fail("empty tile", chunk, strip);
-      const int ys = rb0 * Q + Cl::BMIN;
-      const int ye = (rb0 + nblk - 1) * Q + Cl::BMIN + L;
+      const int ys = rb0 * Q + Cl::BMINV;
+      const int ye = (rb0 + nblk - 1) * Q + Cl::BMINV + L;
       const int y0 = std::max(ys, 0), nrow = std::min(ye, jd.H) - y0;
       if (nrow < 1) return fail("empty stream", ys, ye);
-      if (ys < 0 && ys != Cl::BMIN) return fail("top band offset", ys, 0);
+      if (ys < 0 && ys != Cl::BMINV) return fail("top band offset", ys, 0);
       const int xw = strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
       for (int bx = 0; bx < Cl::NBOX; ++bx) {
         const long long xb = (long long)(xw + bx * Cl::BOXE) * Cl::SZ;
@@ -1182,7 +1241,7 @@ std::string check_rows(const JobDesc& jd) {
             return fail("vector read", lane, b0);
         }
         const int blk0 = strip * Cl::SBLK + lane * Cl::NB, px0 = blk0 * Cl::Q;
-        if (blk0 * P >= jd.OW) continue;
+        if (blk0 * PH >= jd.OW) continue;
         for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
           if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lane, px);
           if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lane, px);
@@ -1212,7 +1271,7 @@ std::string check_rows(const JobDesc& jd) {
           if (wrow[i] != y) return fail("prologue row mismatch", i, wrow[i]);
         }
       if (ys < 0)
-        for (int i = 0; i < Cl::LH; ++i) wrow[i] = wrow[Cl::LH];
+        for (int i = 0; i < Cl::LHV; ++i) wrow[i] = wrow[Cl::LHV];
       const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
       for (int u = 0; u < nunits; ++u)
         for (int st = 0; st < Cl::USTG; ++st) {
@@ -1231,18 +1290,18 @@ std::string check_rows(const JobDesc& jd) {
             if (q != Q - 1) continue;
             const int rr = rb0 + m;
             for (int i2 = 0; i2 < L; ++i2) {
-              int want = rr * Q + Cl::BMIN + i2;
+              int want = rr * Q + Cl::BMINV + i2;
               want = want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want);
               if (wrow[i2] != want) return fail("window row mismatch", i2, wrow[i2]);
             }
             for (int lane = 0; lane < 32; ++lane) {
               const int blk0 = strip * Cl::SBLK + lane * Cl::NB;
-              if (blk0 * P >= jd.OW) continue;
-              const int nv = std::min(Cl::NOUT, jd.OW * Cl::C - blk0 * P * Cl::C);
+              if (blk0 * PH >= jd.OW) continue;
+              const int nv = std::min(Cl::NOUT, jd.OW * Cl::C - blk0 * PH * Cl::C);
               for (int jv = 0; jv < P; ++jv) {
                 const int oy = rr * P + jv;
                 if (oy >= jd.OH) continue;
-                for (int k = 0; k < nv; ++k) written[((size_t)oy * jd.OW) * Cl::C + (size_t)blk0 * P * Cl::C + k]++;
+                for (int k = 0; k < nv; ++k) written[((size_t)oy * jd.OW) * Cl::C + (size_t)blk0 * PH * Cl::C + k]++;
               }
             }
             for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
@@ -1270,6 +1329,8 @@ std::string check_plan(const ds_plan* pl) {
     case kFcU8C3_38: return check_rows<RU8_38, kRowsWPC>(jd);
     case kFcU8C3_12: return check_rows<RU8_12, kRowsWPC>(jd);
     case kFcU8C3_23: return check_rows<RU8_23, kRowsWPC>(jd);
+    case kFcU8C3_CIF: return check_rows<RU8_CIF, kRowsWPC>(jd);
+    case kFcU8C1_CIF: return check_rows<RU8P_CIF, kRowsWPC>(jd);
     default: return std::string();
   }
 }

@@ -31,6 +31,8 @@ enum FastClass : int {
   kFcU8C3_38,     // uint8 RGB, 3/8, K=8
   kFcU8C3_12,     // uint8 RGB, 1/2, K=6
   kFcU8C3_23,     // uint8 RGB, 2/3, K=6
+  kFcU8C3_CIF,    // uint8 RGB, horizontal 3/8 K=8, vertical 4/9 K=8 (the paper's CIF case)
+  kFcU8C1_CIF,    // uint8 one plane (4:2:0 Y, U, V), the same axes
   kFcCount
 };
 
@@ -77,7 +79,7 @@ ds_status cuda_fail(cudaError_t e, const char* what);
 void count_launches(long long n);
 
 // Plan helpers (plan.cpp).
-int fast_class_of(int p, int q, int K, ds_dtype dtype);
+int fast_class_of(int p, int q, int K, int pv, int qv, int Kv, ds_dtype dtype);
 bool frame_tma_ok(const ds_plan* plan, const void* in, size_t frame_stride_bytes);
 
 // Kernel launchers.

@@ -130,6 +130,7 @@ int default_row_blocks(int fast_class) {
     case kFcU8C3_38: return 16;
     case kFcF32_12: case kFcF16_12: case kFcU8C3_12: return 24;
     case kFcF32_23: case kFcF16_23: case kFcU8C3_23: return 20;
+    case kFcU8C3_CIF: case kFcU8C1_CIF: return 8;
     default: return 0;
   }
 }
@@ -153,7 +154,13 @@ ds_status cuda_fail(cudaError_t e, const char* what) {
 
 void count_launches(long long n) { g_launches += n; }
 
-int fast_class_of(int p, int q, int K, ds_dtype dtype) {
+int fast_class_of(int p, int q, int K, int pv, int qv, int Kv, ds_dtype dtype) {
+  if (p == 3 && q == 8 && K == 8 && pv == 4 && qv == 9 && Kv == 8) {
+    if (dtype == DS_U8_RGB) return kFcU8C3_CIF;
+    if (dtype == DS_U8) return kFcU8C1_CIF;
+    return kFcNone;
+  }
+  if (p != pv || q != qv || K != Kv) return kFcNone;
   int r = -1;
   if (p == 3 && q == 8 && K == 8) r = 0;
   if (p == 1 && q == 2 && K == 6) r = 1;
@@ -257,10 +264,9 @@ ds_plan* create_plan(const ds_plan_desc& d, const char* who) {
     delete pl;
     return nullptr;
   }
-  // the fast kernels take one ratio for both axes, clamp-to-edge and the
-  // library's own taps
-  pl->fast_class = (same && d.boundary == DS_CLAMP && !pl->given_taps)
-                       ? fast_class_of(pl->p, pl->q, pl->K, d.dtype) : kFcNone;
+  // the fast kernels take clamp-to-edge and the library's own taps
+  pl->fast_class = (d.boundary == DS_CLAMP && !pl->given_taps)
+                       ? fast_class_of(pl->p, pl->q, pl->K, pl->pv, pl->qv, pl->Kv, d.dtype) : kFcNone;
   pl->row_blocks = default_row_blocks(pl->fast_class);
   if (pl->row_blocks == 0) pl->row_blocks = 8;
   const char* no_tma = std::getenv("DS_NO_TMA");
@@ -391,7 +397,9 @@ ds_status ds_plan_describe(const ds_plan* pl, char* buf, size_t len) {
     return DS_ERR_ARG;
   }
   static const char* names[] = {"f32_3_8_k8", "f32_1_2_k6", "f32_2_3_k6", "f16_3_8_k8", "f16_1_2_k6",
-                                "f16_2_3_k6", "u8rgb_3_8_k8", "u8rgb_1_2_k6", "u8rgb_2_3_k6"};
+                                "f16_2_3_k6", "u8rgb_3_8_k8", "u8rgb_1_2_k6", "u8rgb_2_3_k6",
+                                "u8rgb_h3_8_v4_9_k8", "u8_h3_8_v4_9_k8"};
+  static_assert(sizeof(names) / sizeof(names[0]) == kFcCount, "a name per fast class");
   const bool fast = pl->fast_class >= 0 && !pl->force_general;
   std::snprintf(buf, len,
                 "{\"kernel\": \"%s\", \"class\": \"%s\", \"in\": [%d, %d, %d], \"out\": [%d, %d, %d], "

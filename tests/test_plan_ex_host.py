@@ -30,7 +30,7 @@ def test_axes_shapes_and_taps_match_the_oracle(oracle):
     try:
         assert ds.ds_plan_out_shape(pl) == (128, 132, 3)
         assert ds.ds_plan_get_axes(pl) == ((3, 8, 8), (4, 9, 8), ds.DS_CLAMP)
-        assert '"fused_general"' in ds.ds_plan_describe(pl)
+        assert '"fused_tma"' in ds.ds_plan_describe(pl) and "u8rgb_h3_8_v4_9_k8" in ds.ds_plan_describe(pl)
         for axis, (p, q, K) in enumerate([(3, 8, 8), (4, 9, 8)]):
             t = ds.ds_plan_get_axis_taps(pl, axis)
             np.testing.assert_allclose(t["fp64"], oracle.taps_f64(p, q, K), rtol=0, atol=1e-15)
@@ -74,3 +74,19 @@ def test_equal_axes_keep_the_fast_kernel():
             assert '"fused_general"' in ds.ds_plan_describe(pl)
         finally:
             ds.ds_destroy(pl)
+
+
+def test_cif_classes_take_the_fast_kernel_and_pass_the_host_check():
+    checked = 0
+    for dt in (ds.DS_U8_RGB, ds.DS_U8):
+        for H, W in [(288, 352), (144, 176), (9, 16), (30, 48), (100, 272), (1080, 1920), (17, 512), (288, 368)]:
+            pl = ds.ds_plan_create_ex(H, W, (3, 8), 8, (4, 9), 8, dt)
+            try:
+                assert '"fused_tma"' in ds.ds_plan_describe(pl)
+                for rb in (1, 2, 3, 7, 12, 1000):
+                    ds.ds_plan_set_schedule(pl, rb, 0)
+                    ds.ds_debug_check_plan(pl)
+                    checked += 1
+            finally:
+                ds.ds_destroy(pl)
+    assert checked == 2 * 8 * 6
