@@ -142,29 +142,39 @@ class ClockSampler:
         return out
 
 
+def oracle_filter(w, x, threads=0):
+    """The oracle on one plane of workload w (its ratio and taps per axis)."""
+    import oracle
+    from paper_1103_4881_b300 import synth
+
+    if w.dtype in (synth.DS_U8, synth.DS_U8_RGB):
+        return oracle.filter_ex(x, w.ratio, w.taps, w.vratio, w.vtaps, threads=threads)
+    return oracle.filter_ex(x.astype("float64"), w.ratio, w.taps, w.vratio, w.vtaps, threads=threads)
+
+
 def time_cpu_oracle(w, budget_s=15.0):
     """The oracle as it stands on this host's cores: whole frames of the
-    workload, OpenMP over frames, as many frames as fit the time budget."""
-    import numpy as np
-
+    workload (every plane), OpenMP over frames, as many frames as fit the
+    time budget."""
     import oracle
     from paper_1103_4881_b300 import synth
 
     cores = max(1, oracle.max_threads())
     t = time.perf_counter()
-    x = synth.frames(w, range(1))
-    oracle.filter_f64(x, w.ratio[0], w.ratio[1], w.taps, threads=1)
+    for x in synth.plane_frames(w, range(1)):
+        oracle_filter(w, x, threads=1)
     one = time.perf_counter() - t
     n = int(max(1, min(w.frames, cores * max(1, int(budget_s / max(one, 1e-3) / max(cores, 1))), 4 * cores)))
     n = max(1, min(n, w.frames))
-    x = synth.frames(w, range(n))
-    fn = oracle.filter_u8 if w.dtype in (synth.DS_U8, synth.DS_U8_RGB) else oracle.filter_f64
+    xs = synth.plane_frames(w, range(n))
     t = time.perf_counter()
-    fn(x, w.ratio[0], w.ratio[1], w.taps, threads=0)
+    for x in xs:
+        oracle_filter(w, x, threads=0)
     dt = time.perf_counter() - t
-    del x
+    del xs
     return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of the workload's %d frames (whole frames, FP64 loop nest, OpenMP over frames)" % (n, w.frames),
+            "sample": "%d of the workload's %d frames (whole frames, FP64 / int64 loop nest, OpenMP over frames)"
+                      % (n, w.frames),
             "seconds": round(dt, 3)}
 
 
@@ -176,37 +186,56 @@ def reference_arm(args, w, rank, world):
     from paper_1103_4881_b300 import synth
 
     cores = max(1, oracle.max_threads())
-    fn = oracle.filter_u8 if w.dtype in (synth.DS_U8, synth.DS_U8_RGB) else oracle.filter_f64
-    # one step = a band of rows from `cores` frames (one band per thread), sized
-    # so that warmup + steps take about a minute in total
-    x_full = synth.frames(w, range(min(cores, w.frames)))
-    q = w.ratio[1]
+    # one step = a band of rows from `cores` frames (one band per thread) of
+    # every plane, sized so that warmup + steps take about a minute in total
+    planes = synth.plane_frames(w, range(min(cores, w.frames)))
+    qv = w.vratio[1]
     t = time.perf_counter()
-    fn(x_full[:1, : 8 * q], w.ratio[0], q, w.taps, threads=1)
-    per_row = (time.perf_counter() - t) / (8 * q)
+    for x in planes:
+        oracle_filter(w, x[:1, : 8 * qv], threads=1)
+    per_row = (time.perf_counter() - t) / (8 * qv)  # per row of the first plane, all planes
     total = max(1, args.steps + args.warmup)
     rows = int(60.0 / total / max(per_row, 1e-9))
-    rows = max(q, min(w.height, rows - rows % q))
-    sample = x_full[:, :rows]
+    rows = max(qv, min(w.height, rows - rows % qv))
+    frac = rows / w.height
+    samples = []
+    for x in planes:
+        r = max(qv, int(round(x.shape[1] * frac)) // qv * qv)
+        samples.append(x[:, : min(r, x.shape[1])])
     for _ in range(args.warmup):
-        fn(sample, w.ratio[0], q, w.taps, threads=0)
+        for x in samples:
+            oracle_filter(w, x, threads=0)
     t = time.perf_counter()
     for _ in range(args.steps):
-        fn(sample, w.ratio[0], q, w.taps, threads=0)
+        for x in samples:
+            oracle_filter(w, x, threads=0)
     dt = time.perf_counter() - t
-    frames_per_step = sample.shape[0] * rows / w.height
+    frames_per_step = samples[0].shape[0] * rows / w.height
     value = frames_per_step * args.steps / dt
     line = {
         "impl": "reference", "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "frames": w.frames, "in": [w.height, w.width, w.channels],
-                   "out": [w.out_height, w.out_width, w.channels], "ratio": "%d/%d" % w.ratio, "taps": w.taps},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.dtype in (0, 1) else "int64", "data": "synthetic",
+        "config": workload_config(w, w.frames),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
-                         "sample": "per step: the first %d rows of %d frames, one band per thread" % (rows, sample.shape[0])},
+                         "sample": "per step: the first %d rows of %d frames (all planes), one band per thread"
+                                   % (rows, samples[0].shape[0])},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def workload_config(w, n):
+    """The config block of the JSON line."""
+    cfg = {"workload": w.name, "frames_per_step": n, "in": [w.height, w.width, w.channels],
+           "out": list(w.out_frame_shape()) + ([1] if w.channels == 1 else []),
+           "ratio": "%d/%d" % w.ratio, "taps": w.taps}
+    if w.ratio_v:
+        cfg["ratio_v"] = "%d/%d" % w.vratio
+        cfg["taps_v"] = w.vtaps
+    if w.planes:
+        cfg["planes"] = [list(hw) for hw in w.plane_shapes()]
+    return cfg
 
 
 def main():
@@ -241,23 +270,28 @@ def main():
         dist.barrier()
     dev_index = torch.cuda.current_device()
 
-    plan = ds.ds_plan_create(w.height, w.width, w.ratio, w.taps, w.dtype)
-    oh, ow, c = ds.ds_plan_out_shape(plan)
-    fin, fout = ds.ds_plan_frame_bytes(plan)
+    # one plan per plane (a single plane unless the workload is planar)
+    shapes = w.plane_shapes()
+    plans = [ds.ds_plan_create_ex(h, ww, w.ratio, w.taps, w.vratio, w.vtaps, w.dtype) for h, ww in shapes]
+    plan = plans[0]
+    fbytes = [ds.ds_plan_frame_bytes(pl) for pl in plans]
+    fin, fout = fbytes[0]
     # weak scaling: the job is world x w.frames frames, each rank filters its own
     # contiguous share (global frame indices, so no two ranks hold the same frame)
     from paper_1103_4881_b300 import shard
 
     a, b = shard.frame_range(w.frames * world, world, rank)
     n = b - a
-    x = synth.frames(w, range(a, b))
-    xin = torch.from_numpy(x).cuda()
-    out = torch.empty((n,) + w.out_frame_shape(), dtype=xin.dtype, device="cuda")
+    xs = synth.plane_frames(w, range(a, b))
+    xins = [torch.from_numpy(x).cuda() for x in xs]
+    outs = [torch.empty((n,) + w.plane_out_shape(hw), dtype=xins[0].dtype, device="cuda") for hw in shapes]
+    x, xin, out = xs[0], xins[0], outs[0]
     stream = torch.cuda.current_stream()
     st = stream.cuda_stream
 
-    # the step: one batched persistent launch over the n frames, replayed as a CUDA graph
-    job = [(plan, xin.data_ptr(), out.data_ptr(), n)]
+    # the step: one batched persistent launch over the n frames (of every
+    # plane), replayed as a CUDA graph
+    job = [(pl, xi.data_ptr(), o.data_ptr(), n) for pl, xi, o in zip(plans, xins, outs)]
     graph = ds.ds_graph_create(job)
 
     def step():
@@ -295,7 +329,7 @@ def main():
 
     frames_total = n * world * args.steps
     value = frames_total / (ms / 1e3)
-    alg_bytes = n * (fin + fout)  # input read once + output written once, per launch
+    alg_bytes = n * sum(fi + fo for fi, fo in fbytes)  # input read once + output written once, per launch
     launch_s = ms / 1e3 / args.steps
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_src = measured_peak()
@@ -305,11 +339,12 @@ def main():
         "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "u8", 3: "u8"}[w.dtype], "data": "synthetic",
-        "config": {"workload": w.name, "frames_per_step": n, "in": [w.height, w.width, w.channels],
-                   "out": [oh, ow, c], "ratio": "%d/%d" % w.ratio, "taps": w.taps,
+        "config": dict(workload_config(w, n), **{
                    "form": "batched persistent fused H+V kernel, CUDA graph replay",
-                   "l2": "inputs larger than L2 (%.0f MB per step vs 126 MB)" % (n * fin / 1e6),
-                   "parallelism": ("dp%d: frames sharded over ranks, no data-path collective" % world) if world > 1 else "single"},
+                   "l2": ("inputs larger than L2 (%.0f MB per step vs 126 MB)" if n * sum(f[0] for f in fbytes) > 126e6
+                          else "inputs smaller than L2 (%.0f MB per step vs 126 MB): not an HBM figure")
+                         % (n * sum(f[0] for f in fbytes) / 1e6),
+                   "parallelism": ("dp%d: frames sharded over ranks, no data-path collective" % world) if world > 1 else "single"}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
                      "alg_bytes_per_launch": alg_bytes, "kernel_us": launch_s * 1e6},
@@ -319,23 +354,25 @@ def main():
 
     if rank == 0 and not args.no_extras:
         k2 = max(5, min(args.steps // 50, 50))
-        # plain per-frame: one ds_run per frame
+        # plain per-frame: one ds_run per frame (and plane)
         def per_frame():
             for i in range(n):
-                ds.ds_run(plan, xin.data_ptr() + i * fin, out.data_ptr() + i * fout, st)
+                for pl, xi, o, (fi, fo) in zip(plans, xins, outs, fbytes):
+                    ds.ds_run(pl, xi.data_ptr() + i * fi, o.data_ptr() + i * fo, st)
         per_frame()
         ms_pf = timed(per_frame, k2)
         # unfused two-kernel form over the batch
-        wsb = ds.ds_plan_workspace_bytes(plan) * n
+        wsb = max(ds.ds_plan_workspace_bytes(pl) for pl in plans) * n
         ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
         def unfused():
-            ds.ds_run_unfused(plan, xin.data_ptr(), out.data_ptr(), n, ws.data_ptr(), wsb, st)
+            for pl, xi, o in zip(plans, xins, outs):
+                ds.ds_run_unfused(pl, xi.data_ptr(), o.data_ptr(), n, ws.data_ptr(), wsb, st)
         unfused()
         ms_uf = timed(unfused, k2)
         del ws
         # batched without the graph (direct launch)
         def direct():
-            ds.ds_run_frames(plan, xin.data_ptr(), out.data_ptr(), n, st)
+            ds.ds_batch_run(job, st)
         direct()
         ms_dl = timed(direct, k2)
         line["forms"] = {
@@ -343,31 +380,38 @@ def main():
             "batched_direct_fps": n * k2 / (ms_dl / 1e3),
             "per_frame_fused_fps": n * k2 / (ms_pf / 1e3),
             "unfused_two_kernel_fps": n * k2 / (ms_uf / 1e3),
-            "unfused_alg_gbs": n * (fin + fout) * k2 / (ms_uf / 1e3) / 1e9,
+            "unfused_alg_gbs": alg_bytes * k2 / (ms_uf / 1e3) / 1e9,
         }
         # end to end through the C ABI with pinned host buffers (copies in the timed region)
-        host_in = torch.from_numpy(x).pin_memory()
-        host_out = torch.empty((n,) + w.out_frame_shape(), dtype=xin.dtype).pin_memory()
-        pipe = ds.ds_pipeline_create(plan, 4, 3)
-        ds.ds_pipeline_run(pipe, host_in.data_ptr(), host_out.data_ptr(), n)
+        host_ins = [torch.from_numpy(xx).pin_memory() for xx in xs]
+        host_outs = [torch.empty((n,) + w.plane_out_shape(hw), dtype=xin.dtype).pin_memory() for hw in shapes]
+        chunk = 4 if fin > (1 << 20) else 64  # frames per pipeline chunk
+        pipes = [ds.ds_pipeline_create(pl, chunk, 3) for pl in plans]
+        def e2e_step():
+            for pp, hi, ho in zip(pipes, host_ins, host_outs):
+                ds.ds_pipeline_run(pp, hi.data_ptr(), ho.data_ptr(), n)
+        e2e_step()
         k3 = 5
         t = time.perf_counter()
         for _ in range(k3):
-            ds.ds_pipeline_run(pipe, host_in.data_ptr(), host_out.data_ptr(), n)
+            e2e_step()
         dt = time.perf_counter() - t
-        ds.ds_pipeline_destroy(pipe)
-        line["e2e"] = {"value": n * k3 / dt, "unit": "frames/s", "h2d_bytes_per_step": n * fin,
-                       "d2h_bytes_per_step": n * fout, "api": "ds_pipeline_run (4-frame chunks, 3 streams)"}
-        ok = np.array_equal(host_out.numpy(), out.cpu().numpy())
+        for pp in pipes:
+            ds.ds_pipeline_destroy(pp)
+        line["e2e"] = {"value": n * k3 / dt, "unit": "frames/s", "h2d_bytes_per_step": n * sum(f[0] for f in fbytes),
+                       "d2h_bytes_per_step": n * sum(f[1] for f in fbytes),
+                       "api": "ds_pipeline_run (%d-frame chunks, 3 streams, per plane)" % chunk}
+        ok = all(np.array_equal(ho.numpy(), o.cpu().numpy()) for ho, o in zip(host_outs, outs))
         line["e2e"]["matches_device_path"] = bool(ok)
-        del host_in, host_out
+        del host_ins, host_outs
         if world == 1:
             line["cpu_baseline"] = time_cpu_oracle(w)
     elif world > 1:
         line["e2e"] = None
 
     ds.ds_graph_destroy(graph)
-    ds.ds_destroy(plan)
+    for pl in plans:
+        ds.ds_destroy(pl)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:

@@ -28,30 +28,51 @@ class Workload:
     dtype: int
     seed: int
     content: str  # "uniform", "gradient", "bytes", "noisy_half"
+    ratio_v: tuple = None   # vertical ratio and taps when they differ from the horizontal ones
+    taps_v: int = 0
+    planes: tuple = ()      # planar formats: ((h, w), ...) per plane; () = one plane height x width
 
     @property
     def channels(self) -> int:
         return CHANNELS[self.dtype]
 
     @property
+    def vratio(self) -> tuple:
+        return self.ratio_v if self.ratio_v else self.ratio
+
+    @property
+    def vtaps(self) -> int:
+        return self.taps_v if self.taps_v else self.taps
+
+    @property
     def out_height(self) -> int:
-        return self.height * self.ratio[0] // self.ratio[1]
+        return self.height * self.vratio[0] // self.vratio[1]
 
     @property
     def out_width(self) -> int:
         return self.width * self.ratio[0] // self.ratio[1]
 
+    def plane_shapes(self):
+        return list(self.planes) if self.planes else [(self.height, self.width)]
+
+    def plane_out_shape(self, hw):
+        oh, ow = hw[0] * self.vratio[0] // self.vratio[1], hw[1] * self.ratio[0] // self.ratio[1]
+        return (oh, ow) if self.channels == 1 else (oh, ow, self.channels)
+
     def frame_shape(self):
         return (self.height, self.width) if self.channels == 1 else (self.height, self.width, self.channels)
 
     def out_frame_shape(self):
-        oh, ow = self.out_height, self.out_width
-        return (oh, ow) if self.channels == 1 else (oh, ow, self.channels)
+        return self.plane_out_shape((self.height, self.width))
 
     def bytes_per_frame(self) -> int:
-        """Algorithmic bytes: input read once plus output written once."""
+        """Algorithmic bytes: input read once plus output written once (all planes)."""
         isz = np.dtype(NP_DTYPE[self.dtype]).itemsize
-        return (self.height * self.width + self.out_height * self.out_width) * self.channels * isz
+        tot = 0
+        for hw in self.plane_shapes():
+            oh, ow = self.plane_out_shape(hw)[:2]
+            tot += (hw[0] * hw[1] + oh * ow) * self.channels * isz
+        return tot
 
 
 WORKLOADS = {
@@ -63,6 +84,13 @@ WORKLOADS = {
     "rgb300_1080x1920_u8": Workload("rgb300_1080x1920_u8", 300, 1080, 1920, (1, 2), 6, DS_U8_RGB, 3000, "bytes"),
     # 128 fp16 2160x3840 frames, uniform + N(0, 0.05) clipped, 3/8 K=8
     "uhd128_2160x3840_f16": Workload("uhd128_2160x3840_f16", 128, 2160, 3840, (3, 8), 8, DS_F16, 4000, "noisy_half"),
+    # the paper's case (Sec. 3): 2000 CIF frames, 24-bit RGB 352x288 -> 132x128,
+    # horizontal 3/8 and vertical 4/9, K=8 on both axes; uniform bytes
+    "cif2000_352x288_u8rgb": Workload("cif2000_352x288_u8rgb", 2000, 288, 352, (3, 8), 8, DS_U8_RGB, 7000, "bytes",
+                                      ratio_v=(4, 9), taps_v=8),
+    # the same as planar YUV 4:2:0: Y 352x288, U and V 176x144 (outputs 132x128, 66x64)
+    "cif2000_yuv420_u8": Workload("cif2000_yuv420_u8", 2000, 288, 352, (3, 8), 8, DS_U8, 8000, "bytes",
+                                  ratio_v=(4, 9), taps_v=8, planes=((288, 352), (144, 176), (144, 176))),
 }
 
 
@@ -91,9 +119,22 @@ def frame(w: Workload, i: int) -> np.ndarray:
 
 
 def frames(w: Workload, idx=None) -> np.ndarray:
-    """Frames idx (default: all) stacked as (n, H, W[, C])."""
+    """Frames idx (default: all) stacked as (n, H, W[, C]) (the first plane)."""
     idx = range(w.frames) if idx is None else idx
     return np.stack([frame(w, i) for i in idx])
+
+
+def plane_frames(w: Workload, idx=None):
+    """Frames idx of every plane: a list with one (n, h, w[, C]) array per plane."""
+    if not w.planes:
+        return [frames(w, idx)]
+    idx = range(w.frames) if idx is None else idx
+    out = []
+    for k, (h, ww) in enumerate(w.planes):
+        shape = (h, ww) if w.channels == 1 else (h, ww, w.channels)
+        out.append(np.stack([np.random.default_rng(w.seed + 1_000_003 * k + i).integers(0, 256, shape, dtype=np.uint8)
+                             for i in idx]))
+    return out
 
 
 def random_frames(shape, dtype: int, seed: int) -> np.ndarray:
