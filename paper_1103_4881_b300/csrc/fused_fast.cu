@@ -194,24 +194,33 @@ struct JobDesc {
 };
 static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor layout");
 
-// Q14 taps of the uint8 classes as pairs of int16 for dp2a, [class - first
-// uint8 class][window-start parity][phase][pair]: for parity a, pair i holds
-// taps 2i - a (low half) and 2i + 1 - a (high half), zero outside 0..K-1, so
-// a window that starts on an odd slot is read from the even slot before it.
-constexpr int kU8Classes = kFcCount - kFcU8C3_38;
+// The taps of one class.  tap2h / tap2v: the Q14 taps of a uint8 class as
+// pairs of int16 for dp2a, [window-start parity][phase][pair]: for parity a,
+// pair i holds taps 2i - a (low half) and 2i + 1 - a (high half), zero
+// outside 0..K-1, so a window that starts on an odd slot is read from the
+// even slot before it.
 constexpr int kMaxPairs = 5;  // (K + 1) / 2 + 1 for K <= 8
 constexpr int kMaxPhases = 4;
 
+struct ClassTaps {
+  float taps[kMaxTaps];   // horizontal FP32 taps, or Q14 taps as floats for uint8
+  float tapsv[kMaxTaps];  // the same for the vertical axis
+  uint32_t tap2h[2][kMaxPhases][kMaxPairs];
+  uint32_t tap2v[2][kMaxPhases][kMaxPairs];
+};
+
+// Launch parameters (a __grid_constant__ kernel argument) with room for MAXJ
+// job descriptors: a small size for single jobs keeps the argument -- copied
+// by the driver at every launch -- short.
+template <int MAXJ>
 struct FastParams {
-  JobDesc jobs[kMaxJobs];
-  float taps[kFcCount][kMaxTaps];   // horizontal FP32 taps, or Q14 taps as floats for uint8
-  float tapsv[kFcCount][kMaxTaps];  // the same for the vertical axis
-  uint32_t tap2h[kU8Classes][2][kMaxPhases][kMaxPairs];
-  uint32_t tap2v[kU8Classes][2][kMaxPhases][kMaxPairs];
+  JobDesc jobs[MAXJ];
+  ClassTaps t;
   int n_jobs;
   int total_tiles;
   int sched_slot;                  // row kernel: dynamic scheduling slot
 };
+constexpr int kFewJobs = 2;        // one job, or one job split for the launch tail
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -261,7 +270,8 @@ struct Tile {
   int job, frame, strip, chunk;
 };
 
-__host__ __device__ __forceinline__ Tile decode_tile(const FastParams& prm, int t) {
+template <class PR>
+__host__ __device__ __forceinline__ Tile decode_tile(const PR& prm, int t) {
   int lo = 0, hi = prm.n_jobs - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -476,8 +486,9 @@ struct RowMath<Cl, false> {
   struct Row {
     float v[N];
   };
-  __device__ static __forceinline__ void h(const uint32_t* w, const FastParams& prm, Row& r) {
-    hcompute<Cl>(w, prm.taps[Cl::id], r.v);
+  template <class PR>
+  __device__ static __forceinline__ void h(const uint32_t* w, const PR& prm, Row& r) {
+    hcompute<Cl>(w, prm.t.taps, r.v);
   }
   __device__ static __forceinline__ void copy(Row& d, const Row& s) {
 #pragma unroll
@@ -485,10 +496,10 @@ struct RowMath<Cl, false> {
   }
   // the PV output rows of block rr from the window (CHECK: rows past OH are
   // skipped; without it the caller knows they are all inside)
-  template <bool CHECK>
-  __device__ static __forceinline__ void v(const Row (&win)[Cl::LV], const FastParams& prm, T* obase,
-                                           long long rowe, int rr, int OH, int n_valid) {
-    const float* taps = prm.tapsv[Cl::id];
+  template <bool CHECK, class PR>
+  __device__ static __forceinline__ void v(const Row (&win)[Cl::LV], const PR& prm, T* obase, long long rowe,
+                                           int rr, int OH, int n_valid) {
+    const float* taps = prm.t.tapsv;
 #pragma unroll
     for (int jv = 0; jv < Cl::PV; ++jv) {
       const int oy = rr * Cl::PV + jv;
@@ -598,10 +609,9 @@ struct RowMath<Cl, true> {
   static constexpr int NXP = Cl::LH + Cl::NB * Q + Cl::RH;  // window pixels of a lane
   static constexpr int NCW = (NXP + 1 + 3) / 4;             // channel words (+1: odd-start pad)
   static constexpr int NPR = (LV + 2) / 2;                  // window row pairs (+1 slot of pad)
-  static constexpr int U8I = Cl::id - kFcU8C3_38;
   static_assert(Cl::HB * Cl::VB >= Cl::LH * C, "pixel slot 0 must be a loaded byte");
   static_assert(Cl::HB * Cl::VB - Cl::LH * C + NXP * C <= Cl::NVT * Cl::VB, "gathered bytes must be loaded");
-  static_assert(U8I >= 0 && U8I < kU8Classes && P <= kMaxPhases && PV <= kMaxPhases &&
+  static_assert(P <= kMaxPhases && PV <= kMaxPhases &&
                     (K + 2) / 2 <= kMaxPairs && (KV + 2) / 2 <= kMaxPairs, "tap pair table");
   struct Row {
     uint32_t w[NW];
@@ -610,13 +620,16 @@ struct RowMath<Cl, true> {
 #pragma unroll
     for (int k = 0; k < NW; ++k) d.w[k] = s.w[k];
   }
-  __device__ static __forceinline__ uint32_t tp(const FastParams& prm, int par, int j, int i) {
-    return prm.tap2h[U8I][par][j][i];
+  template <class PR>
+  __device__ static __forceinline__ uint32_t tp(const PR& prm, int par, int j, int i) {
+    return prm.t.tap2h[par][j][i];
   }
-  __device__ static __forceinline__ uint32_t tpv(const FastParams& prm, int par, int j, int i) {
-    return prm.tap2v[U8I][par][j][i];
+  template <class PR>
+  __device__ static __forceinline__ uint32_t tpv(const PR& prm, int par, int j, int i) {
+    return prm.t.tap2v[par][j][i];
   }
-  __device__ static __forceinline__ void h(const uint32_t* w, const FastParams& prm, Row& r) {
+  template <class PR>
+  __device__ static __forceinline__ void h(const uint32_t* w, const PR& prm, Row& r) {
     constexpr int first = Cl::HB * Cl::VB - Cl::LH * C;  // byte of pixel slot 0, channel 0
     uint32_t cw[C][NCW];
 #pragma unroll
@@ -656,8 +669,8 @@ struct RowMath<Cl, true> {
       r.w[k] = pack4(v[e], e + 1 < N ? v[e + 1] : 0, e + 2 < N ? v[e + 2] : 0, e + 3 < N ? v[e + 3] : 0);
     }
   }
-  template <bool CHECK>
-  __device__ static __forceinline__ void v(const Row (&win)[LV], const FastParams& prm, T* obase, long long rowe,
+  template <bool CHECK, class PR>
+  __device__ static __forceinline__ void v(const Row (&win)[LV], const PR& prm, T* obase, long long rowe,
                                            int rr, int OH, int n_valid) {
     // one word column g (4 output columns) at a time: row-pair words
     // pl = bytes 0,1 of rows 2m and 2m+1 interleaved, ph = bytes 2,3
@@ -697,8 +710,8 @@ struct RowMath<Cl, true> {
   }
 };
 
-template <class Cl, int WPC, int MINB>
-__global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__ FastParams prm) {
+template <class Cl, int WPC, int MINB, int MAXJ>
+__global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__ FastParams<MAXJ> prm) {
   using T = typename Cl::T;
   using RM = RowMath<Cl>;
   using Row = typename RM::Row;
@@ -966,25 +979,28 @@ constexpr int kRowsWPC = 4;  // warps (independent pipelines) per CTA of the row
 // Registers are budgeted for Cl::MINB resident CTAs (4 warps each) per SM,
 // which the shared-memory footprint of the stage rings also allows.
 template <class Cl>
-KernelInfo rows_info() {
+KernelInfo rows_info(bool few) {
   constexpr int smem = 128 + kRowsWPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  return KernelInfo{reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, Cl::MINB>), smem, kRowsWPC * 32};
+  const void* fn = few ? reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, Cl::MINB, kFewJobs>)
+                       : reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, Cl::MINB, kMaxJobs>);
+  return KernelInfo{fn, smem, kRowsWPC * 32};
 }
 
-// The kernel that runs class `cls` (all jobs of a launch share the class).
-KernelInfo kernel_for(int cls) {
+// The kernel that runs class `cls` (all jobs of a launch share the class)
+// with room for kFewJobs (few) or kMaxJobs job descriptors.
+KernelInfo kernel_for(int cls, bool few) {
   switch (cls) {
-    case kFcF32_38: return rows_info<RF32_38>();
-    case kFcF32_12: return rows_info<RF32_12>();
-    case kFcF32_23: return rows_info<RF32_23>();
-    case kFcF16_38: return rows_info<RF16_38>();
-    case kFcF16_12: return rows_info<RF16_12>();
-    case kFcF16_23: return rows_info<RF16_23>();
-    case kFcU8C3_38: return rows_info<RU8_38>();
-    case kFcU8C3_12: return rows_info<RU8_12>();
-    case kFcU8C3_CIF: return rows_info<RU8_CIF>();
-    case kFcU8C1_CIF: return rows_info<RU8P_CIF>();
-    default: return rows_info<RU8_23>();
+    case kFcF32_38: return rows_info<RF32_38>(few);
+    case kFcF32_12: return rows_info<RF32_12>(few);
+    case kFcF32_23: return rows_info<RF32_23>(few);
+    case kFcF16_38: return rows_info<RF16_38>(few);
+    case kFcF16_12: return rows_info<RF16_12>(few);
+    case kFcF16_23: return rows_info<RF16_23>(few);
+    case kFcU8C3_38: return rows_info<RU8_38>(few);
+    case kFcU8C3_12: return rows_info<RU8_12>(few);
+    case kFcU8C3_CIF: return rows_info<RU8_CIF>(few);
+    case kFcU8C1_CIF: return rows_info<RU8P_CIF>(few);
+    default: return rows_info<RU8_23>(few);
   }
 }
 
@@ -1013,7 +1029,7 @@ int sm_count() {
   return n;
 }
 
-// int16 tap pairs of one axis for dp2a (see FastParams::tap2h).
+// int16 tap pairs of one axis for dp2a (see ClassTaps::tap2h).
 void pair_taps(const short* q14, int p, int K, uint32_t (*out)[kMaxPhases][kMaxPairs]) {
   for (int par = 0; par < 2; ++par)
     for (int j = 0; j < p; ++j)
@@ -1025,25 +1041,26 @@ void pair_taps(const short* q14, int p, int K, uint32_t (*out)[kMaxPhases][kMaxP
       }
 }
 
-void fill_taps(FastParams& prm) {
-  // the fast classes' taps depend only on their axes: build them once with
-  // a throwaway plan of each class
-  static FastParams taps_only;
+// The taps of fast class `cls`.  They depend only on its axes: built once
+// for every class with a throwaway plan.
+const ClassTaps& class_taps(int cls) {
+  static ClassTaps all[kFcCount];
   static std::once_flag once;
   std::call_once(once, [] {
-    std::memset(&taps_only, 0, sizeof(taps_only));
+    std::memset(all, 0, sizeof(all));
     struct Axes {
       int p, q, K, pv, qv, Kv;
       ds_dtype dt;
     };
-    std::vector<Axes> all;
+    std::vector<Axes> specs;
     const int pq[3][3] = {{3, 8, 8}, {1, 2, 6}, {2, 3, 6}};
     const ds_dtype dts[3] = {DS_F32, DS_F16, DS_U8_RGB};
     for (int d = 0; d < 3; ++d)
-      for (int r = 0; r < 3; ++r) all.push_back({pq[r][0], pq[r][1], pq[r][2], pq[r][0], pq[r][1], pq[r][2], dts[d]});
-    all.push_back({3, 8, 8, 4, 9, 8, DS_U8_RGB});
-    all.push_back({3, 8, 8, 4, 9, 8, DS_U8});
-    for (const Axes& a : all) {
+      for (int r = 0; r < 3; ++r)
+        specs.push_back({pq[r][0], pq[r][1], pq[r][2], pq[r][0], pq[r][1], pq[r][2], dts[d]});
+    specs.push_back({3, 8, 8, 4, 9, 8, DS_U8_RGB});
+    specs.push_back({3, 8, 8, 4, 9, 8, DS_U8});
+    for (const Axes& a : specs) {
       ds_plan_desc d{};
       d.in_h = d.in_w = 72;
       d.ratio_h = ds_ratio{a.p, a.q};
@@ -1057,21 +1074,18 @@ void fill_taps(FastParams& prm) {
         ds_destroy(pl);
         continue;
       }
-      const int cls = pl->fast_class;
+      ClassTaps& t = all[pl->fast_class];
       const bool u8 = a.dt == DS_U8 || a.dt == DS_U8_RGB;
-      for (int i = 0; i < pl->p * pl->K; ++i) taps_only.taps[cls][i] = u8 ? (float)pl->q14[i] : pl->w32[i];
-      for (int i = 0; i < pl->pv * pl->Kv; ++i) taps_only.tapsv[cls][i] = u8 ? (float)pl->q14v[i] : pl->w32v[i];
+      for (int i = 0; i < pl->p * pl->K; ++i) t.taps[i] = u8 ? (float)pl->q14[i] : pl->w32[i];
+      for (int i = 0; i < pl->pv * pl->Kv; ++i) t.tapsv[i] = u8 ? (float)pl->q14v[i] : pl->w32v[i];
       if (u8) {
-        pair_taps(pl->q14, pl->p, pl->K, taps_only.tap2h[cls - kFcU8C3_38]);
-        pair_taps(pl->q14v, pl->pv, pl->Kv, taps_only.tap2v[cls - kFcU8C3_38]);
+        pair_taps(pl->q14, pl->p, pl->K, t.tap2h);
+        pair_taps(pl->q14v, pl->pv, pl->Kv, t.tap2v);
       }
       ds_destroy(pl);
     }
   });
-  std::memcpy(prm.taps, taps_only.taps, sizeof(prm.taps));
-  std::memcpy(prm.tapsv, taps_only.tapsv, sizeof(prm.tapsv));
-  std::memcpy(prm.tap2h, taps_only.tap2h, sizeof(prm.tap2h));
-  std::memcpy(prm.tap2v, taps_only.tap2v, sizeof(prm.tap2v));
+  return all[cls];
 }
 
 // Tile geometry of a job (everything but the tensor map).  `band`: output
@@ -1349,23 +1363,12 @@ int take_graph_slot() {
   return -1;
 }
 
-ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
-  static thread_local FastParams prm;  // ~13 KB, too large for the stack of some callers
-  std::memset(&prm, 0, sizeof(prm));
-  fill_taps(prm);
-  const int cls = jobs[0].plan->fast_class;  // launch_fast groups jobs by class
-  int want_ctas = jobs[0].plan->ctas_per_sm;
-  for (int i = 0; i < n; ++i) want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
-  const KernelInfo ki = kernel_for(cls);
-  int occ = ctas_per_sm(ki);
-  if (occ <= 0) {
-    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", ki.smem);
-    return DS_ERR_UNSUPPORTED;
-  }
-  if (want_ctas > 0) occ = std::min(occ, want_ctas);
+// Fill the launch parameters and launch.
+template <int MAXJ>
+ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, const BandedJob* banded, int nb,
+                      int occ, cudaStream_t st) {
   const int per_cta = ki.threads / 32;  // one tile per warp
-  BandedJob banded[kMaxJobs];
-  const int nb = plan_bands(jobs, n, sm_count() * occ * per_cta, banded);
+  prm.t = class_taps(cls);
   int tiles = 0;
   for (int i = 0; i < nb; ++i) {
     ds_status s = encode_job(prm.jobs[i], banded[i].job, banded[i].band);
@@ -1394,6 +1397,30 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_fail(e, "k_rows launch");
   count_launches(1);
   return DS_OK;
+}
+
+ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
+  const int cls = jobs[0].plan->fast_class;  // launch_fast groups jobs by class
+  int want_ctas = jobs[0].plan->ctas_per_sm;
+  for (int i = 0; i < n; ++i) want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
+  // both instantiations of a class have the same shape and occupancy
+  const KernelInfo big = kernel_for(cls, false);
+  int occ = ctas_per_sm(big);
+  if (occ <= 0) {
+    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", big.smem);
+    return DS_ERR_UNSUPPORTED;
+  }
+  if (want_ctas > 0) occ = std::min(occ, want_ctas);
+  BandedJob banded[kMaxJobs];
+  const int nb = plan_bands(jobs, n, sm_count() * occ * (big.threads / 32), banded);
+  if (nb <= kFewJobs) {
+    static thread_local FastParams<kFewJobs> few;
+    const KernelInfo ki = kernel_for(cls, true);
+    if (ctas_per_sm(ki) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
+    return launch_with(few, ki, cls, banded, nb, occ, st);
+  }
+  static thread_local FastParams<kMaxJobs> many;  // ~17 KB: not on the caller's stack
+  return launch_with(many, big, cls, banded, nb, occ, st);
 }
 
 }  // namespace
