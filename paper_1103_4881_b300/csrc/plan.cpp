@@ -125,8 +125,8 @@ bool axis_ok(const char* who, const char* axis, int p, int q, int K) {
 // 1080p / 4K workloads; the autotuner refines it per plan).
 int default_row_blocks(int fast_class) {
   switch (fast_class) {
-    case kFcF32_38: return 8;
-    case kFcF16_38: return 10;
+    case kFcF32_38: return 12;
+    case kFcF16_38: return 16;
     case kFcU8C3_38: return 16;
     case kFcF32_12: case kFcF16_12: case kFcU8C3_12: return 24;
     case kFcF32_23: case kFcF16_23: case kFcU8C3_23: return 20;
