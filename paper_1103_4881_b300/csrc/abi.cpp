@@ -3,6 +3,8 @@
 // pipeline.  Each job goes to the fused TMA kernel when its plan has a fast
 // class and its input satisfies the TMA alignment rules, else to the general
 // fused kernel.
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -14,6 +16,13 @@
 namespace ds {
 
 namespace {
+
+// NVTX range over one entry point (visible in timeline profilers; a no-op
+// when no tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 bool uses_fast(const ds_plan* pl, const void* in, int n_frames) {
   if (pl->fast_class < 0 || pl->force_general) return false;
@@ -83,6 +92,7 @@ ds_status ds_run_frames(const ds_plan* plan, const void* in, void* out, int n_fr
     return DS_ERR_ARG;
   }
   if (n_frames == 0) return DS_OK;
+  Range r("ds_run_frames");
   ds_job j{plan, in, out, n_frames};
   return run_jobs(&j, 1, (cudaStream_t)stream);
 }
@@ -94,6 +104,7 @@ ds_status ds_batch_run(const ds_job* jobs, int n, void* stream) {
     return DS_ERR_ARG;
   }
   if (n == 0) return DS_OK;
+  Range r("ds_batch_run");
   return run_jobs(jobs, n, (cudaStream_t)stream);
 }
 
@@ -116,6 +127,7 @@ ds_status ds_run_unfused(const ds_plan* plan, const void* in, void* out, int n_f
     return DS_ERR_ARG;
   }
   if (n_frames == 0) return DS_OK;
+  Range r("ds_run_unfused");
   return launch_unfused(plan, in, out, n_frames, workspace, (cudaStream_t)stream);
 }
 
@@ -268,6 +280,7 @@ ds_status ds_pipeline_run(ds_pipeline* pp, const void* in, void* out, int n_fram
     set_error("ds_pipeline_run: bad arguments");
     return DS_ERR_ARG;
   }
+  Range r("ds_pipeline_run");
   const size_t fin = pp->in_chunk_bytes / pp->chunk, fout = pp->out_chunk_bytes / pp->chunk;
   int slot = 0;
   for (int f0 = 0; f0 < n_frames; f0 += pp->chunk, slot = (slot + 1) % pp->depth) {

@@ -57,24 +57,35 @@ class Result:
     max_batch: int = 0
     max_queue: int = 0
     peak_bytes: int = 0
+    alloc_retries: int = 0
 
     def summary(self) -> dict:
         lat = np.array(self.latency_ms) if self.latency_ms else np.zeros(1)
         return {"requests": self.completed, "frames_per_s": self.completed / max(self.wall_s, 1e-9),
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "batches": self.batches, "max_batch": self.max_batch,
-                "max_queue": self.max_queue, "peak_admitted_mb": self.peak_bytes / 1e6, "wall_s": self.wall_s}
+                "max_queue": self.max_queue, "peak_admitted_mb": self.peak_bytes / 1e6, "wall_s": self.wall_s,
+                "alloc_retries": self.alloc_retries}
 
 
 class Server:
-    """Resident plans, a device-memory budget and a pool of streams."""
+    """Resident plans, a device-memory budget and a pool of streams.
 
-    def __init__(self, mem_budget_bytes: int = 4 << 30, n_streams: int = 4, max_batch: int = 64):
+    alloc(shape, dtype) -> device tensor allocates every buffer of a batch
+    (default torch.empty on the GPU).  When it raises out-of-memory, the
+    batch's requests go back to the front of the queue and are admitted again
+    once an in-flight batch has completed (or, with nothing in flight, after a
+    short wait, up to max_alloc_retries times in a row)."""
+
+    def __init__(self, mem_budget_bytes: int = 4 << 30, n_streams: int = 4, max_batch: int = 64, alloc=None,
+                 max_alloc_retries: int = 100):
         torch = _torch()
         self.budget = int(mem_budget_bytes)
         self.max_batch = int(max_batch)
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self.plans = {}
+        self.alloc = alloc or (lambda shape, dtype: torch.empty(shape, dtype=dtype, device="cuda"))
+        self.max_alloc_retries = int(max_alloc_retries)
 
     def close(self):
         for pl in self.plans.values():
@@ -112,6 +123,8 @@ class Server:
         free_streams = list(range(len(self.streams)))
         inflight = []
         admitted = 0
+        blocked = False  # an allocation failed: admit again after a completion
+        failures = 0     # consecutive allocation failures
         res = Result()
         outputs = {}
         for r in requests:  # resident plans before the clock starts
@@ -129,6 +142,7 @@ class Server:
             still = []
             for b in inflight:
                 if b.event.query():
+                    blocked = False
                     t_done = time.perf_counter() - t0
                     for r in b.reqs:
                         arrival = r.arrival_s if realtime else 0.0
@@ -143,7 +157,7 @@ class Server:
                     still.append(b)
             inflight = still
             # admission and launch
-            if queue and free_streams:
+            if queue and free_streams and not blocked:
                 group, nbytes = [], 0
                 while queue and len(group) < self.max_batch:
                     need = self.request_bytes(queue[0], copies)
@@ -154,13 +168,28 @@ class Server:
                 if group:
                     si = free_streams.pop()
                     st = self.streams[si]
+                    try:
+                        batch = self._launch(group, st, inputs, copies, nbytes, time.perf_counter() - t0)
+                    except (torch.cuda.OutOfMemoryError, MemoryError):
+                        # nothing of the batch was launched: requeue it in order
+                        free_streams.append(si)
+                        queue.extendleft(reversed(group))
+                        res.alloc_retries += 1
+                        failures += 1
+                        if failures > self.max_alloc_retries:
+                            raise
+                        blocked = bool(inflight)
+                        if not inflight:
+                            time.sleep(1e-3)
+                        continue
+                    failures = 0
                     admitted += nbytes
                     res.peak_bytes = max(res.peak_bytes, admitted)
-                    inflight.append(self._launch(group, st, inputs, copies, nbytes, time.perf_counter() - t0))
+                    inflight.append(batch)
                     res.batches += 1
                     res.max_batch = max(res.max_batch, len(group))
                     continue
-            if not (queue and free_streams):
+            if not (queue and free_streams) or blocked:
                 time.sleep(20e-6)
         res.wall_s = time.perf_counter() - t0
         return res, outputs
@@ -169,17 +198,18 @@ class Server:
         torch = _torch()
         jobs, outs, host_outs, keep = [], [], [], []
         with torch.cuda.stream(st):
+            # every device buffer first, so an allocation failure launches nothing
+            staged = []
             for r in group:
-                pl = self.plan(r)
                 x = inputs(r)
+                xd = self.alloc(x.shape, x.dtype) if copies else x
+                out = self.alloc(self.out_shape(r), xd.dtype)
+                staged.append((r, x, xd, out))
+            for r, x, xd, out in staged:
                 if copies:
-                    xd = torch.empty(x.shape, dtype=x.dtype, device="cuda")
                     xd.copy_(x, non_blocking=True)
                     keep.append(xd)
-                else:
-                    xd = x
-                out = torch.empty(self.out_shape(r), dtype=xd.dtype, device="cuda")
-                jobs.append((pl, xd.data_ptr(), out.data_ptr(), 1))
+                jobs.append((self.plan(r), xd.data_ptr(), out.data_ptr(), 1))
                 outs.append(out)
             ds.ds_batch_run(jobs, st.cuda_stream)
             for o in outs:

@@ -107,3 +107,30 @@ def test_autotune_keeps_bits_and_caches(oracle, dt, tmp_path, monkeypatch):
             ds.ds_destroy(pl2)
     finally:
         ds.ds_destroy(pl)
+
+
+def test_allocation_failures_requeue_and_every_request_completes():
+    """An injected allocator that runs out of memory now and then: the batch
+    goes back to the queue, nothing of it is launched, and every request
+    still completes with the bits of its solo run."""
+    import torch
+
+    calls = {"n": 0}
+
+    def flaky(shape, dtype):
+        calls["n"] += 1
+        if calls["n"] <= 3 or calls["n"] % 7 == 0:
+            raise torch.cuda.OutOfMemoryError("injected")
+        return torch.empty(shape, dtype=dtype, device="cuda")
+
+    reqs = _requests(30, seed=9)
+    pool = serve.FramePool(reqs, per_class=2)
+    srv = serve.Server(mem_budget_bytes=64 << 20, n_streams=2, max_batch=4, alloc=flaky)
+    try:
+        res, outs = srv.run(reqs, pool.device, realtime=False, keep_outputs=True)
+        finish()
+        assert res.completed == len(reqs) and res.alloc_retries >= 3
+        for r in reqs:
+            np.testing.assert_array_equal(outs[r.rid].cpu().numpy(), _solo(srv, r, pool.device(r)))
+    finally:
+        srv.close()
