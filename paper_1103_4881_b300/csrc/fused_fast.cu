@@ -557,13 +557,18 @@ __device__ __forceinline__ uint32_t gather4(const uint32_t* w, int p0, int p1, i
   return __byte_perm(r1, __byte_perm(w[a + 2], w[a + 3], s2), s3);
 }
 
-// (acc + 2^13) >> 14 has been taken by starting acc at 2^13: floor shift, clamp.
-__device__ __forceinline__ int u8_round(int acc) { return __vimin_s32_relu(acc >> 14, 255); }
+// (acc + 2^13) >> 14 has been taken by starting acc at 2^13: a floor shift.
+// The clamp to [0, 255] happens when the values are packed.
+__device__ __forceinline__ int u8_round(int acc) { return acc >> 14; }
 
-// Four values 0..255 as the bytes of one word (v0 lowest).
+// Four shifted sums as the bytes of one word (v0 lowest), each saturated to
+// [0, 255]: two saturating pack conversions (each converts two s32 values to
+// u8 and places them below the low half of its third operand).
 __device__ __forceinline__ uint32_t pack4(int v0, int v1, int v2, int v3) {
-  return __byte_perm(__byte_perm((uint32_t)v0, (uint32_t)v1, 0x0040u), __byte_perm((uint32_t)v2, (uint32_t)v3, 0x0040u),
-                     0x5410u);
+  uint32_t hi, d;
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(hi) : "r"(v3), "r"(v2), "r"(0u));
+  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(v1), "r"(v0), "r"(hi));
+  return d;
 }
 
 // Store n_valid (<= 4*NW) bytes of words w to o with the widest aligned stores.
