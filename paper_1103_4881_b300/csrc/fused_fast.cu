@@ -531,8 +531,9 @@ __device__ __forceinline__ int dp2a(uint32_t taps, uint32_t px, int c) {
   return d;
 }
 
-// Bytes p0 <= p1 <= p2 <= p3 of the word array w (spanning at most four
-// words, every one of them inside the array) as one word, byte k = byte pk.
+// Bytes p0..p3 of the word array w as one word, byte k = byte pk; p0 is the
+// lowest position and p3 the highest, and the words they span (at most four)
+// are all inside the array.
 // The positions are compile-time constants after unrolling, so the selectors
 // fold and only the words that hold one of the bytes are read.
 __device__ __forceinline__ uint32_t gather4(const uint32_t* w, int p0, int p1, int p2, int p3) {
@@ -636,38 +637,64 @@ struct RowMath<Cl, true> {
   template <class PR>
   __device__ static __forceinline__ void h(const uint32_t* w, const PR& prm, Row& r) {
     constexpr int first = Cl::HB * Cl::VB - Cl::LH * C;  // byte of pixel slot 0, channel 0
-    uint32_t cw[C][NCW];
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-      for (int k = 0; k < NCW; ++k) {
-        int pos[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int slot = (4 * k + i < NXP) ? 4 * k + i : NXP - 1;  // pad slots: any byte
-          pos[i] = first + slot * C + c;
-        }
-        cw[c][k] = gather4(w, pos[0], pos[1], pos[2], pos[3]);
-      }
+    auto pos = [&](int slot, int c) { return first + (slot < NXP ? slot : NXP - 1) * C + c; };  // pads: any byte
     int v[N];
+    if constexpr (C == 3) {
+      // Pixel pair m (slots 2m, 2m+1): one word holds its R pair (low half)
+      // and G pair (high half) -- five consecutive bytes, so one byte_perm --
+      // and another its B pair (low half).
+      constexpr int NPW = (NXP + 2) / 2;
+      uint32_t rg[NPW], bb[NPW];
 #pragma unroll
-    for (int n = 0; n < Cl::NB; ++n)
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
-        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
-#pragma unroll
-        for (int c = 0; c < C; ++c) {
-          int acc = 8192;
-#pragma unroll
-          for (int i = 0; i < npair; ++i) {
-            const int pi = pr0 + i;
-            acc = (pi & 1) ? dp2a<1>(tp(prm, par, j, i), cw[c][pi >> 1], acc)
-                           : dp2a<0>(tp(prm, par, j, i), cw[c][pi >> 1], acc);
-          }
-          v[(n * P + j) * C + c] = u8_round(acc);
-        }
+      for (int m = 0; m < NPW; ++m) {
+        rg[m] = gather4(w, pos(2 * m, 0), pos(2 * m + 1, 0), pos(2 * m, 1), pos(2 * m + 1, 1));
+        bb[m] = gather4(w, pos(2 * m, 2), pos(2 * m + 1, 2), pos(2 * m + 1, 2), pos(2 * m + 1, 2));
       }
+#pragma unroll
+      for (int n = 0; n < Cl::NB; ++n)
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
+          const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            int acc = 8192;
+#pragma unroll
+            for (int i = 0; i < npair; ++i) {
+              const int m = pr0 + i;
+              acc = (c == 1) ? dp2a<1>(tp(prm, par, j, i), rg[m], acc)
+                             : dp2a<0>(tp(prm, par, j, i), c == 0 ? rg[m] : bb[m], acc);
+            }
+            v[(n * P + j) * C + c] = u8_round(acc);
+          }
+        }
+    } else {
+      // one channel word per 4 consecutive pixel slots (pairs 2k, 2k+1)
+      uint32_t cw[C][NCW];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int k = 0; k < NCW; ++k)
+          cw[c][k] = gather4(w, pos(4 * k, c), pos(4 * k + 1, c), pos(4 * k + 2, c), pos(4 * k + 3, c));
+#pragma unroll
+      for (int n = 0; n < Cl::NB; ++n)
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
+          const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            int acc = 8192;
+#pragma unroll
+            for (int i = 0; i < npair; ++i) {
+              const int pi = pr0 + i;
+              acc = (pi & 1) ? dp2a<1>(tp(prm, par, j, i), cw[c][pi >> 1], acc)
+                             : dp2a<0>(tp(prm, par, j, i), cw[c][pi >> 1], acc);
+            }
+            v[(n * P + j) * C + c] = u8_round(acc);
+          }
+        }
+    }
 #pragma unroll
     for (int k = 0; k < NW; ++k) {
       const int e = 4 * k;
