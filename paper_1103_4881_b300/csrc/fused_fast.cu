@@ -180,6 +180,10 @@ using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false>;
 //                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV
 using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
 using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
+// uint8, one channel
+using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 2, 4, 3, false>;
+using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 8, 4, 3, false>;
+using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 8, 4, 3, false>;
 
 // ---------------------------------------------------------------------------
 // launch parameters
@@ -983,6 +987,9 @@ HostGeom geom_of(int cls) {
     case kFcU8C3_12: return host_geom<RU8_12>();
     case kFcU8C3_CIF: return host_geom<RU8_CIF>();
     case kFcU8C1_CIF: return host_geom<RU8P_CIF>();
+    case kFcU8C1_38: return host_geom<RU8P_38>();
+    case kFcU8C1_12: return host_geom<RU8P_12>();
+    case kFcU8C1_23: return host_geom<RU8P_23>();
     default: return host_geom<RU8_23>();
   }
 }
@@ -1032,6 +1039,9 @@ KernelInfo kernel_for(int cls, bool few) {
     case kFcU8C3_12: return rows_info<RU8_12>(few);
     case kFcU8C3_CIF: return rows_info<RU8_CIF>(few);
     case kFcU8C1_CIF: return rows_info<RU8P_CIF>(few);
+    case kFcU8C1_38: return rows_info<RU8P_38>(few);
+    case kFcU8C1_12: return rows_info<RU8P_12>(few);
+    case kFcU8C1_23: return rows_info<RU8P_23>(few);
     default: return rows_info<RU8_23>(few);
   }
 }
@@ -1086,8 +1096,8 @@ const ClassTaps& class_taps(int cls) {
     };
     std::vector<Axes> specs;
     const int pq[3][3] = {{3, 8, 8}, {1, 2, 6}, {2, 3, 6}};
-    const ds_dtype dts[3] = {DS_F32, DS_F16, DS_U8_RGB};
-    for (int d = 0; d < 3; ++d)
+    const ds_dtype dts[4] = {DS_F32, DS_F16, DS_U8_RGB, DS_U8};
+    for (int d = 0; d < 4; ++d)
       for (int r = 0; r < 3; ++r)
         specs.push_back({pq[r][0], pq[r][1], pq[r][2], pq[r][0], pq[r][1], pq[r][2], dts[d]});
     specs.push_back({3, 8, 8, 4, 9, 8, DS_U8_RGB});
@@ -1377,6 +1387,9 @@ std::string check_plan(const ds_plan* pl) {
     case kFcU8C3_23: return check_rows<RU8_23, kRowsWPC>(jd);
     case kFcU8C3_CIF: return check_rows<RU8_CIF, kRowsWPC>(jd);
     case kFcU8C1_CIF: return check_rows<RU8P_CIF, kRowsWPC>(jd);
+    case kFcU8C1_38: return check_rows<RU8P_38, kRowsWPC>(jd);
+    case kFcU8C1_12: return check_rows<RU8P_12, kRowsWPC>(jd);
+    case kFcU8C1_23: return check_rows<RU8P_23, kRowsWPC>(jd);
     default: return std::string();
   }
 }

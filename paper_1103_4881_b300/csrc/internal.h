@@ -33,6 +33,9 @@ enum FastClass : int {
   kFcU8C3_23,     // uint8 RGB, 2/3, K=6
   kFcU8C3_CIF,    // uint8 RGB, horizontal 3/8 K=8, vertical 4/9 K=8 (the paper's CIF case)
   kFcU8C1_CIF,    // uint8 one plane (4:2:0 Y, U, V), the same axes
+  kFcU8C1_38,     // uint8 one channel, 3/8, K=8
+  kFcU8C1_12,     // uint8 one channel, 1/2, K=6
+  kFcU8C1_23,     // uint8 one channel, 2/3, K=6
   kFcCount
 };
 

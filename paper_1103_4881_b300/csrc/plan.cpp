@@ -131,6 +131,9 @@ int default_row_blocks(int fast_class) {
     case kFcF32_12: case kFcF16_12: case kFcU8C3_12: return 24;
     case kFcF32_23: case kFcF16_23: case kFcU8C3_23: return 20;
     case kFcU8C3_CIF: case kFcU8C1_CIF: return 8;
+    case kFcU8C1_38: return 16;
+    case kFcU8C1_12: return 24;
+    case kFcU8C1_23: return 20;
     default: return 0;
   }
 }
@@ -170,6 +173,7 @@ int fast_class_of(int p, int q, int K, int pv, int qv, int Kv, ds_dtype dtype) {
     case DS_F32: return kFcF32_38 + r;
     case DS_F16: return kFcF16_38 + r;
     case DS_U8_RGB: return kFcU8C3_38 + r;
+    case DS_U8: return kFcU8C1_38 + r;
     default: return kFcNone;
   }
 }
@@ -398,7 +402,7 @@ ds_status ds_plan_describe(const ds_plan* pl, char* buf, size_t len) {
   }
   static const char* names[] = {"f32_3_8_k8", "f32_1_2_k6", "f32_2_3_k6", "f16_3_8_k8", "f16_1_2_k6",
                                 "f16_2_3_k6", "u8rgb_3_8_k8", "u8rgb_1_2_k6", "u8rgb_2_3_k6",
-                                "u8rgb_h3_8_v4_9_k8", "u8_h3_8_v4_9_k8"};
+                                "u8rgb_h3_8_v4_9_k8", "u8_h3_8_v4_9_k8", "u8_3_8_k8", "u8_1_2_k6", "u8_2_3_k6"};
   static_assert(sizeof(names) / sizeof(names[0]) == kFcCount, "a name per fast class");
   const bool fast = pl->fast_class >= 0 && !pl->force_general;
   std::snprintf(buf, len,

@@ -115,7 +115,7 @@ SHAPES = [(8, 8), (16, 16), (8, 32), (24, 40), (17, 64), (33, 100), (480, 640), 
           (1080, 1920), (288, 352), (3, 16), (1, 16), (2, 48), (100, 4), (129, 2048), (7, 520), (300, 1568),
           (2160, 3840)]
 RATIOS = [((3, 8), 8), ((1, 2), 6), ((2, 3), 6)]
-DTYPES = [ds.DS_F32, ds.DS_F16, ds.DS_U8_RGB]
+DTYPES = [ds.DS_F32, ds.DS_F16, ds.DS_U8_RGB, ds.DS_U8]
 
 
 def test_fused_kernel_index_arithmetic_host_check():

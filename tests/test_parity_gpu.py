@@ -16,7 +16,7 @@ from tests.gpu_util import (assert_parity, finish, frames, general_kernel, oracl
 pytestmark = pytest.mark.gpu
 
 FAST = [((3, 8), 8), ((1, 2), 6), ((2, 3), 6)]
-DTYPES = [ds.DS_F32, ds.DS_F16, ds.DS_U8_RGB]
+DTYPES = [ds.DS_F32, ds.DS_F16, ds.DS_U8_RGB, ds.DS_U8]
 # (H, W): widths multiple of 16 keep every dtype on the TMA path
 FAST_SHAPES = [(72, 528), (8, 16), (16, 16), (3, 16), (41, 272), (200, 784), (1, 32)]
 
@@ -83,7 +83,7 @@ def test_schedule_does_not_change_bits(oracle, rb):
     (29, 22, (5, 7), 10, ds.DS_F32),     # ratio without a fast class
     (33, 48, (1, 4), 16, ds.DS_U8_RGB),
     (19, 40, (3, 8), 6, ds.DS_U8_RGB),   # K outside the fast class
-    (64, 96, (3, 8), 8, ds.DS_U8),       # single-channel uint8
+    (64, 90, (3, 8), 8, ds.DS_U8),       # single-channel uint8, rows not 16-byte multiples
     (45, 50, (2, 3), 6, ds.DS_U8),
     (70, 130, (7, 16), 14, ds.DS_F16),
     (200, 70, (1, 64), 8, ds.DS_F32),    # q at its limit
@@ -207,13 +207,15 @@ def test_constant_and_impulse_frames(oracle):
     for dt in DTYPES:
         pl = ds.ds_plan_create(H, W, (3, 8), 8, dt)
         try:
-            c = 200 if dt == ds.DS_U8_RGB else 0.625
+            u8 = dt in (ds.DS_U8, ds.DS_U8_RGB)
+            c = 200 if u8 else 0.625
             shape = (1, H, W, 3) if dt == ds.DS_U8_RGB else (1, H, W)
-            x = np.full(shape, c, dtype={ds.DS_F32: np.float32, ds.DS_F16: np.float16, ds.DS_U8_RGB: np.uint8}[dt])
+            x = np.full(shape, c, dtype={ds.DS_F32: np.float32, ds.DS_F16: np.float16, ds.DS_U8_RGB: np.uint8,
+                                         ds.DS_U8: np.uint8}[dt])
             y = run_fused(pl, x).astype(np.float64)
-            assert np.abs(y - c).max() <= (0 if dt == ds.DS_U8_RGB else 1e-6)
+            assert np.abs(y - c).max() <= (0 if u8 else 1e-6)
             x[...] = 0
-            x[0, 31, 101] = 1 if dt != ds.DS_U8_RGB else 255
+            x[0, 31, 101] = 255 if u8 else 1
             assert_parity(run_fused(pl, x), oracle_out(oracle, x, 3, 8, 8, dt), dt)
         finally:
             ds.ds_destroy(pl)
