@@ -181,9 +181,9 @@ using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false>;
 using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
 using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
 // uint8, one channel
-using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 2, 4, 3, false>;
-using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 8, 4, 3, false>;
-using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 8, 4, 3, false>;
+using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 4, 3, false>;
+using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, false>;
+using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, false>;
 
 // ---------------------------------------------------------------------------
 // launch parameters
