@@ -133,3 +133,29 @@ def test_fused_kernel_index_arithmetic_host_check():
         finally:
             ds.ds_destroy(pl)
     assert checked > 300
+
+
+def test_fast_kernel_host_check_on_random_shapes():
+    """ds_debug_check_plan over seeded random frame sizes and bands for every
+    fast class (host replay of the kernel's index arithmetic, no GPU)."""
+    rng = np.random.default_rng(77)
+    specs = [((3, 8), 8, (3, 8), 8), ((1, 2), 6, (1, 2), 6), ((2, 3), 6, (2, 3), 6), ((3, 8), 8, (4, 9), 8)]
+    checked = 0
+    for _ in range(150):
+        rh, kh, rv, kv = specs[rng.integers(len(specs))]
+        dt = [ds.DS_F32, ds.DS_F16, ds.DS_U8, ds.DS_U8_RGB][rng.integers(4)]
+        H = int(rng.integers(1, 700))
+        W = 16 * int(rng.integers(1, 160))
+        try:
+            pl = ds.ds_plan_create_ex(H, W, rh, kh, rv, kv, dt)
+        except ds.DsError:
+            continue
+        try:
+            if '"fused_tma"' not in ds.ds_plan_describe(pl):
+                continue
+            ds.ds_plan_set_schedule(pl, int(rng.integers(1, 40)), 0)
+            ds.ds_debug_check_plan(pl)
+            checked += 1
+        finally:
+            ds.ds_destroy(pl)
+    assert checked > 60
