@@ -13,11 +13,13 @@
  * independent elementary tasks (Sec. 3.A, "Downscaler Model").
  *
  * Readings of what the paper leaves open (identical in every entry point):
- *   - n_out = floor(n_in * p / q) on each axis, the same ratio on both;
+ *   - n_out = floor(n_in * p / q) on each axis; the same ratio on both
+ *     axes unless a plan is created with ds_plan_create_ex;
  *   - output o = r*p + j (block r, phase j) is centred on input coordinate
  *     r*q + (j + 1/2) q/p - 1/2 and reads the K pixels
  *     r*q + b_j ... r*q + b_j + K - 1, b_j = floor(centre_j) - K/2 + 1,
- *     each clamped to the frame (clamp-to-edge);
+ *     each clamped to the frame (clamp-to-edge; ds_plan_create_ex can take
+ *     them modulo the frame instead, the Array-OL reading of tilers);
  *   - taps: Lanczos-3 stretched by 6/K over the window, normalised to sum 1,
  *     computed in FP64 on the host; FP32 copies for float data, Q14 integers
  *     (round half up, residual on the largest tap) for uint8 data;
@@ -277,11 +279,13 @@ ds_status ds_debug_timeout_probe(long long limit_cycles, void* stream);
 /*
  * Host-only self-check of the fused kernel's tile schedule for this plan:
  * walks every tile of a frame with the kernel's own index arithmetic and
- * verifies that TMA coordinates are aligned, every shared-memory access
- * stays inside its buffer, the on-chip intermediate ring is never read
- * before it is written or after it is overwritten, and every output element
- * is written exactly once.  No device work.  DS_OK, or DS_ERR_ARG with the
- * first violation in ds_last_error().  Plans without a fast kernel: DS_OK.
+ * verifies that TMA coordinates are aligned, every shared-memory read stays
+ * inside the loaded window and never straddles a box, border pixels are
+ * fixed up before use, the row stream delivers each frame row in order, the
+ * register window holds exactly the (clamped) rows of every output block,
+ * and every output element is written exactly once.  No device work.
+ * DS_OK, or DS_ERR_ARG with the first violation in ds_last_error().  Plans
+ * without a fast kernel: DS_OK.
  */
 ds_status ds_debug_check_plan(const ds_plan* plan);
 
