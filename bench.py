@@ -333,7 +333,8 @@ def main():
     launch_s = ms / 1e3 / args.steps
     achieved = alg_bytes / launch_s / 1e9
     peak, peak_src = measured_peak()
-    traffic = profiled_traffic(w.name)
+    # the committed capture is of the full workload's launch: none for a resized one
+    traffic = profiled_traffic(w.name) if n == synth.WORKLOADS[w.name].frames else None
 
     line = {
         "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,

@@ -94,9 +94,15 @@ struct TmaType<uint8_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP
 // stages per warp;
 // FP: whether interior units run a second, check-free copy of the loop body
 // (faster for some classes, slower where the larger code costs more than the
-// checks, measured per class).
+// checks, measured per class);
+// FPW: frames per warp -- the warp's lanes split into FPW groups of 32/FPW,
+// each filtering the same strip and band of its own frame (for narrow frames,
+// whose width is a poor multiple of 32 lanes' packets);
+// PRO: the window prologue runs through the loop body as lead blocks whose
+// outputs are dropped (less code, a few more rows filtered per tile) instead
+// of a separate unrolled copy of the row code.
 template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_, bool FP_, int PV_ = P_,
-          int QV_ = Q_, int KV_ = K_>
+          int QV_ = Q_, int KV_ = K_, int FPW_ = 1, bool PRO_ = false>
 struct Cls {
   using T = T_;
   static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
@@ -108,6 +114,8 @@ struct Cls {
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
+  static constexpr int FPW = FPW_;                  // frames per warp
+  static constexpr int LPS = 32 / FPW_;             // lanes per frame (a strip's lanes)
   // horizontal axis: the strip, its halo columns and the lane chunks
   static constexpr int BMIN = phase_b(P, Q, K, 0);
   static constexpr int BMAX = phase_b(P, Q, K, P - 1);
@@ -118,15 +126,16 @@ struct Cls {
   static constexpr int EB = E * SZ;
   static constexpr int HLB = rup(LH * C * SZ, 16);  // left halo bytes in the window (TMA x alignment)
   static constexpr int RHB = rup(RH * C * SZ, 16);
-  static constexpr int SBLK = 32 * NB;              // packets (blocks) per strip
+  static constexpr int SBLK = LPS * NB;             // packets (blocks) per strip
   static constexpr int SPX = SBLK * Q;              // input pixels per strip
   static constexpr int WINB = HLB + SPX * C * SZ + RHB;
   static constexpr int NBOX = cdiv(WINB / SZ, 256);
   static constexpr int BOXB = rup(cdiv(WINB, NBOX), 16);
   static constexpr int BOXE = BOXB / SZ;
   static constexpr int BOXSTR = rup(SR_ * BOXB, 128);  // each box lands 128-B aligned
-  static constexpr int RSTAGE = NBOX * BOXSTR;
-  static constexpr int RTX = NBOX * SR_ * BOXB;        // TMA bytes per stage
+  static constexpr int FSTR = NBOX * BOXSTR;          // one frame's window in a stage
+  static constexpr int RSTAGE = FPW_ * FSTR;
+  static constexpr int RTX = NBOX * SR_ * BOXB;        // TMA bytes per stage and frame
   static constexpr int WARP_BYTES = NST_ * RSTAGE;
   static constexpr int NX = (LH + NB * Q + RH) * C;    // elements one lane reads per row
   static constexpr int VB = (EB % 16 == 0) ? 16 : ((EB % 8 == 0) ? 8 : 4);
@@ -152,6 +161,12 @@ struct Cls {
   static constexpr int U = SR_ / cgcd(SR_, QV) * QV;
   static constexpr int USTG = U / SR_;
   static constexpr int UBLK = U / QV;
+  // With PRO, the stream instead starts VBLK blocks early (whole units): the
+  // lead blocks fill the window, their outputs are not computed.
+  static constexpr bool PRO = PRO_;
+  static constexpr int VBLK = PRO_ ? rup(cdiv(PRE, QV), UBLK) : 0;  // lead blocks
+  static constexpr int STG0 = PRO_ ? 0 : NPS;                         // first stage of unit 0
+  static constexpr int YOFF = PRO_ ? PRE - VBLK * QV : -EXTRA;        // stream start - first pattern row
   __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
   __host__ __device__ static constexpr int bv(int j) { return phase_b(PV, QV, KV, j); }
   static_assert(EB % 4 == 0, "a lane's chunk must be whole words");
@@ -163,27 +178,28 @@ struct Cls {
   static_assert(PRE > LHV, "the window prologue must reach frame row 0");
   static_assert(LV * (SZ == 1 ? (NOUT + 3) / 4 : NOUT) <= 48, "register window too large");
   static_assert(U <= 16, "iteration unit too long to unroll");
+  static_assert(FPW_ == 1 || FPW_ == 2 || FPW_ == 4, "frames per warp");
 };
 
-//                 id          T       C  P  Q  K  NB SR NST FP
+//                 id          T       C  P  Q  K  NB SR NST FP   (PV QV KV FPW PRO)
 using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 4, 3, false>;
 using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3, true>;
 using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3, true>;
-using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, true>;
+using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, true, 3, 8, 8, 1, true>;
 using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
 using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3, true>;
 // uint8 RGB (integer row math)
-using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3, false>;
+using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3, false, 3, 8, 8, 1, true>;
 using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, false>;
-using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false>;
+using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false, 2, 3, 6, 1, true>;
 // the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
-//                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV
-using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
-using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, false, 4, 9, 8>;
+//                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV FPW PRO
+using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8, 2, true>;
+using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, false, 4, 9, 8, 2, true>;
 // uint8, one channel
 using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 4, 3, false>;
 using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, false>;
-using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, false>;
+using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, true>;
 
 // ---------------------------------------------------------------------------
 // launch parameters
@@ -271,7 +287,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 // tiles
 // ---------------------------------------------------------------------------
 struct Tile {
-  int job, frame, strip, chunk;
+  int job, frame, strip, chunk;  // frame: the group of the job's frames FPW * frame .. + FPW - 1
 };
 
 template <class PR>
@@ -329,9 +345,10 @@ struct Offs {
 template <class Cl>
 __device__ __forceinline__ Offs<Cl> thread_offs(int lane) {
   Offs<Cl> o;
-  const int first = Cl::HLB + lane * Cl::EB - Cl::HB * Cl::VB;
+  const int sub = lane / Cl::LPS, li = lane % Cl::LPS;  // the lane's frame in the group, its lane in the strip
+  const int first = Cl::HLB + li * Cl::EB - Cl::HB * Cl::VB;
 #pragma unroll
-  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = win_off<Cl>(first + v * Cl::VB);
+  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = sub * Cl::FSTR + win_off<Cl>(first + v * Cl::VB);
   return o;
 }
 
@@ -378,14 +395,16 @@ __host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int W) {
 template <class Cl>
 __device__ __forceinline__ void apply_edge_fix(uint8_t* rowbase, const EdgeFix& f, int lane, int W, int xw) {
   using T = typename Cl::T;
-  for (int e = lane; e < f.nl + f.nr; e += 32) {
+  const int n = f.nl + f.nr;  // elements to fix per frame window
+  for (int e2 = lane; e2 < Cl::FPW * n; e2 += 32) {
+    const int sub = Cl::FPW == 1 ? 0 : e2 / n, e = e2 - sub * n;
     const bool left = e < f.nl;
     const int k = left ? e : e - f.nl;
     const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
     const int src = (left ? 0 : W - 1) * Cl::C + c - xw;
     const int dst = px * Cl::C + c - xw;
-    *reinterpret_cast<T*>(rowbase + win_off<Cl>(dst * Cl::SZ)) =
-        *reinterpret_cast<const T*>(rowbase + win_off<Cl>(src * Cl::SZ));
+    uint8_t* const wb = rowbase + sub * Cl::FSTR;
+    *reinterpret_cast<T*>(wb + win_off<Cl>(dst * Cl::SZ)) = *reinterpret_cast<const T*>(wb + win_off<Cl>(src * Cl::SZ));
   }
   // these generic-proxy writes must land before the TMA refills the stage
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -794,25 +813,29 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     const int rb0 = tl.chunk * jd.rbc;
     const int nblk = min(jd.rbc, nby - rb0);
     const int ys = rb0 * Q + Cl::BMINV;  // first pattern row; < 0 only for the top band (then == BMINV)
-    const int nst = Cl::NPS + (nblk * Q + SR - 1) / SR;
-    const int ystream = ys - Cl::EXTRA;  // frame row of stage 0's first row
+    const int nst = Cl::STG0 + ((nblk + Cl::VBLK) * Q + SR - 1) / SR;
+    const int ystream = ys + Cl::YOFF;  // frame row of stage 0's first row
     const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
     const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
     const bool fixing = fix.nl + fix.nr > 0;
-    const int blk0 = tl.strip * Cl::SBLK + lane * Cl::NB;
-    const bool active = blk0 * Cl::P < jd.OW;
+    const int frame0 = tl.frame * Cl::FPW;              // the group's first frame
+    const int nf = Cl::FPW == 1 ? 1 : min(Cl::FPW, jd.nframes - frame0);  // frames in the group
+    const int sub = lane / Cl::LPS;                     // this lane's frame in the group
+    const int blk0 = tl.strip * Cl::SBLK + (lane % Cl::LPS) * Cl::NB;
+    const bool active = sub < nf && blk0 * Cl::P < jd.OW;
     const int n_valid = jd.OW * Cl::C - blk0 * Cl::P * Cl::C;
-    T* const obase =
-        reinterpret_cast<T*>(jd.out) + (long long)tl.frame * jd.out_frame + (long long)blk0 * Cl::P * Cl::C;
+    T* const obase = reinterpret_cast<T*>(jd.out) + (long long)(frame0 + sub) * jd.out_frame +
+                     (long long)blk0 * Cl::P * Cl::C;
     const long long rowe = (long long)jd.OW * Cl::C;
 
     auto issue = [&](int s) {  // stage s of the tile into slot (g + s) mod NST
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
-      mbar_expect_tx(&full[slot], Cl::RTX);
+      mbar_expect_tx(&full[slot], (uint32_t)(nf * Cl::RTX));
+      for (int f = 0; f < nf; ++f)
 #pragma unroll
-      for (int bx = 0; bx < Cl::NBOX; ++bx)
-        tma_load_3d(ring + slot * Cl::RSTAGE + bx * Cl::BOXSTR, &jd.tmap, &full[slot], xw + bx * Cl::BOXE,
-                    ystream + s * SR, tl.frame);
+        for (int bx = 0; bx < Cl::NBOX; ++bx)
+          tma_load_3d(ring + slot * Cl::RSTAGE + f * Cl::FSTR + bx * Cl::BOXSTR, &jd.tmap, &full[slot],
+                      xw + bx * Cl::BOXE, ystream + s * SR, frame0 + f);
     };
     if (lane == 0)
       for (int s = 0; s < NST && s < nst; ++s) issue(s);
@@ -840,9 +863,9 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     };
 
     Row win[L];
-    // ---- prologue: pattern rows 0 .. L-Q-1
+    // ---- prologue: pattern rows 0 .. L-Q-1 (with PRO: the lead blocks below)
 #pragma unroll
-    for (int ps = 0; ps < Cl::NPS; ++ps) {
+    for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps) {
       uint8_t* sb = stage_wait(ps);
       if (!sb) {
         ok = false;
@@ -863,20 +886,26 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       stage_release(ps);
     }
     if (!ok) break;
-    if (ys < 0) {  // ys == BMINV: slots 0..LHV-1 are frame row 0, held in slot LHV
+    // top band (ys == BMINV): slots 0..LHV-1 are frame row 0, held in slot LHV
+    auto top_fix = [&]() {
+      if (ys < 0) {
 #pragma unroll
-      for (int i = 0; i < Cl::LHV; ++i) RM::copy(win[i], win[Cl::LHV]);
-    }
+        for (int i = 0; i < Cl::LHV; ++i) RM::copy(win[i], win[Cl::LHV]);
+      }
+    };
+    if constexpr (!Cl::PRO) top_fix();
     // ---- block steps, U rows (USTG stages, UBLK blocks) at a time.  A unit
     // whose blocks are all inside the tile, whose rows are all above the
     // frame's last row and whose outputs are all inside the frame, in a strip
     // that needs no border fix-up and has every lane active, runs a copy of
-    // the body without any of those checks.
+    // the body without any of those checks.  With PRO, blocks m < 0 are the
+    // lead blocks: their rows (those above frame row 0 included, filtered
+    // from the zero fill and then overwritten) only fill the window.
     auto unit = [&](auto fast, int u) {
       constexpr bool FAST = decltype(fast)::value;
 #pragma unroll
       for (int st = 0; st < Cl::USTG; ++st) {
-        const int s = Cl::NPS + u * Cl::USTG + st;
+        const int s = Cl::STG0 + u * Cl::USTG + st;
         if (!FAST && s >= nst) break;
         uint8_t* sb = stage_wait(s);
         if (!sb) {
@@ -887,7 +916,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
         for (int r = 0; r < SR; ++r) {
           const int ru = st * SR + r;       // row within the unit
           const int bq = ru / Q, q = ru - bq * Q;
-          const int m = u * Cl::UBLK + bq;  // block step
+          const int m = u * Cl::UBLK + bq - Cl::VBLK;  // block step
           if (FAST || m < nblk) {
             const int i = L - Q + q;
             if constexpr (FAST) {
@@ -902,21 +931,26 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
             if (q == Q - 1) {
               // the window holds block m's pattern: its P output rows
               if constexpr (FAST) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
-              else if (active) RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+              else if (active && (!Cl::PRO || m >= 0))
+                RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
 #pragma unroll
               for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
+              if constexpr (!FAST && Cl::PRO)
+                if (m == -1) top_fix();
             }
           }
         }
         stage_release(s);
       }
     };
-    const bool x_inside = !fixing && (tl.strip * Cl::SBLK + 32 * Cl::NB) * Cl::P <= jd.OW;  // every lane complete
-    const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
+    // every lane complete, every frame of the group present
+    const bool x_inside = !fixing && nf == Cl::FPW && (tl.strip + 1) * Cl::SBLK * Cl::P <= jd.OW;
+    const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
     for (int u = 0; ok && u < nunits; ++u) {
       if constexpr (Cl::FASTPATH) {
-        const int mend = (u + 1) * Cl::UBLK;  // one past the unit's last block
-        if (x_inside && mend <= nblk && ys + (mend - 1) * Q + L - 1 < H && (rb0 + mend) * P <= jd.OH) {
+        const int mend = (u + 1) * Cl::UBLK - Cl::VBLK;  // one past the unit's last block
+        if (x_inside && mend - Cl::UBLK >= 0 && mend <= nblk && ys + (mend - 1) * Q + L - 1 < H &&
+            (rb0 + mend) * P <= jd.OH) {
           unit(std::true_type{}, u);
           continue;
         }
@@ -964,13 +998,13 @@ __global__ void k_timeout_probe(long long limit) {
 // host side
 // ---------------------------------------------------------------------------
 struct HostGeom {
-  int sblk, spx, p, q, pv, boxe, sr, sz, c;
+  int sblk, spx, p, q, pv, boxe, sr, sz, c, fpw;
   CUtensorMapDataType dt;
 };
 
 template <class Cl>
 HostGeom host_geom() {
-  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C,
+  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW,
                   TmaType<typename Cl::T>::v};
 }
 
@@ -1147,7 +1181,7 @@ void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, 
   jd.strips = (nbx + hg.sblk - 1) / hg.sblk;
   jd.rbc = std::max(1, std::min(band > 0 ? band : pl->row_blocks, nby));
   jd.chunks = (nby + jd.rbc - 1) / jd.rbc;
-  jd.tiles = jd.strips * jd.chunks * n_frames;
+  jd.tiles = jd.strips * jd.chunks * ((n_frames + hg.fpw - 1) / hg.fpw);  // per group of fpw frames
   jd.out_vec = (((uintptr_t)out & 3u) == 0 && ((size_t)pl->out_w * pl->channels) % 4 == 0) ? 1 : 0;
 }
 
@@ -1191,7 +1225,9 @@ struct BandedJob {
 };
 
 int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
-  std::vector<long long> per_frame(n);
+  // units: block rows of one strip of a group of fpw frames (one warp's work per block step)
+  std::vector<long long> per_group(n), groups(n);
+  std::vector<int> fpw(n);
   long long units = 0;
   int cap = 0;
   bool fixed = false;
@@ -1200,8 +1236,10 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
     fixed = fixed || pl->schedule_set;
     const HostGeom hg = geom_of(pl->fast_class);
     const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.pv - 1) / hg.pv;
-    per_frame[i] = (nbx + hg.sblk - 1) / hg.sblk * nby;
-    units += per_frame[i] * jobs[i].n_frames;
+    fpw[i] = hg.fpw;
+    per_group[i] = (nbx + hg.sblk - 1) / hg.sblk * nby;
+    groups[i] = (jobs[i].n_frames + hg.fpw - 1) / hg.fpw;
+    units += per_group[i] * groups[i];
     cap = std::max(cap, pl->row_blocks);
   }
   if (fixed) {
@@ -1217,17 +1255,19 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
   long long acc = 0;
   int count = n;
   for (int i = n - 1; i >= 0 && acc < target; --i) {
-    const long long whole = per_frame[i] * jobs[i].n_frames;
-    if (acc + whole <= target || jobs[i].n_frames < 2) {
+    const long long whole = per_group[i] * groups[i];
+    if (acc + whole <= target || groups[i] < 2) {
       out[i].band = tail_band;
       acc += whole;
       continue;
     }
-    const int k = (int)std::min<long long>(jobs[i].n_frames - 1, (target - acc + per_frame[i] - 1) / per_frame[i]);
+    // the tail takes kg whole groups (a partial last group stays at the end)
+    const long long kg = std::min<long long>(groups[i] - 1, (target - acc + per_group[i] - 1) / per_group[i]);
     if (count + 1 > kMaxJobs) break;
     size_t fin = 0, fout = 0;
     ds_plan_frame_bytes(jobs[i].plan, &fin, &fout);
-    const int head = jobs[i].n_frames - k;
+    const int head = (int)(groups[i] - kg) * fpw[i];
+    const int k = jobs[i].n_frames - head;
     for (int m = count; m > i + 1; --m) out[m] = out[m - 1];
     out[i] = BandedJob{FastJob{jobs[i].plan, jobs[i].in, jobs[i].out, head}, band};
     out[i + 1] = BandedJob{FastJob{jobs[i].plan, static_cast<const uint8_t*>(jobs[i].in) + (size_t)head * fin,
@@ -1259,7 +1299,8 @@ std::string check_rows(const JobDesc& jd) {
   };
   constexpr int smem = 128 + WPC * (Cl::WARP_BYTES + Cl::NST * 8);
   if (smem > 227 * 1024) return fail("shared memory above 227 KB", smem, 0);
-  if (Cl::BOXSTR < Cl::SRR * Cl::BOXB) return fail("stage layout", Cl::BOXSTR, 0);
+  if (Cl::BOXSTR < Cl::SRR * Cl::BOXB || Cl::BOXSTR % 128 != 0) return fail("stage layout", Cl::BOXSTR, 0);
+  if (Cl::LPS * Cl::FPW != 32) return fail("lanes per frame", Cl::LPS, Cl::FPW);
   const int win = Cl::NBOX * Cl::BOXB;
   // L, Q, P: the vertical axis; PH: the horizontal phases per packet
   constexpr int L = Cl::LV, Q = Cl::QV, P = Cl::PV, PH = Cl::P;
@@ -1289,7 +1330,8 @@ std::string check_rows(const JobDesc& jd) {
         if (src < 0 || (src + 1) * Cl::SZ > win || dst < 0 || (dst + 1) * Cl::SZ > win)
           return fail("edge fix outside the window", src, dst);
       }
-      for (int lane = 0; lane < 32; ++lane) {
+      // every frame of a warp's group has the same window layout: lanes li of the strip
+      for (int lane = 0; lane < Cl::LPS; ++lane) {
         const int first = Cl::HLB + lane * Cl::EB - Cl::HB * Cl::VB;
         for (int v = 0; v < Cl::NVT; ++v) {
           const int b0 = first + v * Cl::VB;
@@ -1305,8 +1347,8 @@ std::string check_rows(const JobDesc& jd) {
       }
       // replay of the stream and window on frame-row indices: stage s holds
       // frame rows ystream + s*SR .. + SR - 1
-      const int nst = Cl::NPS + (nblk * Q + Cl::SRR - 1) / Cl::SRR;
-      const int ystream = ys - Cl::EXTRA;
+      const int nst = Cl::STG0 + ((nblk + Cl::VBLK) * Q + Cl::SRR - 1) / Cl::SRR;
+      const int ystream = ys + Cl::YOFF;
       int wrow[64];
       int sr = 0;  // rows consumed from the stream, checked against their position
       auto take = [&](int s, int r, int i) -> std::string {
@@ -1315,7 +1357,7 @@ std::string check_rows(const JobDesc& jd) {
         ++sr;
         return std::string();
       };
-      for (int ps = 0; ps < Cl::NPS; ++ps)
+      for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps)
         for (int r = 0; r < Cl::SRR; ++r) {
           const int i = ps * Cl::SRR + r - Cl::EXTRA;
           if (i < 0) continue;
@@ -1326,15 +1368,15 @@ std::string check_rows(const JobDesc& jd) {
           if (!e.empty()) return e;
           if (wrow[i] != y) return fail("prologue row mismatch", i, wrow[i]);
         }
-      if (ys < 0)
+      if (ys < 0 && !Cl::PRO)
         for (int i = 0; i < Cl::LHV; ++i) wrow[i] = wrow[Cl::LHV];
-      const int nunits = (nblk + Cl::UBLK - 1) / Cl::UBLK;
+      const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
       for (int u = 0; u < nunits; ++u)
         for (int st = 0; st < Cl::USTG; ++st) {
-          const int s = Cl::NPS + u * Cl::USTG + st;
+          const int s = Cl::STG0 + u * Cl::USTG + st;
           if (s >= nst) break;
           for (int r = 0; r < Cl::SRR; ++r) {
-            const int ru = st * Cl::SRR + r, bq = ru / Q, q = ru - bq * Q, m = u * Cl::UBLK + bq;
+            const int ru = st * Cl::SRR + r, bq = ru / Q, q = ru - bq * Q, m = u * Cl::UBLK + bq - Cl::VBLK;
             if (m >= nblk) continue;
             const int i = L - Q + q, y = ys + m * Q + i;
             if (y >= jd.H) wrow[i] = wrow[i - 1];
@@ -1344,13 +1386,19 @@ std::string check_rows(const JobDesc& jd) {
               if (wrow[i] != y) return fail("stream row mismatch", i, wrow[i]);
             }
             if (q != Q - 1) continue;
+            if (m < 0) {  // a lead block: no outputs, the window moves on
+              for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
+              if (m == -1 && ys < 0)
+                for (int i2 = 0; i2 < Cl::LHV; ++i2) wrow[i2] = wrow[Cl::LHV];
+              continue;
+            }
             const int rr = rb0 + m;
             for (int i2 = 0; i2 < L; ++i2) {
               int want = rr * Q + Cl::BMINV + i2;
               want = want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want);
               if (wrow[i2] != want) return fail("window row mismatch", i2, wrow[i2]);
             }
-            for (int lane = 0; lane < 32; ++lane) {
+            for (int lane = 0; lane < Cl::LPS; ++lane) {
               const int blk0 = strip * Cl::SBLK + lane * Cl::NB;
               if (blk0 * PH >= jd.OW) continue;
               const int nv = std::min(Cl::NOUT, jd.OW * Cl::C - blk0 * PH * Cl::C);
@@ -1363,7 +1411,9 @@ std::string check_rows(const JobDesc& jd) {
             for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
           }
         }
-      if (sr != nrow) return fail("stream rows left over", sr, nrow);
+      // with lead blocks every stream row above the frame's end is filtered (those above row 0 too)
+      const int want_rows = Cl::PRO ? std::min(ye, jd.H) - ystream : nrow;
+      if (sr != want_rows) return fail("stream rows left over", sr, want_rows);
     }
   }
   for (size_t i = 0; i < written.size(); ++i)

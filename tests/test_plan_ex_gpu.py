@@ -79,3 +79,78 @@ def test_cif_frames_in_one_batch_with_yuv_planes(oracle):
     finally:
         ds.ds_destroy(py)
         ds.ds_destroy(pc)
+
+
+CIF_PLANES = [(288, 352, ds.DS_U8_RGB), (288, 352, ds.DS_U8), (144, 176, ds.DS_U8)]
+
+
+@pytest.mark.parametrize("H,W,dt", CIF_PLANES)
+@pytest.mark.parametrize("n", [1, 2, 3, 7])
+def test_cif_frame_groups(oracle, H, W, dt, n):
+    """The CIF classes filter two frames per warp (half a warp each): odd
+    counts leave the last group half empty, and its missing frame must be
+    neither loaded nor written."""
+    pl = ds.ds_plan_create_ex(H, W, (3, 8), 8, (4, 9), 8, dt)
+    try:
+        assert ds.ds_plan_describe(pl).find("fused_tma") >= 0
+        x = frames((H, W), dt, n, 100 + n)
+        got = run_fused(pl, x)
+        assert_parity(got, oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), dt, "cif groups %dx%d n=%d" % (H, W, n))
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_cif_frame_groups_guarded_output(oracle):
+    """A half-empty last group writes nothing past its one frame: the output
+    buffer's next frame (a sentinel) is untouched."""
+    import torch
+
+    from tests.gpu_util import finish, stream, to_dev
+    pl = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8_RGB)
+    try:
+        n = 5
+        x = frames((288, 352), ds.DS_U8_RGB, n, 77)
+        xd = to_dev(x)
+        out = torch.full((n + 1, 128, 132, 3), 201, dtype=torch.uint8, device="cuda")
+        ds.ds_run_frames(pl, xd.data_ptr(), out.data_ptr(), n, stream())
+        finish()
+        got = out.cpu().numpy()
+        assert_parity(got[:n], oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8_RGB)
+        assert (got[n] == 201).all()
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_cif_frame_groups_split_tail(oracle):
+    """1201 CIF frames: long enough that the launch's last units run in
+    shorter bands, the job being split at a whole group of frames; the odd
+    count leaves the tail's last group half empty."""
+    pl = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8_RGB)
+    try:
+        x = frames((288, 352), ds.DS_U8_RGB, 1201, 1201)
+        got = run_fused(pl, x)
+        assert_parity(got, oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8_RGB, "cif 1201 frames")
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_cif_planes_odd_counts_in_one_batch(oracle):
+    """Y, U and V jobs of odd frame counts in one launch (each job's groups
+    are its own: a group never spans two jobs)."""
+    from tests.gpu_util import finish, out_buffer, stream, to_dev
+    py = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    pc = ds.ds_plan_create_ex(144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        counts = (3, 5, 1)
+        xs = [frames((288, 352), ds.DS_U8, counts[0], 31), frames((144, 176), ds.DS_U8, counts[1], 32),
+              frames((144, 176), ds.DS_U8, counts[2], 33)]
+        ins = [to_dev(a) for a in xs]
+        outs = [out_buffer(py, counts[0]), out_buffer(pc, counts[1]), out_buffer(pc, counts[2])]
+        plans = (py, pc, pc)
+        ds.ds_batch_run([(plans[i], ins[i].data_ptr(), outs[i].data_ptr(), counts[i]) for i in range(3)], stream())
+        finish()
+        for o, x in zip(outs, xs):
+            assert_parity(o.cpu().numpy(), oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8)
+    finally:
+        ds.ds_destroy(py)
+        ds.ds_destroy(pc)
