@@ -392,19 +392,24 @@ __host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int W) {
   return f;
 }
 
+// Applied to all SR rows of a stage at once: each element's source and
+// destination offsets are worked out once for the stage (one copy of this
+// code per stage wait, not per row).
 template <class Cl>
-__device__ __forceinline__ void apply_edge_fix(uint8_t* rowbase, const EdgeFix& f, int lane, int W, int xw) {
+__device__ __forceinline__ void apply_edge_fix(uint8_t* stagebase, const EdgeFix& f, int lane, int W, int xw) {
   using T = typename Cl::T;
-  const int n = f.nl + f.nr;  // elements to fix per frame window
+  const int n = f.nl + f.nr;  // elements to fix per row of a frame window
   for (int e2 = lane; e2 < Cl::FPW * n; e2 += 32) {
     const int sub = Cl::FPW == 1 ? 0 : e2 / n, e = e2 - sub * n;
     const bool left = e < f.nl;
     const int k = left ? e : e - f.nl;
     const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
-    const int src = (left ? 0 : W - 1) * Cl::C + c - xw;
-    const int dst = px * Cl::C + c - xw;
-    uint8_t* const wb = rowbase + sub * Cl::FSTR;
-    *reinterpret_cast<T*>(wb + win_off<Cl>(dst * Cl::SZ)) = *reinterpret_cast<const T*>(wb + win_off<Cl>(src * Cl::SZ));
+    const int src = sub * Cl::FSTR + win_off<Cl>(((left ? 0 : W - 1) * Cl::C + c - xw) * Cl::SZ);
+    const int dst = sub * Cl::FSTR + win_off<Cl>((px * Cl::C + c - xw) * Cl::SZ);
+#pragma unroll
+    for (int r = 0; r < Cl::SRR; ++r)
+      *reinterpret_cast<T*>(stagebase + r * Cl::BOXB + dst) =
+          *reinterpret_cast<const T*>(stagebase + r * Cl::BOXB + src);
   }
   // these generic-proxy writes must land before the TMA refills the stage
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -840,11 +845,16 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     if (lane == 0)
       for (int s = 0; s < NST && s < nst; ++s) issue(s);
     issued = g + (uint32_t)min(NST, nst);
-    // wait for stage s; returns the stage's row-0 base, or nullptr on timeout
-    auto stage_wait = [&](int s) -> uint8_t* {
+    // wait for stage s; returns the stage's row-0 base, or nullptr on timeout.
+    // FIXED: the stage's columns outside the frame get their border values
+    // (only tiles whose strip needs it)
+    auto stage_wait = [&](int s, auto fixed) -> uint8_t* {
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
       if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (G / NST) & 1u))) return nullptr;
-      return ring + slot * Cl::RSTAGE;
+      uint8_t* const sb = ring + slot * Cl::RSTAGE;
+      if constexpr (decltype(fixed)::value)
+        if (fixing) apply_edge_fix<Cl>(sb, fix, lane, jd.W, xw);
+      return sb;
     };
     // stage s fully read: refill its slot with stage s + NST
     auto stage_release = [&](int s) {
@@ -856,7 +866,6 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     };
     // H pass of one loaded row into a window row
     auto hrow_regs = [&](uint8_t* rowbase, Row& o) {
-      if (fixing) apply_edge_fix<Cl>(rowbase, fix, lane, jd.W, xw);
       uint32_t w[Cl::NWT];
       load_row<Cl>(rowbase, of, w);
       if (active) RM::h(w, prm, o);
@@ -866,7 +875,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     // ---- prologue: pattern rows 0 .. L-Q-1 (with PRO: the lead blocks below)
 #pragma unroll
     for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps) {
-      uint8_t* sb = stage_wait(ps);
+      uint8_t* sb = stage_wait(ps, std::true_type{});
       if (!sb) {
         ok = false;
         break;
@@ -907,7 +916,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       for (int st = 0; st < Cl::USTG; ++st) {
         const int s = Cl::STG0 + u * Cl::USTG + st;
         if (!FAST && s >= nst) break;
-        uint8_t* sb = stage_wait(s);
+        uint8_t* sb = stage_wait(s, std::integral_constant<bool, !FAST>{});
         if (!sb) {
           ok = false;
           return;
