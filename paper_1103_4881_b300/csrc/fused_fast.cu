@@ -190,14 +190,14 @@ using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
 using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3, true>;
 // uint8 RGB (integer row math)
 using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3, false, 3, 8, 8, 1, true>;
-using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, false>;
+using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, true>;
 using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false, 2, 3, 6, 1, true>;
 // the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
 //                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV FPW PRO
 using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8, 2, true>;
-using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, false, 4, 9, 8, 2, true>;
+using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, true, 4, 9, 8, 2, true>;
 // uint8, one channel
-using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 4, 3, false>;
+using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 4, 3, false, 3, 8, 8, 1, true>;
 using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, false>;
 using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, true>;
 
@@ -400,7 +400,9 @@ __device__ __forceinline__ void apply_edge_fix(uint8_t* stagebase, const EdgeFix
   using T = typename Cl::T;
   const int n = f.nl + f.nr;  // elements to fix per row of a frame window
   for (int e2 = lane; e2 < Cl::FPW * n; e2 += 32) {
-    const int sub = Cl::FPW == 1 ? 0 : e2 / n, e = e2 - sub * n;
+    int sub = 0;  // e2 / n, for at most 4 frames
+    if constexpr (Cl::FPW > 1) sub = (e2 >= n) + (Cl::FPW > 2 ? (e2 >= 2 * n) + (e2 >= 3 * n) : 0);
+    const int e = e2 - sub * n;
     const bool left = e < f.nl;
     const int k = left ? e : e - f.nl;
     const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
@@ -600,28 +602,39 @@ __device__ __forceinline__ uint32_t pack4(int v0, int v1, int v2, int v3) {
   return d;
 }
 
-// Store n_valid (<= 4*NW) bytes of words w to o with the widest aligned stores.
-template <int NB>
+// Store the first n_valid (<= N) of a lane's N output bytes (packed 4 to a
+// word in w).  Every lane of a warp takes the same path: wide stores when N
+// is a multiple of 4 (so all lanes share the row's alignment), byte stores
+// otherwise or at a frame's right edge.
+template <int N>
 __device__ __forceinline__ void store_bytes(uint8_t* o, const uint32_t* w, int n_valid) {
-  constexpr int NW = (NB + 3) / 4;
-  const uintptr_t a = reinterpret_cast<uintptr_t>(o);
-  if (n_valid >= NB && (a & 3) == 0) {
+  if constexpr (N % 4 == 0) {
+    const uintptr_t a = reinterpret_cast<uintptr_t>(o);
+    if (n_valid >= N) {
+      if constexpr (N % 16 == 0) {
+        if ((a & 15) == 0) {
 #pragma unroll
-    for (int i = 0; i < NB / 4; ++i) reinterpret_cast<uint32_t*>(o)[i] = w[i];
+          for (int i = 0; i < N / 16; ++i)
+            reinterpret_cast<uint4*>(o)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+          return;
+        }
+      }
+      if constexpr (N % 8 == 0) {
+        if ((a & 7) == 0) {
 #pragma unroll
-    for (int i = NB / 4 * 4; i < NB; ++i) o[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
-    return;
+          for (int i = 0; i < N / 8; ++i) reinterpret_cast<uint2*>(o)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
+          return;
+        }
+      }
+      if ((a & 3) == 0) {
+#pragma unroll
+        for (int i = 0; i < N / 4; ++i) reinterpret_cast<uint32_t*>(o)[i] = w[i];
+        return;
+      }
+    }
   }
-  if (n_valid >= NB && (a & 1) == 0) {
 #pragma unroll
-    for (int i = 0; i < NB / 2; ++i)
-      reinterpret_cast<unsigned short*>(o)[i] = (unsigned short)(w[(2 * i) >> 2] >> (8 * ((2 * i) & 3)));
-    if constexpr (NB % 2) o[NB - 1] = (uint8_t)(w[(NB - 1) >> 2] >> (8 * ((NB - 1) & 3)));
-    return;
-  }
-  (void)NW;
-#pragma unroll
-  for (int i = 0; i < NB; ++i)
+  for (int i = 0; i < N; ++i)
     if (i < n_valid) o[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
 }
 
@@ -828,7 +841,9 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     const int sub = lane / Cl::LPS;                     // this lane's frame in the group
     const int blk0 = tl.strip * Cl::SBLK + (lane % Cl::LPS) * Cl::NB;
     const bool active = sub < nf && blk0 * Cl::P < jd.OW;
-    const int n_valid = jd.OW * Cl::C - blk0 * Cl::P * Cl::C;
+    // elements this lane stores per output row (none for an inactive lane,
+    // which runs the same code on in-window data with its stores masked)
+    const int n_valid = active ? jd.OW * Cl::C - blk0 * Cl::P * Cl::C : 0;
     T* const obase = reinterpret_cast<T*>(jd.out) + (long long)(frame0 + sub) * jd.out_frame +
                      (long long)blk0 * Cl::P * Cl::C;
     const long long rowe = (long long)jd.OW * Cl::C;
@@ -868,7 +883,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     auto hrow_regs = [&](uint8_t* rowbase, Row& o) {
       uint32_t w[Cl::NWT];
       load_row<Cl>(rowbase, of, w);
-      if (active) RM::h(w, prm, o);
+      RM::h(w, prm, o);
     };
 
     Row win[L];
@@ -933,14 +948,16 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
               load_row<Cl>(sb + r * Cl::BOXB, of, w);
               RM::h(w, prm, win[i]);
             } else {
+              // rows below the frame's last repeat it (filtered from the zero
+              // fill, then replaced: a select, not a branch)
               const int y = ys + m * Q + i;
+              hrow_regs(sb + r * Cl::BOXB, win[i]);
               if (y >= H) RM::copy(win[i], win[i - 1]);
-              else hrow_regs(sb + r * Cl::BOXB, win[i]);
             }
             if (q == Q - 1) {
               // the window holds block m's pattern: its P output rows
               if constexpr (FAST) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
-              else if (active && (!Cl::PRO || m >= 0))
+              else if (!Cl::PRO || m >= 0)
                 RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
 #pragma unroll
               for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
