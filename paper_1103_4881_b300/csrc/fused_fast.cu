@@ -78,14 +78,12 @@ __host__ __device__ constexpr int phase_b(int P, int Q, int K, int j) {
 }
 __host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
 
-template <typename T>
-struct TmaType;
-template <>
-struct TmaType<float> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32; };
-template <>
-struct TmaType<__half> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT16; };
-template <>
-struct TmaType<uint8_t> { static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_UINT8; };
+// The tensor maps view every row as 8-byte elements, whatever the pixel type:
+// a box row can then hold 256 x 8 bytes, so one box covers a strip's window
+// (one TMA copy per stage and frame).  Rows are a multiple of 16 bytes on
+// the fast path, and every strip's window starts on a 16-byte boundary.
+constexpr int kTmaElem = 8;
+constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_UINT64;
 
 // A fast-path class: data type, channels, horizontal ratio P/Q and taps K,
 // vertical ratio PV/QV and taps KV (by default those of the horizontal axis),
@@ -129,9 +127,9 @@ struct Cls {
   static constexpr int SBLK = LPS * NB;             // packets (blocks) per strip
   static constexpr int SPX = SBLK * Q;              // input pixels per strip
   static constexpr int WINB = HLB + SPX * C * SZ + RHB;
-  static constexpr int NBOX = cdiv(WINB / SZ, 256);
+  static constexpr int NBOX = cdiv(WINB / kTmaElem, 256);
   static constexpr int BOXB = rup(cdiv(WINB, NBOX), 16);
-  static constexpr int BOXE = BOXB / SZ;
+  static constexpr int BOXE = BOXB / kTmaElem;         // box width in TMA elements
   static constexpr int BOXSTR = rup(SR_ * BOXB, 128);  // each box lands 128-B aligned
   static constexpr int FSTR = NBOX * BOXSTR;          // one frame's window in a stage
   static constexpr int RSTAGE = FPW_ * FSTR;
@@ -172,6 +170,7 @@ struct Cls {
   static_assert(EB % 4 == 0, "a lane's chunk must be whole words");
   static_assert(HB * VB <= HLB && HA * VB <= RHB, "halo vectors must lie in the loaded window");
   static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
+  static_assert((SPX * C * SZ) % 16 == 0 && HLB % 16 == 0, "strip windows start on 16-byte boundaries");
   static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
   static_assert(P * K <= kMaxTaps && PV * KV <= kMaxTaps, "tap table size");
   static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
@@ -833,7 +832,8 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     const int ys = rb0 * Q + Cl::BMINV;  // first pattern row; < 0 only for the top band (then == BMINV)
     const int nst = Cl::STG0 + ((nblk + Cl::VBLK) * Q + SR - 1) / SR;
     const int ystream = ys + Cl::YOFF;  // frame row of stage 0's first row
-    const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
+    const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;  // window start, in elements
+    const int xt = xw * Cl::SZ / kTmaElem;                          // ... in TMA elements (exact)
     const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
     const bool fixing = fix.nl + fix.nr > 0;
     const int frame0 = tl.frame * Cl::FPW;              // the group's first frame
@@ -855,7 +855,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
 #pragma unroll
         for (int bx = 0; bx < Cl::NBOX; ++bx)
           tma_load_3d(ring + slot * Cl::RSTAGE + f * Cl::FSTR + bx * Cl::BOXSTR, &jd.tmap, &full[slot],
-                      xw + bx * Cl::BOXE, ystream + s * SR, frame0 + f);
+                      xt + bx * Cl::BOXE, ystream + s * SR, frame0 + f);
     };
     if (lane == 0)
       for (int s = 0; s < NST && s < nst; ++s) issue(s);
@@ -1030,8 +1030,7 @@ struct HostGeom {
 
 template <class Cl>
 HostGeom host_geom() {
-  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW,
-                  TmaType<typename Cl::T>::v};
+  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW, kTmaType};
 }
 
 // Geometry of the kernel that runs class `cls`.
@@ -1219,9 +1218,9 @@ ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return DS_ERR_CUDA;
   }
-  const cuuint64_t row_elems = (cuuint64_t)pl->in_w * pl->channels;
-  cuuint64_t dims[3] = {row_elems, (cuuint64_t)pl->in_h, (cuuint64_t)job.n_frames};
-  cuuint64_t strides[2] = {row_elems * hg.sz, row_elems * hg.sz * (cuuint64_t)pl->in_h};
+  const cuuint64_t row_bytes = (cuuint64_t)pl->in_w * pl->channels * hg.sz;  // a multiple of 16
+  cuuint64_t dims[3] = {row_bytes / kTmaElem, (cuuint64_t)pl->in_h, (cuuint64_t)job.n_frames};
+  cuuint64_t strides[2] = {row_bytes, row_bytes * (cuuint64_t)pl->in_h};
   cuuint32_t box[3] = {(cuuint32_t)hg.boxe, (cuuint32_t)hg.sr, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(&jd.tmap, hg.dt, 3, const_cast<void*>(job.in), dims, strides, box, estr,
@@ -1343,8 +1342,9 @@ std::string check_rows(const JobDesc& jd) {
       if (nrow < 1) return fail("empty stream", ys, ye);
       if (ys < 0 && ys != Cl::BMINV) return fail("top band offset", ys, 0);
       const int xw = strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
+      if ((xw * Cl::SZ) % kTmaElem != 0) return fail("window start not a whole TMA element", xw, 0);
       for (int bx = 0; bx < Cl::NBOX; ++bx) {
-        const long long xb = (long long)(xw + bx * Cl::BOXE) * Cl::SZ;
+        const long long xb = (long long)(xw * Cl::SZ / kTmaElem + bx * Cl::BOXE) * kTmaElem;
         if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", xw, bx);
       }
       const EdgeFix fx = edge_fix<Cl>(strip, jd.W);
