@@ -181,7 +181,7 @@ struct Cls {
 };
 
 //                 id          T       C  P  Q  K  NB SR NST FP   (PV QV KV FPW PRO)
-using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 4, 3, false>;
+using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 8, 2, false>;
 using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3, true>;
 using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3, true>;
 using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, true, 3, 8, 8, 1, true>;
