@@ -175,7 +175,8 @@ def time_cpu_oracle(w, budget_s=15.0):
     return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": "%d of the workload's %d frames (whole frames, FP64 / int64 loop nest, OpenMP over frames)"
                       % (n, w.frames),
-            "seconds": round(dt, 3)}
+            "seconds": round(dt, 3),
+            "one_core": {"value": 1.0 / max(one, 1e-9), "unit": "frames/s", "sample": "frame 0, one thread"}}
 
 
 def reference_arm(args, w, rank, world):
