@@ -131,7 +131,7 @@ int default_row_blocks(int fast_class) {
     case kFcF32_12: case kFcF16_12: return 24;
     case kFcU8C3_12: return 40;
     case kFcF32_23: case kFcF16_23: case kFcU8C3_23: return 20;
-    case kFcU8C3_CIF: case kFcU8C1_CIF: return 8;
+    case kFcU8C3_CIF: case kFcU8C1_CIF: return 16;
     case kFcU8C1_38: return 16;
     case kFcU8C1_12: return 24;
     case kFcU8C1_23: return 20;
