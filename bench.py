@@ -64,7 +64,7 @@ def kernel_source_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("fused_fast.cu", "pixel.cuh", "internal.h"):
+    for name in ("fused_fast.cu", "pixel.cuh", "internal.h", "plan.cpp"):  # kernels and their schedule
         with open(os.path.join(ROOT, "paper_1103_4881_b300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
