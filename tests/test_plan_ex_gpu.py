@@ -154,3 +154,20 @@ def test_cif_planes_odd_counts_in_one_batch(oracle):
     finally:
         ds.ds_destroy(py)
         ds.ds_destroy(pc)
+
+
+@pytest.mark.parametrize("dt", [ds.DS_U8_RGB, ds.DS_U8])
+@pytest.mark.parametrize("H", [3, 5, 10, 30])
+@pytest.mark.parametrize("W", [16, 48, 272])
+@pytest.mark.parametrize("n", [1, 3])
+def test_cif_classes_on_tiny_and_ragged_frames(oracle, dt, H, W, n):
+    """The CIF classes' lead blocks on frames shorter than a window (every
+    row clamped), strips narrower than a half warp, and half-empty groups."""
+    pl = ds.ds_plan_create_ex(H, W, (3, 8), 8, (4, 9), 8, dt)
+    try:
+        assert '"fused_tma"' in ds.ds_plan_describe(pl)
+        x = frames((H, W), dt, n, H * 1000 + W * 10 + n)
+        assert_parity(run_fused(pl, x), oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), dt,
+                      "cif %dx%d n=%d dt=%d" % (H, W, n, dt))
+    finally:
+        ds.ds_destroy(pl)
