@@ -186,17 +186,17 @@ using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3, true>;
 using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3, true>;
 using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, true, 3, 8, 8, 1, true>;
 using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
-using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3, true>;
+using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 2, true>;
 // uint8 RGB (integer row math)
-using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 4, 3, false, 3, 8, 8, 1, true>;
+using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 8, 2, false, 3, 8, 8, 1, true>;
 using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, true>;
 using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false, 2, 3, 6, 1, true>;
 // the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
 //                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV FPW PRO
-using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 3, 4, false, 4, 9, 8, 2, true>;
-using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 3, 4, true, 4, 9, 8, 2, true>;
+using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 9, 2, false, 4, 9, 8, 2, true>;
+using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 9, 2, true, 4, 9, 8, 2, true>;
 // uint8, one channel
-using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 4, 3, false, 3, 8, 8, 1, true>;
+using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 8, 2, false, 3, 8, 8, 1, true>;
 using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, false>;
 using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, true>;
 
