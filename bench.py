@@ -167,14 +167,19 @@ def time_cpu_oracle(w, budget_s=15.0):
     n = int(max(1, min(w.frames, cores * max(1, int(budget_s / max(one, 1e-3) / max(cores, 1))), 4 * cores)))
     n = max(1, min(n, w.frames))
     xs = synth.plane_frames(w, range(n))
-    t = time.perf_counter()
-    for x in xs:
-        oracle_filter(w, x, threads=0)
-    dt = time.perf_counter() - t
+    # whole passes over the sample until about the time budget is spent
+    passes, t = 0, time.perf_counter()
+    while True:
+        for x in xs:
+            oracle_filter(w, x, threads=0)
+        passes += 1
+        dt = time.perf_counter() - t
+        if dt >= 0.66 * budget_s or passes >= 1000:
+            break
     del xs
-    return {"value": n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of the workload's %d frames (whole frames, FP64 / int64 loop nest, OpenMP over frames)"
-                      % (n, w.frames),
+    return {"value": passes * n / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "%d pass(es) over %d of the workload's %d frames (whole frames, FP64 / int64 loop nest, "
+                      "OpenMP over frames)" % (passes, n, w.frames),
             "seconds": round(dt, 3),
             "one_core": {"value": 1.0 / max(one, 1e-9), "unit": "frames/s", "sample": "frame 0, one thread"}}
 
