@@ -165,6 +165,11 @@ struct Cls {
   static constexpr int VBLK = PRO_ ? rup(cdiv(PRE, QV), UBLK) : 0;  // lead blocks
   static constexpr int STG0 = PRO_ ? 0 : NPS;                         // first stage of unit 0
   static constexpr int YOFF = PRO_ ? PRE - VBLK * QV : -EXTRA;        // stream start - first pattern row
+  // Stage 0 of a tile is loaded S0SHIFT rows later than the stream grid puts
+  // it: it starts at the first pattern row, so the EXTRA alignment rows are
+  // not read from memory (its last EXTRA rows repeat the first rows of
+  // stage 1, fetched at the same time and served from L2).
+  static constexpr int S0SHIFT = PRO_ ? 0 : EXTRA;
   __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
   __host__ __device__ static constexpr int bv(int j) { return phase_b(PV, QV, KV, j); }
   static_assert(EB % 4 == 0, "a lane's chunk must be whole words");
@@ -855,7 +860,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
 #pragma unroll
         for (int bx = 0; bx < Cl::NBOX; ++bx)
           tma_load_3d(ring + slot * Cl::RSTAGE + f * Cl::FSTR + bx * Cl::BOXSTR, &jd.tmap, &full[slot],
-                      xt + bx * Cl::BOXE, ystream + s * SR, frame0 + f);
+                      xt + bx * Cl::BOXE, ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0), frame0 + f);
     };
     if (lane == 0)
       for (int s = 0; s < NST && s < nst; ++s) issue(s);
@@ -897,8 +902,10 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       }
 #pragma unroll
       for (int r = 0; r < SR; ++r) {
-        const int i = ps * SR + r - Cl::EXTRA;  // pattern row index
-        if (i < 0) continue;                    // loaded only to align the stages
+        // pattern row index: stage 0 holds pattern rows 0.. (S0SHIFT), and
+        // its last EXTRA rows repeat rows of stage 1
+        const int i = ps == 0 ? r - Cl::EXTRA + Cl::S0SHIFT : ps * SR + r - Cl::EXTRA;
+        if (i < 0 || (ps == 0 && r >= SR - Cl::S0SHIFT)) continue;
         const int y = ys + i;
         if (y < 0) continue;                    // top band: filled from frame row 0 below
         if (i > 0 && y >= H) {
@@ -1379,14 +1386,14 @@ std::string check_rows(const JobDesc& jd) {
       int sr = 0;  // rows consumed from the stream, checked against their position
       auto take = [&](int s, int r, int i) -> std::string {
         if (s >= nst) return fail("stage beyond the tile", s, nst);
-        wrow[i] = ystream + s * Cl::SRR + r;
+        wrow[i] = ystream + s * Cl::SRR + r + (s == 0 ? Cl::S0SHIFT : 0);
         ++sr;
         return std::string();
       };
       for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps)
         for (int r = 0; r < Cl::SRR; ++r) {
-          const int i = ps * Cl::SRR + r - Cl::EXTRA;
-          if (i < 0) continue;
+          const int i = ps == 0 ? r - Cl::EXTRA + Cl::S0SHIFT : ps * Cl::SRR + r - Cl::EXTRA;
+          if (i < 0 || (ps == 0 && r >= Cl::SRR - Cl::S0SHIFT)) continue;
           const int y = ys + i;
           if (y < 0) continue;
           if (i > 0 && y >= jd.H) { wrow[i] = wrow[i - 1]; continue; }
