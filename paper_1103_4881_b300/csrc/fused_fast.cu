@@ -20,6 +20,12 @@
 //   each time q new rows have entered the window, the warp computes the p
 //     output rows of one block from it and stores them.
 //
+// Per class: a warp may split into groups of 32/FPW lanes that filter the
+// same strip and band of FPW frames (narrow frames), and the window may be
+// filled by lead blocks run through the loop body instead of a separate
+// unrolled prologue.  The row loop has no per-lane branch: lanes past the
+// frame's edge compute on in-window data with their stores masked.
+//
 // Float data accumulate in FP32 with fmaf in tap order t = 0..K-1 from 0, the
 // same sequence as the general kernels; uint8 data use exact integer dot
 // products (dp2a) whose rounding is the same integer formula; so results are
