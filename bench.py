@@ -308,7 +308,17 @@ def main():
     torch.cuda.synchronize()
     ds.ds_stream_check(st)
 
+    def clock_warm(fn, ms=20.0):
+        # keep the GPU busy right before a timed region: after an idle gap
+        # (a sync, the clock sampler starting) its clocks take a moment to
+        # come back up, which would land inside a short timed region
+        t = time.perf_counter()
+        while (time.perf_counter() - t) * 1e3 < ms:
+            fn()
+            torch.cuda.synchronize()
+
     def timed(fn, k):
+        clock_warm(fn)
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -348,6 +358,7 @@ def main():
         "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "u8", 3: "u8"}[w.dtype], "data": "synthetic",
         "config": dict(workload_config(w, n), **{
                    "form": "batched persistent fused H+V kernel, CUDA graph replay",
+                   "warm": "W warm-up steps, then about 20 ms more of untimed steps right before the timed region",
                    "l2": ("inputs larger than L2 (%.0f MB per step vs 126 MB)" if n * sum(f[0] for f in fbytes) > 126e6
                           else "inputs smaller than L2 (%.0f MB per step vs 126 MB): not an HBM figure")
                          % (n * sum(f[0] for f in fbytes) / 1e6),
@@ -360,7 +371,9 @@ def main():
     }
 
     if rank == 0 and not args.no_extras:
-        k2 = max(5, min(args.steps // 50, 50))
+        # enough repetitions for at least 256 frames per form (a 1-frame workload
+        # would otherwise time a few launches, dominated by host jitter)
+        k2 = max(5, min(args.steps // 50, 50), -(-256 // n))
         # plain per-frame: one ds_run per frame (and plane)
         def per_frame():
             for i in range(n):
