@@ -1262,23 +1262,32 @@ struct BandedJob {
   int band;  // 0 = the plan's
 };
 
+// The launch's last tiles, from the end: tiles per pipeline at band / div.
+struct TailLevel {
+  int div, tiles_per_pipeline;
+};
+constexpr TailLevel kTail[] = {{4, 2}};
+
 int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
   // units: block rows of one strip of a group of fpw frames (one warp's work per block step)
-  std::vector<long long> per_group(n), groups(n);
-  std::vector<int> fpw(n);
+  auto geometry = [](const FastJob& j, long long& per_group, long long& groups, int& fpw) {
+    const ds_plan* pl = j.plan;
+    const HostGeom hg = geom_of(pl->fast_class);
+    const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.pv - 1) / hg.pv;
+    fpw = hg.fpw;
+    per_group = (nbx + hg.sblk - 1) / hg.sblk * nby;
+    groups = (j.n_frames + hg.fpw - 1) / hg.fpw;
+  };
   long long units = 0;
   int cap = 0;
   bool fixed = false;
   for (int i = 0; i < n; ++i) {
-    const ds_plan* pl = jobs[i].plan;
-    fixed = fixed || pl->schedule_set;
-    const HostGeom hg = geom_of(pl->fast_class);
-    const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.pv - 1) / hg.pv;
-    fpw[i] = hg.fpw;
-    per_group[i] = (nbx + hg.sblk - 1) / hg.sblk * nby;
-    groups[i] = (jobs[i].n_frames + hg.fpw - 1) / hg.fpw;
-    units += per_group[i] * groups[i];
-    cap = std::max(cap, pl->row_blocks);
+    long long pg = 0, ng = 0;
+    int f = 1;
+    geometry(jobs[i], pg, ng, f);
+    units += pg * ng;
+    fixed = fixed || jobs[i].plan->schedule_set;
+    cap = std::max(cap, jobs[i].plan->row_blocks);
   }
   if (fixed) {
     for (int i = 0; i < n; ++i) out[i] = BandedJob{jobs[i], 0};
@@ -1286,33 +1295,42 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
   }
   pipelines = std::max(1, pipelines);
   const int band = (int)std::max<long long>(1, std::min<long long>(cap, (units + pipelines - 1) / pipelines));
-  const int tail_band = std::max(1, band / 4);
   for (int i = 0; i < n; ++i) out[i] = BandedJob{jobs[i], band};
   if (band < 4) return n;
-  const long long target = 2ll * pipelines * tail_band;
-  long long acc = 0;
-  int count = n;
-  for (int i = n - 1; i >= 0 && acc < target; --i) {
-    const long long whole = per_group[i] * groups[i];
-    if (acc + whole <= target || groups[i] < 2) {
-      out[i].band = tail_band;
-      acc += whole;
-      continue;
+  // walk back from the last job, giving each tail level its units (whole
+  // jobs, or the last groups of a job split in two)
+  int count = n, i = n - 1;
+  for (const TailLevel& lv : kTail) {
+    const int lband = std::max(1, band / lv.div);
+    const long long target = (long long)lv.tiles_per_pipeline * pipelines * lband;
+    long long acc = 0;
+    while (i >= 0 && acc < target) {
+      long long pg = 0, ng = 0;
+      int f = 1;
+      geometry(out[i].job, pg, ng, f);
+      const long long whole = pg * ng;
+      if (acc + whole <= target || ng < 2) {
+        out[i].band = lband;
+        acc += whole;
+        --i;
+        continue;
+      }
+      if (count + 1 > kMaxJobs) return count;
+      // the level takes the job's last kg whole groups (a partial last group
+      // stays at the end); the head stays at index i for the next level
+      const long long kg = std::min<long long>(ng - 1, (target - acc + pg - 1) / pg);
+      const FastJob j = out[i].job;
+      size_t fin = 0, fout = 0;
+      ds_plan_frame_bytes(j.plan, &fin, &fout);
+      const int head = (int)(ng - kg) * f;
+      for (int m = count; m > i + 1; --m) out[m] = out[m - 1];
+      out[i] = BandedJob{FastJob{j.plan, j.in, j.out, head}, band};
+      out[i + 1] = BandedJob{FastJob{j.plan, static_cast<const uint8_t*>(j.in) + (size_t)head * fin,
+                                     static_cast<uint8_t*>(j.out) + (size_t)head * fout, j.n_frames - head},
+                             lband};
+      ++count;
+      acc = target;
     }
-    // the tail takes kg whole groups (a partial last group stays at the end)
-    const long long kg = std::min<long long>(groups[i] - 1, (target - acc + per_group[i] - 1) / per_group[i]);
-    if (count + 1 > kMaxJobs) break;
-    size_t fin = 0, fout = 0;
-    ds_plan_frame_bytes(jobs[i].plan, &fin, &fout);
-    const int head = (int)(groups[i] - kg) * fpw[i];
-    const int k = jobs[i].n_frames - head;
-    for (int m = count; m > i + 1; --m) out[m] = out[m - 1];
-    out[i] = BandedJob{FastJob{jobs[i].plan, jobs[i].in, jobs[i].out, head}, band};
-    out[i + 1] = BandedJob{FastJob{jobs[i].plan, static_cast<const uint8_t*>(jobs[i].in) + (size_t)head * fin,
-                                   static_cast<uint8_t*>(jobs[i].out) + (size_t)head * fout, k},
-                           tail_band};
-    ++count;
-    break;
   }
   return count;
 }
