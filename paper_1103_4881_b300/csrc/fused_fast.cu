@@ -113,8 +113,9 @@ struct Cls {
   static constexpr int PV = PV_, QV = QV_, KV = KV_;
   static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
   // resident CTAs per SM the registers are budgeted for (4 x 4 warps; the
-  // uint8 1/2 class fits in the tighter budget of 5, which measures faster)
-  static constexpr int MINB = (ID == kFcU8C3_12) ? 5 : 4;
+  // uint8 RGB 1/2 and one-plane CIF classes fit in the tighter budget of 5,
+  // which measures faster for them)
+  static constexpr int MINB = (ID == kFcU8C3_12 || ID == kFcU8C1_CIF) ? 5 : 4;
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
