@@ -124,7 +124,6 @@ struct Cls {
   // horizontal axis: the strip, its halo columns and the lane chunks
   static constexpr int BMIN = phase_b(P, Q, K, 0);
   static constexpr int BMAX = phase_b(P, Q, K, P - 1);
-  static constexpr int L = BMAX - BMIN + K;         // pattern length (pixels per block window)
   static constexpr int LH = -BMIN;                  // halo pixels left of a block
   static constexpr int RH = BMAX + K - Q;           // halo pixels right of a block
   static constexpr int E = NB * Q * C;              // elements per lane and row
@@ -190,6 +189,7 @@ struct Cls {
   static_assert(LV * (SZ == 1 ? (NOUT + 3) / 4 : NOUT) <= 48, "register window too large");
   static_assert(U <= 16, "iteration unit too long to unroll");
   static_assert(FPW_ == 1 || FPW_ == 2 || FPW_ == 4, "frames per warp");
+  static_assert(NX == (LH + NB * Q + RH) * C, "lane window (float row math)");
 };
 
 //                 id          T       C  P  Q  K  NB SR NST FP   (PV QV KV FPW PRO)
@@ -665,7 +665,6 @@ struct RowMath<Cl, true> {
   static constexpr int N = Cl::NOUT;
   static constexpr int NW = (N + 3) / 4;
   static constexpr int NXP = Cl::LH + Cl::NB * Q + Cl::RH;  // window pixels of a lane
-  static constexpr int NCW = (NXP + 1 + 3) / 4;             // channel words (+1: odd-start pad)
   static constexpr int NPR = (LV + 2) / 2;                  // window row pairs (+1 slot of pad)
   static_assert(Cl::HB * Cl::VB >= Cl::LH * C, "pixel slot 0 must be a loaded byte");
   static_assert(Cl::HB * Cl::VB - Cl::LH * C + NXP * C <= Cl::NVT * Cl::VB, "gathered bytes must be loaded");
@@ -722,6 +721,7 @@ struct RowMath<Cl, true> {
         }
     } else {
       // one channel word per 4 consecutive pixel slots (pairs 2k, 2k+1)
+      constexpr int NCW = (NXP + 1 + 3) / 4;  // channel words (+1: odd-start pad)
       uint32_t cw[C][NCW];
 #pragma unroll
       for (int c = 0; c < C; ++c)
