@@ -112,10 +112,13 @@ struct Cls {
   static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
   static constexpr int PV = PV_, QV = QV_, KV = KV_;
   static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
-  // resident CTAs per SM the registers are budgeted for (4 x 4 warps; the
-  // uint8 RGB 1/2 and one-plane CIF classes fit in the tighter budget of 5,
-  // which measures faster for them)
-  static constexpr int MINB = (ID == kFcU8C3_12 || ID == kFcU8C1_CIF) ? 5 : 4;
+  // warps (independent tile pipelines) per CTA, and the resident CTAs per SM
+  // the registers are budgeted for: 4 x 4 warps; the uint8 RGB 1/2 and
+  // one-plane CIF classes fit in the tighter budget of 5, which measures
+  // faster for them; the CIF RGB class, whose stage rings hold a CTA of 4 to
+  // 3 per SM, runs one-warp CTAs (budgeted for 14; 13 fit by shared memory)
+  static constexpr int WPC = (ID == kFcU8C3_CIF) ? 1 : 4;
+  static constexpr int MINB = (ID == kFcU8C3_CIF) ? 14 : ((ID == kFcU8C3_12 || ID == kFcU8C1_CIF) ? 5 : 4);
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
@@ -1086,16 +1089,13 @@ struct KernelInfo {
   int threads;
 };
 
-constexpr int kRowsWPC = 4;  // warps (independent pipelines) per CTA of the row-streaming kernel
-
-// Registers are budgeted for Cl::MINB resident CTAs (4 warps each) per SM,
-// which the shared-memory footprint of the stage rings also allows.
+// Registers are budgeted for Cl::MINB resident CTAs (of Cl::WPC warps) per SM.
 template <class Cl>
 KernelInfo rows_info(bool few) {
-  constexpr int smem = 128 + kRowsWPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  const void* fn = few ? reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, Cl::MINB, kFewJobs>)
-                       : reinterpret_cast<const void*>(&k_rows<Cl, kRowsWPC, Cl::MINB, kMaxJobs>);
-  return KernelInfo{fn, smem, kRowsWPC * 32};
+  constexpr int smem = 128 + Cl::WPC * (Cl::WARP_BYTES + Cl::NST * 8);
+  const void* fn = few ? reinterpret_cast<const void*>(&k_rows<Cl, Cl::WPC, Cl::MINB, kFewJobs>)
+                       : reinterpret_cast<const void*>(&k_rows<Cl, Cl::WPC, Cl::MINB, kMaxJobs>);
+  return KernelInfo{fn, smem, Cl::WPC * 32};
 }
 
 // The kernel that runs class `cls` (all jobs of a launch share the class)
@@ -1484,20 +1484,20 @@ std::string check_plan(const ds_plan* pl) {
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);
   switch (pl->fast_class) {
-    case kFcF32_38: return check_rows<RF32_38, kRowsWPC>(jd);
-    case kFcF32_12: return check_rows<RF32_12, kRowsWPC>(jd);
-    case kFcF32_23: return check_rows<RF32_23, kRowsWPC>(jd);
-    case kFcF16_38: return check_rows<RF16_38, kRowsWPC>(jd);
-    case kFcF16_12: return check_rows<RF16_12, kRowsWPC>(jd);
-    case kFcF16_23: return check_rows<RF16_23, kRowsWPC>(jd);
-    case kFcU8C3_38: return check_rows<RU8_38, kRowsWPC>(jd);
-    case kFcU8C3_12: return check_rows<RU8_12, kRowsWPC>(jd);
-    case kFcU8C3_23: return check_rows<RU8_23, kRowsWPC>(jd);
-    case kFcU8C3_CIF: return check_rows<RU8_CIF, kRowsWPC>(jd);
-    case kFcU8C1_CIF: return check_rows<RU8P_CIF, kRowsWPC>(jd);
-    case kFcU8C1_38: return check_rows<RU8P_38, kRowsWPC>(jd);
-    case kFcU8C1_12: return check_rows<RU8P_12, kRowsWPC>(jd);
-    case kFcU8C1_23: return check_rows<RU8P_23, kRowsWPC>(jd);
+    case kFcF32_38: return check_rows<RF32_38, RF32_38::WPC>(jd);
+    case kFcF32_12: return check_rows<RF32_12, RF32_12::WPC>(jd);
+    case kFcF32_23: return check_rows<RF32_23, RF32_23::WPC>(jd);
+    case kFcF16_38: return check_rows<RF16_38, RF16_38::WPC>(jd);
+    case kFcF16_12: return check_rows<RF16_12, RF16_12::WPC>(jd);
+    case kFcF16_23: return check_rows<RF16_23, RF16_23::WPC>(jd);
+    case kFcU8C3_38: return check_rows<RU8_38, RU8_38::WPC>(jd);
+    case kFcU8C3_12: return check_rows<RU8_12, RU8_12::WPC>(jd);
+    case kFcU8C3_23: return check_rows<RU8_23, RU8_23::WPC>(jd);
+    case kFcU8C3_CIF: return check_rows<RU8_CIF, RU8_CIF::WPC>(jd);
+    case kFcU8C1_CIF: return check_rows<RU8P_CIF, RU8P_CIF::WPC>(jd);
+    case kFcU8C1_38: return check_rows<RU8P_38, RU8P_38::WPC>(jd);
+    case kFcU8C1_12: return check_rows<RU8P_12, RU8P_12::WPC>(jd);
+    case kFcU8C1_23: return check_rows<RU8P_23, RU8P_23::WPC>(jd);
     default: return std::string();
   }
 }
