@@ -113,12 +113,12 @@ struct Cls {
   static constexpr int PV = PV_, QV = QV_, KV = KV_;
   static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
   // warps (independent tile pipelines) per CTA, and the resident CTAs per SM
-  // the registers are budgeted for: 4 x 4 warps; the uint8 RGB 1/2 and
-  // one-plane CIF classes fit in the tighter budget of 5, which measures
-  // faster for them; the CIF RGB class, whose stage rings hold a CTA of 4 to
-  // 3 per SM, runs one-warp CTAs (budgeted for 14; 13 fit by shared memory)
-  static constexpr int WPC = (ID == kFcU8C3_CIF) ? 1 : 4;
-  static constexpr int MINB = (ID == kFcU8C3_CIF) ? 14 : ((ID == kFcU8C3_12 || ID == kFcU8C1_CIF) ? 5 : 4);
+  // the registers are budgeted for: 4 x 4 warps by default.  Three uint8
+  // classes run one-warp CTAs, which pack an SM more finely: CIF RGB (its
+  // stage rings would hold 4-warp CTAs to 12 warps per SM; 13 fit), RGB 1/2
+  // (21 warps against 20) and the one-plane CIF class (22 against 20)
+  static constexpr int WPC = (ID == kFcU8C3_CIF || ID == kFcU8C3_12 || ID == kFcU8C1_CIF) ? 1 : 4;
+  static constexpr int MINB = (ID == kFcU8C3_CIF) ? 14 : (ID == kFcU8C3_12 ? 21 : (ID == kFcU8C1_CIF ? 22 : 4));
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
