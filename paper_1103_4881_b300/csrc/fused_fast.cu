@@ -116,9 +116,10 @@ struct Cls {
   // the registers are budgeted for: 4 x 4 warps by default.  Three uint8
   // classes run one-warp CTAs, which pack an SM more finely: CIF RGB (its
   // stage rings would hold 4-warp CTAs to 12 warps per SM; 13 fit), RGB 1/2
-  // (21 warps against 20) and the one-plane CIF class (22 against 20)
+  // (32, the most an SM takes, against 20) and the one-plane CIF class (22
+  // against 20)
   static constexpr int WPC = (ID == kFcU8C3_CIF || ID == kFcU8C3_12 || ID == kFcU8C1_CIF) ? 1 : 4;
-  static constexpr int MINB = (ID == kFcU8C3_CIF) ? 14 : (ID == kFcU8C3_12 ? 21 : (ID == kFcU8C1_CIF ? 22 : 4));
+  static constexpr int MINB = (ID == kFcU8C3_CIF) ? 14 : (ID == kFcU8C3_12 ? 32 : (ID == kFcU8C1_CIF ? 22 : 4));
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
@@ -204,7 +205,7 @@ using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
 using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 2, true>;
 // uint8 RGB (integer row math)
 using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 8, 2, false, 3, 8, 8, 1, true>;
-using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 3, true>;
+using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 2, true>;
 using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false, 2, 3, 6, 1, true>;
 // the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
 //                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV FPW PRO
