@@ -113,19 +113,19 @@ struct Cls {
   static constexpr int PV = PV_, QV = QV_, KV = KV_;
   static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
   // warps (independent tile pipelines) per CTA, and the resident CTAs per SM
-  // the registers are budgeted for.  Most classes run one-warp CTAs, which
-  // pack an SM more finely than 4-warp ones (measured faster or equal):
-  // 12 per SM where the stage rings allow 12 warps (fp32 and one-channel
-  // 3/8), 13 (CIF RGB), 16 (fp16 and RGB 3/8), 22 (one-plane CIF) and 32,
-  // the most an SM takes (RGB 1/2); the rest 4-warp CTAs, 4 per SM
-  static constexpr int WPC = (ID == kFcU8C3_CIF || ID == kFcU8C3_12 || ID == kFcU8C1_CIF || ID == kFcF32_38 ||
-                              ID == kFcF16_38 || ID == kFcU8C3_38 || ID == kFcU8C1_38) ? 1 : 4;
-  static constexpr int MINB = (ID == kFcU8C3_CIF)                      ? 14
+  // the registers are budgeted for.  One-warp CTAs pack an SM more finely
+  // than 4-warp ones, as many as the stage rings and registers allow (32 is
+  // the most an SM takes); they measured faster or equal for every class but
+  // fp32 2/3 and one-channel 2/3, which keep 4-warp CTAs, 4 per SM
+  static constexpr int WPC = (ID == kFcF32_23 || ID == kFcU8C1_23) ? 4 : 1;
+  static constexpr int MINB = (ID == kFcF32_23 || ID == kFcU8C1_23) ? 4
+                              : (ID == kFcU8C3_CIF)                    ? 14
                               : (ID == kFcU8C3_12)                     ? 32
                               : (ID == kFcU8C1_CIF)                    ? 22
                               : (ID == kFcF32_38 || ID == kFcU8C1_38)  ? 12
-                              : (ID == kFcF16_38 || ID == kFcU8C3_38)  ? 16
-                                                                       : 4;
+                              : (ID == kFcF32_12 || ID == kFcU8C1_12)  ? 17
+                              : (ID == kFcF16_23)                      ? 18
+                                                                       : 16;
   static constexpr int SRR = SR_;                   // input rows per stage
   static constexpr int NST = NST_;                  // stages per warp
   static constexpr int SZ = (int)sizeof(T);
