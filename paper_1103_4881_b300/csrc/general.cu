@@ -62,7 +62,7 @@ GenParams make_params(const ds_plan* pl) {
   g.OW = pl->out_w;
   g.wrap = pl->boundary == DS_WRAP ? 1 : 0;
   g.nby = (pl->out_h + pl->pv - 1) / pl->pv;
-  g.tob = std::max(1, 32 / pl->qv);
+  g.tob = std::max(1, 64 / pl->qv);  // about 64 input rows of progress per tile
   g.tox = 32;
   return g;
 }
