@@ -94,8 +94,8 @@ constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_UINT64;
 // A fast-path class: data type, channels, horizontal ratio P/Q and taps K,
 // vertical ratio PV/QV and taps KV (by default those of the horizontal axis),
 // and the tile shape -- NB packets (of Q input pixels) per lane and row, so a
-// warp's strip is 32*NB packets wide; SR input rows per pipeline stage, NST
-// stages per warp;
+// strip is 32*NB packets wide (32/FPW*NB with frame groups); SR input rows per
+// pipeline stage, NST stages per warp;
 // FP: whether interior units run a second, check-free copy of the loop body
 // (faster for some classes, slower where the larger code costs more than the
 // checks, measured per class);
