@@ -38,6 +38,11 @@
  * Errors: functions return DS_OK (0) or a negative ds_status; functions that
  * return a pointer return NULL.  The reason is in ds_last_error() (a
  * thread-local string, valid until the next call on the same thread).
+ *
+ * Environment: DS_LOG=1 logs each plan's choices and every error to stderr
+ * (prefix "[ds] "), DS_LOG=2 also every launch (class, jobs, tiles, grid);
+ * read once per process.  DS_NO_TMA=1 sends new plans to the general
+ * kernels; DS_TUNE_CACHE names the autotuner's cache file (Python side).
  */
 #ifndef DS_H
 #define DS_H

@@ -1552,6 +1552,8 @@ ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, cons
     prm.sched_slot = (int)(slot_counter.fetch_add(1) % kGraphSlot0);
   }
   const int grid = std::min((tiles + per_cta - 1) / per_cta, sm_count() * occ);
+  log_msg(2, "k_rows class %d: %d jobs, %d tiles, grid %d x %d threads, %d B shared, slot %d", cls, nb, tiles, grid,
+          ki.threads, ki.smem, prm.sched_slot);
   void* args[] = {&prm};
   cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, (size_t)ki.smem, st);
   if (e != cudaSuccess) return cuda_fail(e, "k_rows launch");

@@ -179,6 +179,7 @@ ds_status fused_general_t(const ds_plan* pl, const void* in, void* out, int n_fr
   for (int f0 = 0; f0 < n_frames; f0 += kMaxGridZ) {
     const int nf = std::min(kMaxGridZ, n_frames - f0);
     dim3 grid((g.OW + g.tox - 1) / g.tox, (g.nby + g.tob - 1) / g.tob, nf);
+    log_msg(2, "k_fused_general: %d frames, grid %d x %d x %d, %zu B shared", nf, grid.x, grid.y, grid.z, smem);
     k_fused_general<T><<<grid, 256, smem, st>>>((const T*)in, (T*)out, g, f0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_fused_general launch");
@@ -198,6 +199,7 @@ ds_status unfused_t(const ds_plan* pl, const void* in, void* out, int n_frames, 
   for (int f0 = 0; f0 < n_frames; f0 += kMaxGridZ) {
     const int nf = std::min(kMaxGridZ, n_frames - f0);
     dim3 gh((ne + 255) / 256, g.H, nf);
+    log_msg(2, "k_hpass + k_vpass: %d frames", nf);
     k_hpass<T, I><<<gh, 256, 0, st>>>((const T*)in, (I*)ws, g, f0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_hpass launch");

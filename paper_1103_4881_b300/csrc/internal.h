@@ -73,8 +73,12 @@ struct ds_plan {
 
 namespace ds {
 
-// Error reporting (thread-local message).
+// Error reporting (thread-local message).  Errors are also logged at level 1.
 void set_error(const char* fmt, ...);
+// Logging to stderr, prefixed "[ds] ", when the DS_LOG environment variable
+// (read once) is at least `level`: 1 = plans and errors, 2 = every launch too.
+int log_level();
+void log_msg(int level, const char* fmt, ...);
 void clear_error();
 ds_status cuda_fail(cudaError_t e, const char* what);
 

@@ -140,6 +140,24 @@ int default_row_blocks(int fast_class) {
 }
 }  // namespace
 
+int log_level() {
+  static const int level = [] {
+    const char* s = std::getenv("DS_LOG");
+    return s ? std::atoi(s) : 0;
+  }();
+  return level;
+}
+
+void log_msg(int level, const char* fmt, ...) {
+  if (log_level() < level) return;
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::fprintf(stderr, "[ds] %s\n", buf);
+}
+
 void set_error(const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -147,6 +165,7 @@ void set_error(const char* fmt, ...) {
   std::vsnprintf(buf, sizeof(buf), fmt, ap);
   va_end(ap);
   g_last_error = buf;
+  log_msg(1, "error: %s", buf);
 }
 
 void clear_error() { g_last_error.clear(); }
@@ -276,6 +295,10 @@ ds_plan* create_plan(const ds_plan_desc& d, const char* who) {
   if (pl->row_blocks == 0) pl->row_blocks = 8;
   const char* no_tma = std::getenv("DS_NO_TMA");
   pl->force_general = (no_tma && no_tma[0] && no_tma[0] != '0');
+  log_msg(1, "plan %dx%dx%d dtype %d: h %d/%d K%d, v %d/%d K%d, %s%s -> %s (class %d, band %d)", pl->in_h,
+          pl->in_w, pl->channels, (int)pl->dtype, pl->p, pl->q, pl->K, pl->pv, pl->qv, pl->Kv,
+          pl->boundary == DS_WRAP ? "wrap" : "clamp", pl->given_taps ? ", given taps" : "",
+          pl->fast_class >= 0 && !pl->force_general ? "fused_tma" : "fused_general", pl->fast_class, pl->row_blocks);
   return pl;
 }
 
