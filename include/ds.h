@@ -74,7 +74,8 @@ typedef enum {
     DS_ERR_NOMEM = -2,       /* host or device allocation failed              */
     DS_ERR_CUDA = -3,        /* a CUDA runtime/driver call failed             */
     DS_ERR_TIMEOUT = -4,     /* a kernel gave up a bounded wait (device flag) */
-    DS_ERR_UNSUPPORTED = -5  /* valid, but not supported by this build        */
+    DS_ERR_UNSUPPORTED = -5, /* valid, but not supported by this build        */
+    DS_ERR_BOUNDS = -6       /* a bounds check failed (DS_CHECK_BOUNDS build) */
 } ds_status;
 
 /* ---------------------------------------------------------------------- */
@@ -266,10 +267,28 @@ ds_status ds_run_unfused_static(const ds_plan* plan, const void* in, void* out, 
 
 /*
  * Synchronise `stream` and read the device status word that kernels set
- * when a bounded wait gives up; the word is cleared by the read.
- * DS_ERR_TIMEOUT if it was set, DS_ERR_CUDA on an asynchronous CUDA error.
+ * when a bounded wait gives up (or, in a DS_CHECK_BOUNDS build, when one of
+ * the kernel's own bounds checks fails); the word is cleared by the read.
+ * DS_ERR_TIMEOUT or DS_ERR_BOUNDS (what failed, and where, in
+ * ds_last_error()) if it was set, DS_ERR_CUDA on an asynchronous CUDA error.
  */
 ds_status ds_stream_check(void* stream);
+
+/*
+ * 1 if this library was built with DS_CHECK_BOUNDS: the fused kernel then
+ * checks every shared-memory row read, border write, tensor copy and output
+ * row against its buffer, and a failed check skips the access and sets the
+ * device status word (see ds_stream_check).  0 for the normal build.
+ */
+int ds_bounds_checked(void);
+
+/*
+ * Test of the bounds-check report (DS_CHECK_BOUNDS builds): launch on
+ * `stream` one warp that runs the kernels' check on an offset one past a
+ * 64-byte buffer (no access is made), so the next ds_stream_check returns
+ * DS_ERR_BOUNDS.  DS_ERR_UNSUPPORTED in the normal build.
+ */
+ds_status ds_debug_bounds_probe(void* stream);
 
 /*
  * Test of the timeout path: launch on `stream` one warp that waits, with the

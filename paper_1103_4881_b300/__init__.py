@@ -19,12 +19,15 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libds.so")
+# the same library built with DS_CHECK_BOUNDS (the kernel checks its own
+# indices); load it instead with use_library(CHECK_LIB_PATH)
+CHECK_LIB_PATH = os.path.join(_HERE, "libds_check.so")
 
 DS_F32, DS_F16, DS_U8, DS_U8_RGB = 0, 1, 2, 3
 DS_CLAMP, DS_WRAP = 0, 1
-DS_OK, DS_ERR_ARG, DS_ERR_NOMEM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+DS_OK, DS_ERR_ARG, DS_ERR_NOMEM, DS_ERR_CUDA, DS_ERR_TIMEOUT, DS_ERR_UNSUPPORTED, DS_ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6
 _STATUS_NAMES = {0: "DS_OK", -1: "DS_ERR_ARG", -2: "DS_ERR_NOMEM", -3: "DS_ERR_CUDA",
-                 -4: "DS_ERR_TIMEOUT", -5: "DS_ERR_UNSUPPORTED"}
+                 -4: "DS_ERR_TIMEOUT", -5: "DS_ERR_UNSUPPORTED", -6: "DS_ERR_BOUNDS"}
 
 # exported symbols of libds (the declarations in include/ds.h)
 ABI_SYMBOLS = (
@@ -35,6 +38,7 @@ ABI_SYMBOLS = (
     "ds_pipeline_create", "ds_pipeline_run", "ds_pipeline_destroy", "ds_last_error", "ds_version",
     "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static", "ds_plan_autotune",
     "ds_debug_timeout_probe", "ds_plan_create_ex", "ds_plan_get_axes", "ds_plan_get_axis_taps",
+    "ds_bounds_checked", "ds_debug_bounds_probe",
 )
 
 
@@ -102,6 +106,8 @@ def lib() -> ctypes.CDLL:
         "ds_plan_autotune": (i, [vp, vp, vp, i, vp, i, ip, ctypes.POINTER(ctypes.c_float)]),
         "ds_run_unfused_static": (i, [vp, vp, vp, i, vp]),
         "ds_debug_timeout_probe": (i, [ctypes.c_longlong, vp]),
+        "ds_bounds_checked": (i, []),
+        "ds_debug_bounds_probe": (i, [vp]),
         "ds_plan_create_ex": (vp, [ctypes.POINTER(ds_plan_desc)]),
         "ds_plan_get_axes": (i, [vp, ip, ip, ip, ip, ip, ip, ip]),
         "ds_plan_get_axis_taps": (i, [vp, i, vp, vp, vp, vp]),
@@ -243,6 +249,26 @@ def ds_debug_timeout_probe(limit_cycles: int, stream: int = 0) -> None:
     """Launch a warp whose bounded wait runs out after limit_cycles (nothing
     completes its barrier); the next ds_stream_check raises DS_ERR_TIMEOUT."""
     _check(lib().ds_debug_timeout_probe(limit_cycles, _ptr(stream)))
+
+
+def ds_bounds_checked() -> bool:
+    """Whether the loaded library is the DS_CHECK_BOUNDS build."""
+    return bool(lib().ds_bounds_checked())
+
+
+def ds_debug_bounds_probe(stream: int = 0) -> None:
+    """DS_CHECK_BOUNDS builds: run the kernels' bounds check on an index one
+    past a buffer (no access is made); the next ds_stream_check raises
+    DS_ERR_BOUNDS."""
+    _check(lib().ds_debug_bounds_probe(_ptr(stream)))
+
+
+def use_library(path: str) -> None:
+    """Load libds from `path` for the calls that follow (plans made with the
+    previous library must not be used with the new one)."""
+    global _lib, LIB_PATH
+    _lib = None
+    LIB_PATH = path
 
 
 # ---------------------------------------------------------------------- running

@@ -1,6 +1,8 @@
-"""Build libds.so (the CUDA library) in-tree with nvcc for sm_103a.
+"""Build libds.so (the CUDA library) in-tree with nvcc for sm_103a, and
+libds_check.so, the same sources with -DDS_CHECK_BOUNDS (the fused kernel
+checks its own indices and reports a failure instead of making the access).
 
-Usage: python -m paper_1103_4881_b300.build [--force] [--verbose]
+Usage: python -m paper_1103_4881_b300.build [--force] [--verbose] [--check]
 """
 from __future__ import annotations
 
@@ -14,6 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libds.so")
+CHECK_LIB = os.path.join(HERE, "libds_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -26,10 +29,10 @@ def _inputs():
         [os.path.join(INCLUDE, "ds.h"), os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
@@ -40,13 +43,17 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every source under csrc/ into paper_1103_4881_b300/libds.so."""
-    if not force and up_to_date():
-        return LIB
-    objdir = os.path.join(HERE, "_build")
+def build(force: bool = False, verbose: bool = False, check_bounds: bool = False) -> str:
+    """Compile every source under csrc/ into paper_1103_4881_b300/libds.so
+    (check_bounds: libds_check.so, with -DDS_CHECK_BOUNDS)."""
+    lib = CHECK_LIB if check_bounds else LIB
+    if not force and up_to_date(lib):
+        return lib
+    objdir = os.path.join(HERE, "_build_check" if check_bounds else "_build")
     os.makedirs(objdir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC] + ARCH
+    if check_bounds:
+        common += ["-DDS_CHECK_BOUNDS"]
     if verbose:
         common += ["-Xptxas", "-v"]
     objs = []
@@ -65,12 +72,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
         failed |= p.returncode != 0
     if failed:
         raise RuntimeError("nvcc failed building libds")
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     subprocess.check_call([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="--verbose" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv, check_bounds="--check" in sys.argv))

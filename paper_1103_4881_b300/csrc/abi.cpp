@@ -147,13 +147,31 @@ ds_status ds_stream_check(void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "ds_stream_check");
   int status = 0;
-  ds_status s = read_device_status(&status);
+  long long info[2];
+  ds_status s = read_device_status(&status, info);
   if (s != DS_OK) return s;
+  if (status == 3) {
+    static const char* kinds[] = {"", "shared-memory row read", "border write", "output row", "tensor copy"};
+    set_error("a bounds check failed: %s at offset %lld", info[0] >= 1 && info[0] <= 4 ? kinds[info[0]] : "probe",
+              info[1]);
+    return DS_ERR_BOUNDS;
+  }
   if (status != 0) {
     set_error("a kernel gave up a bounded wait (device status %d)", status);
     return DS_ERR_TIMEOUT;
   }
   return DS_OK;
+}
+
+int ds_bounds_checked(void) { return bounds_checked() ? 1 : 0; }
+
+ds_status ds_debug_bounds_probe(void* stream) {
+  clear_error();
+  if (!bounds_checked()) {
+    set_error("ds_debug_bounds_probe: this library was built without DS_CHECK_BOUNDS");
+    return DS_ERR_UNSUPPORTED;
+  }
+  return launch_bounds_probe((cudaStream_t)stream);
 }
 
 ds_status ds_debug_timeout_probe(long long limit_cycles, void* stream) {

@@ -50,7 +50,24 @@
 
 namespace ds {
 
-__device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out; 2 = bad class
+__device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out or bad class; 3 = bounds check
+// Bounds-checking builds (-DDS_CHECK_BOUNDS): the kernel checks its own shared
+// memory row reads, border writes, TMA copies and output rows against their
+// buffers, and a failed check records what failed (kind, offset) and skips
+// the access instead of making it.
+#ifdef DS_CHECK_BOUNDS
+constexpr bool kCheckBounds = true;
+#else
+constexpr bool kCheckBounds = false;
+#endif
+constexpr int kStatusBounds = 3;
+__device__ long long g_bounds_info[2];  // kind (1 row read, 2 border write, 3 output row, 4 copy), offset
+__device__ __forceinline__ void bounds_fail(int kind, long long offset) {
+  if (atomicCAS(&g_fast_status, 0, kStatusBounds) == 0) {
+    g_bounds_info[0] = kind;
+    g_bounds_info[1] = offset;
+  }
+}
 
 // Dynamic tile scheduling of the row-streaming kernel: launch slot s hands out
 // tiles from g_tile_next[s]; the last warp to finish puts both counters of
@@ -430,9 +447,17 @@ __device__ __forceinline__ void apply_edge_fix(uint8_t* stagebase, const EdgeFix
     const int src = sub * Cl::FSTR + win_off<Cl>(((left ? 0 : W - 1) * Cl::C + c - xw) * Cl::SZ);
     const int dst = sub * Cl::FSTR + win_off<Cl>((px * Cl::C + c - xw) * Cl::SZ);
 #pragma unroll
-    for (int r = 0; r < Cl::SRR; ++r)
+    for (int r = 0; r < Cl::SRR; ++r) {
+      if constexpr (kCheckBounds) {  // both elements inside this stage
+        const int lo = r * Cl::BOXB + (src < dst ? src : dst), hi = r * Cl::BOXB + (src > dst ? src : dst);
+        if (lo < 0 || hi + Cl::SZ > Cl::RSTAGE) {
+          bounds_fail(2, lo < 0 ? lo : hi);
+          continue;
+        }
+      }
       *reinterpret_cast<T*>(stagebase + r * Cl::BOXB + dst) =
           *reinterpret_cast<const T*>(stagebase + r * Cl::BOXB + src);
+    }
   }
   // these generic-proxy writes must land before the TMA refills the stage
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -872,6 +897,13 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
 
     auto issue = [&](int s) {  // stage s of the tile into slot (g + s) mod NST
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
+      if constexpr (kCheckBounds) {  // frames of the job, window start on 16 bytes
+        if (frame0 < 0 || frame0 + nf > jd.nframes || (xt * kTmaElem) % 16 != 0) {
+          bounds_fail(4, (long long)xt * kTmaElem);
+          mbar_expect_tx(&full[slot], 0u);  // completes the phase with no copy
+          return;
+        }
+      }
       mbar_expect_tx(&full[slot], (uint32_t)(nf * Cl::RTX));
       for (int f = 0; f < nf; ++f)
 #pragma unroll
@@ -902,7 +934,37 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       }
     };
     // H pass of one loaded row into a window row
+    // every vector a lane reads of a row lies in the warp's ring
+    auto row_ok = [&](const uint8_t* rowbase) -> bool {
+      if constexpr (kCheckBounds) {
+#pragma unroll
+        for (int v = 0; v < Cl::NVT; ++v) {
+          const long long off = (long long)(rowbase - ring) + of.v[v];
+          if (off < 0 || off + Cl::VB > Cl::WARP_BYTES) {
+            bounds_fail(1, off);
+            return false;
+          }
+        }
+      }
+      return true;
+    };
+    // the output rows of block rr this lane stores lie in its frame
+    auto store_ok = [&](int rr) -> bool {
+      if constexpr (kCheckBounds) {
+        if (n_valid > 0) {
+          const long long first = (long long)blk0 * Cl::P * Cl::C + (long long)rr * P * rowe;
+          const int last_row = min(rr * P + P, jd.OH) - 1 - rr * P;
+          const long long last = first + (long long)last_row * rowe + min(n_valid, Cl::NOUT) - 1;
+          if (first < 0 || last >= jd.out_frame || frame0 + sub >= jd.nframes) {
+            bounds_fail(3, first < 0 ? first : last);
+            return false;
+          }
+        }
+      }
+      return true;
+    };
     auto hrow_regs = [&](uint8_t* rowbase, Row& o) {
+      if (!row_ok(rowbase)) return;
       uint32_t w[Cl::NWT];
       load_row<Cl>(rowbase, of, w);
       RM::h(w, prm, o);
@@ -969,7 +1031,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
             const int i = L - Q + q;
             if constexpr (FAST) {
               uint32_t w[Cl::NWT];
-              load_row<Cl>(sb + r * Cl::BOXB, of, w);
+              if (row_ok(sb + r * Cl::BOXB)) load_row<Cl>(sb + r * Cl::BOXB, of, w);
               RM::h(w, prm, win[i]);
             } else {
               // rows below the frame's last repeat it (filtered from the zero
@@ -980,9 +1042,11 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
             }
             if (q == Q - 1) {
               // the window holds block m's pattern: its P output rows
-              if constexpr (FAST) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
-              else if (!Cl::PRO || m >= 0)
-                RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+              if constexpr (FAST) {
+                if (store_ok(rb0 + m)) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+              } else if (!Cl::PRO || m >= 0) {
+                if (store_ok(rb0 + m)) RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+              }
 #pragma unroll
               for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
               if constexpr (!FAST && Cl::PRO)
@@ -1042,6 +1106,16 @@ __global__ void k_timeout_probe(long long limit) {
   __syncwarp();
   const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar, 0u, limit));
   if (!ok && threadIdx.x == 0) atomicCAS(&g_fast_status, 0, kStatusTimeout);
+}
+
+// Exercise of the bounds-check report (bounds-checking builds): one thread
+// runs the kernels' check on an offset one past a 64-byte buffer, which
+// fails; the access itself is never made.
+__global__ void k_bounds_probe() {
+  if (threadIdx.x == 0) {
+    const long long off = 64, size = 64;
+    if (off + 1 > size) bounds_fail(9, off);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1621,15 +1695,30 @@ ds_status launch_timeout_probe(long long limit_cycles, cudaStream_t st) {
   return DS_OK;
 }
 
+bool bounds_checked() { return kCheckBounds; }
+
+ds_status launch_bounds_probe(cudaStream_t st) {
+  k_bounds_probe<<<1, 32, 0, st>>>();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "bounds probe launch");
+  count_launches(1);
+  return DS_OK;
+}
+
 ds_status debug_check_plan(const ds_plan* pl, std::string& msg) {
   msg = check_plan(pl);
   return msg.empty() ? DS_OK : DS_ERR_ARG;
 }
 
-ds_status read_device_status(int* status) {
+ds_status read_device_status(int* status, long long* info) {
   int v = 0, zero = 0;
   cudaError_t e = cudaMemcpyFromSymbol(&v, g_fast_status, sizeof(int));
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+  info[0] = info[1] = 0;
+  if (v == kStatusBounds) {
+    e = cudaMemcpyFromSymbol(info, g_bounds_info, 2 * sizeof(long long));
+    if (e != cudaSuccess) return cuda_fail(e, "reading the bounds-check record");
+  }
   if (v != 0) {
     e = cudaMemcpyToSymbol(g_fast_status, &zero, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");

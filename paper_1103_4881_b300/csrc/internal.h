@@ -104,8 +104,12 @@ ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t stream);
 extern thread_local std::vector<int>* g_capture_slots;
 void release_graph_slots(const std::vector<int>& slots);
 int fast_max_jobs_per_launch();
-ds_status read_device_status(int* status);  // reads and clears the status word
+// reads and clears the status word (1: a wait gave up, 3: a bounds check
+// failed, with kind and offset in info)
+ds_status read_device_status(int* status, long long* info);
 ds_status launch_timeout_probe(long long limit_cycles, cudaStream_t stream);
+bool bounds_checked();  // built with -DDS_CHECK_BOUNDS
+ds_status launch_bounds_probe(cudaStream_t stream);
 ds_status debug_check_plan(const ds_plan* plan, std::string& msg);
 
 // general.cu: any plan, any alignment.

@@ -159,3 +159,12 @@ def test_fast_kernel_host_check_on_random_shapes():
         finally:
             ds.ds_destroy(pl)
     assert checked > 60
+
+
+def test_normal_build_is_not_bounds_checked():
+    """The normal library has no index checks; its bounds probe is refused
+    before any launch (so this runs without a GPU)."""
+    assert not ds.ds_bounds_checked()
+    with pytest.raises(ds.DsError) as e:
+        ds.ds_debug_bounds_probe(0)
+    assert e.value.status == ds.DS_ERR_UNSUPPORTED

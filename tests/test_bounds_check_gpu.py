@@ -1,0 +1,87 @@
+"""The bounds-checking build (libds_check.so, -DDS_CHECK_BOUNDS): every fast
+class, on ragged and tiny frames, in single and batched launches, runs with
+all of the kernel's own index checks passing (ds_stream_check would raise
+DS_ERR_BOUNDS otherwise) and gives the oracle's results; the check's report
+path works (a probe that checks an index one past a buffer, with no
+access)."""
+import numpy as np
+import pytest
+
+import paper_1103_4881_b300 as ds
+from tests.gpu_util import assert_parity, finish, frames, out_buffer, run_fused, stream, to_dev
+
+pytestmark = pytest.mark.gpu
+
+FAST_AXES = [((3, 8), 8, (3, 8), 8), ((1, 2), 6, (1, 2), 6), ((2, 3), 6, (2, 3), 6), ((3, 8), 8, (4, 9), 8)]
+SHAPES = [(72, 528), (9, 16), (41, 272), (3, 48), (200, 784)]
+
+
+@pytest.fixture(scope="module")
+def checked():
+    from paper_1103_4881_b300 import build
+
+    build.build(check_bounds=True)
+    previous = ds.LIB_PATH
+    ds.use_library(ds.CHECK_LIB_PATH)
+    assert ds.ds_bounds_checked()
+    yield
+    ds.use_library(previous)
+
+
+def _oracle(oracle, x, rh, Kh, rv, Kv, dt):
+    xo = x if dt in (ds.DS_U8, ds.DS_U8_RGB) else x.astype(np.float64)
+    return oracle.filter_ex(xo, rh, Kh, rv, Kv)
+
+
+@pytest.mark.parametrize("dt", [ds.DS_F32, ds.DS_F16, ds.DS_U8_RGB, ds.DS_U8])
+@pytest.mark.parametrize("rh,Kh,rv,Kv", FAST_AXES)
+@pytest.mark.parametrize("H,W", SHAPES)
+def test_checked_build_every_class(checked, oracle, H, W, rh, Kh, rv, Kv, dt):
+    try:
+        pl = ds.ds_plan_create_ex(H, W, rh, Kh, rv, Kv, dt)
+    except ds.DsError:
+        pytest.skip("empty output")
+    try:
+        x = frames((H, W), dt, 3, H * 31 + W)
+        got = run_fused(pl, x)  # ds_stream_check inside: raises on a failed bounds check
+        assert_parity(got, _oracle(oracle, x, rh, Kh, rv, Kv, dt), dt, ds.ds_plan_describe(pl))
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_checked_build_large_batch_with_tail_split(checked, oracle):
+    """Enough frames that the launch's last tiles run in shorter bands, the job
+    split in two, plus the CIF planes of odd counts in one launch."""
+    pl = ds.ds_plan_create(270, 480, (3, 8), 8, ds.DS_F32)
+    py = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    pc = ds.ds_plan_create_ex(144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        x = frames((270, 480), ds.DS_F32, 97, 5)
+        got = run_fused(pl, x)
+        assert_parity(got, oracle.filter_ex(x.astype(np.float64), (3, 8), 8, (3, 8), 8), ds.DS_F32)
+        counts = (5, 3, 3)
+        xs = [frames((288, 352), ds.DS_U8, 5, 6), frames((144, 176), ds.DS_U8, 3, 7), frames((144, 176), ds.DS_U8, 3, 8)]
+        ins = [to_dev(a) for a in xs]
+        outs = [out_buffer(py, 5), out_buffer(pc, 3), out_buffer(pc, 3)]
+        ds.ds_batch_run([(p, i.data_ptr(), o.data_ptr(), n) for p, i, o, n in zip((py, pc, pc), ins, outs, counts)],
+                        stream())
+        finish()
+        for o, a in zip(outs, xs):
+            assert_parity(o.cpu().numpy(), oracle.filter_ex(a, (3, 8), 8, (4, 9), 8), ds.DS_U8)
+    finally:
+        for p in (pl, py, pc):
+            ds.ds_destroy(p)
+
+
+def test_bounds_probe_is_reported_and_the_context_stays_usable(checked, oracle):
+    ds.ds_debug_bounds_probe(stream())
+    with pytest.raises(ds.DsError) as e:
+        ds.ds_stream_check(stream())
+    assert e.value.status == ds.DS_ERR_BOUNDS
+    ds.ds_stream_check(stream())  # the read cleared the word
+    pl = ds.ds_plan_create(72, 528, (1, 2), 6, ds.DS_U8_RGB)
+    try:
+        x = frames((72, 528), ds.DS_U8_RGB, 2, 9)
+        assert_parity(run_fused(pl, x), oracle.filter_u8(x, 1, 2, 6), ds.DS_U8_RGB)
+    finally:
+        ds.ds_destroy(pl)
