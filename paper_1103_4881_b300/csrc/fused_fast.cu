@@ -845,6 +845,12 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* const ring = smem + warp * Cl::WARP_BYTES;
   uint64_t* const full = reinterpret_cast<uint64_t*>(smem + WPC * Cl::WARP_BYTES) + warp * NST;
+  if constexpr (kCheckBounds) {
+    // poison the ring (all-ones bytes: NaN for float data) so that a read of
+    // staging memory before its copy lands shows up in the results
+    for (int i = lane; i < Cl::WARP_BYTES / 4; i += 32) reinterpret_cast<uint32_t*>(ring)[i] = 0xffffffffu;
+    __syncwarp();
+  }
   if (lane == 0) {
     for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
