@@ -51,3 +51,23 @@ def test_random_plans_match_the_oracle(oracle, H, W, rh, Kh, rv, Kv, dt, wrap):
         np.testing.assert_array_equal(run_unfused(pl, x), got)
     finally:
         ds.ds_destroy(pl)
+
+
+EXTREME = [((1, 64), 2), ((1, 64), 16), ((16, 17), 16), ((15, 64), 16), ((16, 33), 2), ((1, 2), 16), ((16, 63), 16)]
+
+
+@pytest.mark.parametrize("ratio,K", EXTREME)
+@pytest.mark.parametrize("dt", [ds.DS_F32, ds.DS_U8_RGB])
+def test_extreme_ratios_and_tap_counts(oracle, ratio, K, dt):
+    """The ends of the supported range (q up to 64, p up to 16, K from 2 to
+    16) on ragged frames, both axes, through the general kernels."""
+    H, W = 131, 197
+    pl = ds.ds_plan_create_ex(H, W, ratio, K, ratio, K, dt)
+    try:
+        x = frames((H, W), dt, 2, ratio[0] * 100 + ratio[1] + K)
+        got = run_fused(pl, x)
+        xo = x if dt == ds.DS_U8_RGB else x.astype(np.float64)
+        assert_parity(got, oracle.filter_ex(xo, ratio, K, ratio, K), dt, ds.ds_plan_describe(pl))
+        np.testing.assert_array_equal(run_unfused(pl, x), got)
+    finally:
+        ds.ds_destroy(pl)
