@@ -239,6 +239,34 @@ using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 8, 2, false, 3, 8, 8, 1,
 using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, false>;
 using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, true>;
 
+// The class of an id, as a type tag: f(ClassTag<RXX>{}) for class `cls`
+// (the one place that lists them; every per-class host function goes
+// through it).  Ids without a class map to the last one's tag only to keep
+// one return type: callers check fast_class >= 0 first.
+template <class Cl_>
+struct ClassTag {
+  using type = Cl_;
+};
+template <class F>
+auto with_class(int cls, F&& f) {
+  switch (cls) {
+    case kFcF32_38: return f(ClassTag<RF32_38>{});
+    case kFcF32_12: return f(ClassTag<RF32_12>{});
+    case kFcF32_23: return f(ClassTag<RF32_23>{});
+    case kFcF16_38: return f(ClassTag<RF16_38>{});
+    case kFcF16_12: return f(ClassTag<RF16_12>{});
+    case kFcF16_23: return f(ClassTag<RF16_23>{});
+    case kFcU8C3_38: return f(ClassTag<RU8_38>{});
+    case kFcU8C3_12: return f(ClassTag<RU8_12>{});
+    case kFcU8C3_23: return f(ClassTag<RU8_23>{});
+    case kFcU8C3_CIF: return f(ClassTag<RU8_CIF>{});
+    case kFcU8C1_CIF: return f(ClassTag<RU8P_CIF>{});
+    case kFcU8C1_38: return f(ClassTag<RU8P_38>{});
+    case kFcU8C1_12: return f(ClassTag<RU8P_12>{});
+    default: return f(ClassTag<RU8P_23>{});
+  }
+}
+
 // ---------------------------------------------------------------------------
 // launch parameters
 // ---------------------------------------------------------------------------
@@ -1139,22 +1167,7 @@ HostGeom host_geom() {
 
 // Geometry of the kernel that runs class `cls`.
 HostGeom geom_of(int cls) {
-  switch (cls) {
-    case kFcF32_38: return host_geom<RF32_38>();
-    case kFcF32_12: return host_geom<RF32_12>();
-    case kFcF32_23: return host_geom<RF32_23>();
-    case kFcF16_38: return host_geom<RF16_38>();
-    case kFcF16_12: return host_geom<RF16_12>();
-    case kFcF16_23: return host_geom<RF16_23>();
-    case kFcU8C3_38: return host_geom<RU8_38>();
-    case kFcU8C3_12: return host_geom<RU8_12>();
-    case kFcU8C3_CIF: return host_geom<RU8_CIF>();
-    case kFcU8C1_CIF: return host_geom<RU8P_CIF>();
-    case kFcU8C1_38: return host_geom<RU8P_38>();
-    case kFcU8C1_12: return host_geom<RU8P_12>();
-    case kFcU8C1_23: return host_geom<RU8P_23>();
-    default: return host_geom<RU8_23>();
-  }
+  return with_class(cls, [](auto tag) { return host_geom<typename decltype(tag)::type>(); });
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1188,22 +1201,7 @@ KernelInfo rows_info(bool few) {
 // The kernel that runs class `cls` (all jobs of a launch share the class)
 // with room for kFewJobs (few) or kMaxJobs job descriptors.
 KernelInfo kernel_for(int cls, bool few) {
-  switch (cls) {
-    case kFcF32_38: return rows_info<RF32_38>(few);
-    case kFcF32_12: return rows_info<RF32_12>(few);
-    case kFcF32_23: return rows_info<RF32_23>(few);
-    case kFcF16_38: return rows_info<RF16_38>(few);
-    case kFcF16_12: return rows_info<RF16_12>(few);
-    case kFcF16_23: return rows_info<RF16_23>(few);
-    case kFcU8C3_38: return rows_info<RU8_38>(few);
-    case kFcU8C3_12: return rows_info<RU8_12>(few);
-    case kFcU8C3_CIF: return rows_info<RU8_CIF>(few);
-    case kFcU8C1_CIF: return rows_info<RU8P_CIF>(few);
-    case kFcU8C1_38: return rows_info<RU8P_38>(few);
-    case kFcU8C1_12: return rows_info<RU8P_12>(few);
-    case kFcU8C1_23: return rows_info<RU8P_23>(few);
-    default: return rows_info<RU8_23>(few);
-  }
+  return with_class(cls, [few](auto tag) { return rows_info<typename decltype(tag)::type>(few); });
 }
 
 // Occupancy per kernel, computed once per process (one device).
@@ -1567,26 +1565,14 @@ std::string check_rows(const JobDesc& jd) {
 }
 
 std::string check_plan(const ds_plan* pl) {
+  if (pl->fast_class < 0 || pl->fast_class >= kFcCount) return std::string();
   JobDesc jd;
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);
-  switch (pl->fast_class) {
-    case kFcF32_38: return check_rows<RF32_38, RF32_38::WPC>(jd);
-    case kFcF32_12: return check_rows<RF32_12, RF32_12::WPC>(jd);
-    case kFcF32_23: return check_rows<RF32_23, RF32_23::WPC>(jd);
-    case kFcF16_38: return check_rows<RF16_38, RF16_38::WPC>(jd);
-    case kFcF16_12: return check_rows<RF16_12, RF16_12::WPC>(jd);
-    case kFcF16_23: return check_rows<RF16_23, RF16_23::WPC>(jd);
-    case kFcU8C3_38: return check_rows<RU8_38, RU8_38::WPC>(jd);
-    case kFcU8C3_12: return check_rows<RU8_12, RU8_12::WPC>(jd);
-    case kFcU8C3_23: return check_rows<RU8_23, RU8_23::WPC>(jd);
-    case kFcU8C3_CIF: return check_rows<RU8_CIF, RU8_CIF::WPC>(jd);
-    case kFcU8C1_CIF: return check_rows<RU8P_CIF, RU8P_CIF::WPC>(jd);
-    case kFcU8C1_38: return check_rows<RU8P_38, RU8P_38::WPC>(jd);
-    case kFcU8C1_12: return check_rows<RU8P_12, RU8P_12::WPC>(jd);
-    case kFcU8C1_23: return check_rows<RU8P_23, RU8P_23::WPC>(jd);
-    default: return std::string();
-  }
+  return with_class(pl->fast_class, [&jd](auto tag) {
+    using Cl = typename decltype(tag)::type;
+    return check_rows<Cl, Cl::WPC>(jd);
+  });
 }
 
 // Scheduling slots owned by live graphs.
