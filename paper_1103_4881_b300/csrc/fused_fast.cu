@@ -1241,8 +1241,21 @@ void pair_taps(const short* q14, int p, int K, uint32_t (*out)[kMaxPhases][kMaxP
       }
 }
 
-// The taps of fast class `cls`.  They depend only on its axes: built once
-// for every class with a throwaway plan.
+// The launch tap tables of a plan with a fast class: FP32 taps (or Q14 taps
+// as floats) per axis, and the int16 pairs of the Q14 taps for dp2a.
+void plan_taps(const ds_plan* pl, ClassTaps& t) {
+  std::memset(&t, 0, sizeof(t));
+  const bool u8 = pl->dtype == DS_U8 || pl->dtype == DS_U8_RGB;
+  for (int i = 0; i < pl->p * pl->K; ++i) t.taps[i] = u8 ? (float)pl->q14[i] : pl->w32[i];
+  for (int i = 0; i < pl->pv * pl->Kv; ++i) t.tapsv[i] = u8 ? (float)pl->q14v[i] : pl->w32v[i];
+  if (u8) {
+    pair_taps(pl->q14, pl->p, pl->K, t.tap2h);
+    pair_taps(pl->q14v, pl->pv, pl->Kv, t.tap2v);
+  }
+}
+
+// The taps of fast class `cls` with the library's own taps.  They depend only
+// on its axes: built once for every class with a throwaway plan.
 const ClassTaps& class_taps(int cls) {
   static ClassTaps all[kFcCount];
   static std::once_flag once;
@@ -1274,14 +1287,7 @@ const ClassTaps& class_taps(int cls) {
         ds_destroy(pl);
         continue;
       }
-      ClassTaps& t = all[pl->fast_class];
-      const bool u8 = a.dt == DS_U8 || a.dt == DS_U8_RGB;
-      for (int i = 0; i < pl->p * pl->K; ++i) t.taps[i] = u8 ? (float)pl->q14[i] : pl->w32[i];
-      for (int i = 0; i < pl->pv * pl->Kv; ++i) t.tapsv[i] = u8 ? (float)pl->q14v[i] : pl->w32v[i];
-      if (u8) {
-        pair_taps(pl->q14, pl->p, pl->K, t.tap2h);
-        pair_taps(pl->q14v, pl->pv, pl->Kv, t.tap2v);
-      }
+      plan_taps(pl, all[pl->fast_class]);
       ds_destroy(pl);
     }
   });
@@ -1591,10 +1597,10 @@ int take_graph_slot() {
 
 // Fill the launch parameters and launch.
 template <int MAXJ>
-ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, const BandedJob* banded, int nb,
-                      int occ, cudaStream_t st) {
+ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, const ClassTaps& taps,
+                      const BandedJob* banded, int nb, int occ, cudaStream_t st) {
   const int per_cta = ki.threads / 32;  // one tile per warp
-  prm.t = class_taps(cls);
+  prm.t = taps;
   int tiles = 0;
   for (int i = 0; i < nb; ++i) {
     ds_status s = encode_job(prm.jobs[i], banded[i].job, banded[i].band);
@@ -1628,7 +1634,12 @@ ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, cons
 }
 
 ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
-  const int cls = jobs[0].plan->fast_class;  // launch_fast groups jobs by class
+  // launch_fast groups jobs by class and tap table: a plan with given taps
+  // launches with its own tables, every other plan with its class's
+  const int cls = jobs[0].plan->fast_class;
+  static thread_local ClassTaps given;
+  if (jobs[0].plan->given_taps) plan_taps(jobs[0].plan, given);
+  const ClassTaps& taps = jobs[0].plan->given_taps ? given : class_taps(cls);
   int want_ctas = jobs[0].plan->ctas_per_sm;
   for (int i = 0; i < n; ++i) want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
   // both instantiations of a class have the same shape and occupancy
@@ -1645,10 +1656,10 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
     static thread_local FastParams<kFewJobs> few;
     const KernelInfo ki = kernel_for(cls, true);
     if (ctas_per_sm(ki) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
-    return launch_with(few, ki, cls, banded, nb, occ, st);
+    return launch_with(few, ki, cls, taps, banded, nb, occ, st);
   }
   static thread_local FastParams<kMaxJobs> many;  // ~17 KB: not on the caller's stack
-  return launch_with(many, big, cls, banded, nb, occ, st);
+  return launch_with(many, big, cls, taps, banded, nb, occ, st);
 }
 
 }  // namespace
@@ -1666,15 +1677,33 @@ void release_graph_slots(const std::vector<int>& slots) {
 // One launch per class present (each kernel is specialised for its class),
 // at most kMaxJobs descriptors per launch.
 ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
+  // one group per class for the plans with the library's taps, one per plan
+  // with given taps (its own tap tables)
   std::vector<FastJob> group;
-  for (int cls = 0; cls < kFcCount; ++cls) {
-    group.clear();
-    for (int i = 0; i < n; ++i)
-      if (jobs[i].plan->fast_class == cls) group.push_back(jobs[i]);
+  auto launch_group = [&]() -> ds_status {
     for (size_t i = 0; i < group.size(); i += kMaxJobs) {
       ds_status s = launch_chunk(group.data() + i, (int)std::min<size_t>(kMaxJobs, group.size() - i), st);
       if (s != DS_OK) return s;
     }
+    return DS_OK;
+  };
+  for (int cls = 0; cls < kFcCount; ++cls) {
+    group.clear();
+    for (int i = 0; i < n; ++i)
+      if (jobs[i].plan->fast_class == cls && !jobs[i].plan->given_taps) group.push_back(jobs[i]);
+    ds_status s = launch_group();
+    if (s != DS_OK) return s;
+  }
+  std::vector<const ds_plan*> done;
+  for (int i = 0; i < n; ++i) {
+    const ds_plan* pl = jobs[i].plan;
+    if (!pl->given_taps || std::find(done.begin(), done.end(), pl) != done.end()) continue;
+    done.push_back(pl);
+    group.clear();
+    for (int k = i; k < n; ++k)
+      if (jobs[k].plan == pl) group.push_back(jobs[k]);
+    ds_status s = launch_group();
+    if (s != DS_OK) return s;
   }
   return DS_OK;
 }

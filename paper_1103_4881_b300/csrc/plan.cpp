@@ -288,8 +288,9 @@ ds_plan* create_plan(const ds_plan_desc& d, const char* who) {
     delete pl;
     return nullptr;
   }
-  // the fast kernels take clamp-to-edge and the library's own taps
-  pl->fast_class = (d.boundary == DS_CLAMP && !pl->given_taps)
+  // the fast kernels take clamp-to-edge (a plan's given taps travel with its
+  // launch)
+  pl->fast_class = (d.boundary == DS_CLAMP)
                        ? fast_class_of(pl->p, pl->q, pl->K, pl->pv, pl->qv, pl->Kv, d.dtype) : kFcNone;
   pl->row_blocks = default_row_blocks(pl->fast_class);
   if (pl->row_blocks == 0) pl->row_blocks = 8;

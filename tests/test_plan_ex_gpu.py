@@ -171,3 +171,69 @@ def test_cif_classes_on_tiny_and_ragged_frames(oracle, dt, H, W, n):
                       "cif %dx%d n=%d dt=%d" % (H, W, n, dt))
     finally:
         ds.ds_destroy(pl)
+
+
+GIVEN_FAST = [
+    # (H, W, rh, Kh, rv, Kv, dtype): fast classes with caller-given taps
+    (72, 528, (3, 8), 8, (3, 8), 8, ds.DS_F32),
+    (64, 256, (1, 2), 6, (1, 2), 6, ds.DS_U8_RGB),
+    (41, 272, (2, 3), 6, (2, 3), 6, ds.DS_F16),
+    (288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8_RGB),
+    (144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8),
+    (9, 16, (3, 8), 8, (3, 8), 8, ds.DS_U8),
+]
+
+
+def _given(rh, Kh, rv, Kv, seed):
+    rng = np.random.default_rng(seed)
+    wh, wv = rng.normal(0, 0.3, (rh[0], Kh)), rng.normal(0, 0.3, (rv[0], Kv))
+    wh[:, Kh // 2] += 1.0  # a dominant centre tap, like a smoothing filter
+    wv[:, Kv // 2] += 1.0
+    return wh, wv
+
+
+@pytest.mark.parametrize("H,W,rh,Kh,rv,Kv,dt", GIVEN_FAST)
+def test_given_taps_on_the_fast_kernel(oracle, H, W, rh, Kh, rv, Kv, dt):
+    wh, wv = _given(rh, Kh, rv, Kv, H + W)
+    pl = ds.ds_plan_create_ex(H, W, rh, Kh, rv, Kv, dt, ds.DS_CLAMP, wh, wv)
+    try:
+        assert '"fused_tma"' in ds.ds_plan_describe(pl)
+        x = frames((H, W), dt, 3, H * 13 + W)
+        got = run_fused(pl, x)
+        assert_parity(got, _oracle(oracle, x, rh, Kh, rv, Kv, dt, ds.DS_CLAMP, wh, wv), dt,
+                      "given taps %dx%d %s/%s dt=%d" % (H, W, rh, rv, dt))
+        np.testing.assert_array_equal(run_unfused(pl, x), got)
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_batch_mixes_given_and_library_taps_of_one_class(oracle):
+    """Plans of one class with different tap tables in one ds_batch_run and in
+    one graph: each launch group carries its own tables."""
+    from tests.gpu_util import finish, out_buffer, stream, to_dev
+    wa, wb = _given((3, 8), 8, (3, 8), 8, 1), _given((3, 8), 8, (3, 8), 8, 2)
+    plans = [ds.ds_plan_create(96, 528, (3, 8), 8, ds.DS_U8_RGB),
+             ds.ds_plan_create_ex(96, 528, (3, 8), 8, (3, 8), 8, ds.DS_U8_RGB, ds.DS_CLAMP, *wa),
+             ds.ds_plan_create_ex(96, 528, (3, 8), 8, (3, 8), 8, ds.DS_U8_RGB, ds.DS_CLAMP, *wb),
+             ds.ds_plan_create(96, 528, (3, 8), 8, ds.DS_U8_RGB)]
+    weights = [(None, None), wa, wb, (None, None)]
+    try:
+        xs = [frames((96, 528), ds.DS_U8_RGB, 2, 60 + k) for k in range(4)]
+        ins = [to_dev(a) for a in xs]
+        for use_graph in (False, True):
+            outs = [out_buffer(pl, 2) for pl in plans]
+            jobs = [(pl, i.data_ptr(), o.data_ptr(), 2) for pl, i, o in zip(plans, ins, outs)]
+            if use_graph:
+                g = ds.ds_graph_create(jobs)
+                ds.ds_graph_launch(g, stream())
+                finish()
+                ds.ds_graph_destroy(g)
+            else:
+                ds.ds_batch_run(jobs, stream())
+                finish()
+            for o, a, (wh, wv) in zip(outs, xs, weights):
+                want = oracle.filter_ex(a, (3, 8), 8, (3, 8), 8, weights_h=wh, weights_v=wv)
+                assert_parity(o.cpu().numpy(), want, ds.DS_U8_RGB, "graph=%s" % use_graph)
+    finally:
+        for pl in plans:
+            ds.ds_destroy(pl)

@@ -68,10 +68,13 @@ def test_equal_axes_keep_the_fast_kernel():
         assert '"fused_tma"' in ds.ds_plan_describe(pl)
     finally:
         ds.ds_destroy(pl)
-    for kw in (dict(boundary=ds.DS_WRAP), dict(weights_h=None, weights_v=np.eye(3, 8))):
+    # modular tilers take the general kernels; given taps (clamp) keep the
+    # fast kernel, which launches with the plan's own tap tables
+    for kw, kernel in ((dict(boundary=ds.DS_WRAP), '"fused_general"'),
+                       (dict(weights_h=None, weights_v=np.eye(3, 8)), '"fused_tma"')):
         pl = ds.ds_plan_create_ex(1080, 1920, (3, 8), 8, (3, 8), 8, ds.DS_F32, **kw)
         try:
-            assert '"fused_general"' in ds.ds_plan_describe(pl)
+            assert kernel in ds.ds_plan_describe(pl)
         finally:
             ds.ds_destroy(pl)
 
