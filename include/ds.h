@@ -111,8 +111,10 @@ typedef enum {
  *     Q14 rounding: q = floor(w * 16384 + 1/2), with the residual
  *     floor(16384 * row sum + 1/2) - sum(q) added to the largest tap of
  *     the row.
- * Axes with equal ratio and taps, DS_CLAMP and no given taps run on the
- * fast fused kernel; every other plan runs on the general kernels.
+ * DS_CLAMP plans whose axes form a fast class (equal ratio and taps at 3/8
+ * K=8, 1/2 K=6 or 2/3 K=6; or uint8 with H 3/8 K=8, V 4/9 K=8) run on the
+ * fast fused kernel, with given taps too (a launch then carries the plan's
+ * own tables); every other plan runs on the general kernels.
  * Errors (NULL + ds_last_error): those of ds_plan_create per axis; an
  * unknown boundary; a given tap that is not finite; for uint8, a Q14 tap
  * outside the int16 range or a row whose Q14 magnitudes sum past 65535
