@@ -85,3 +85,22 @@ def test_bounds_probe_is_reported_and_the_context_stays_usable(checked, oracle):
         assert_parity(run_fused(pl, x), oracle.filter_u8(x, 1, 2, 6), ds.DS_U8_RGB)
     finally:
         ds.ds_destroy(pl)
+
+
+@pytest.mark.parametrize("rh,Kh,rv,Kv,dt", [((3, 8), 8, (3, 8), 8, ds.DS_F32), ((1, 2), 6, (1, 2), 6, ds.DS_U8_RGB),
+                                            ((3, 8), 8, (4, 9), 8, ds.DS_U8)])
+def test_checked_build_given_taps(checked, oracle, rh, Kh, rv, Kv, dt):
+    """Given tap tables on the fast kernel, with every index check passing."""
+    rng = np.random.default_rng(Kh + Kv)
+    wh, wv = rng.normal(0, 0.3, (rh[0], Kh)), rng.normal(0, 0.3, (rv[0], Kv))
+    wh[:, Kh // 2] += 1.0
+    wv[:, Kv // 2] += 1.0
+    pl = ds.ds_plan_create_ex(100, 272, rh, Kh, rv, Kv, dt, ds.DS_CLAMP, wh, wv)
+    try:
+        assert '"fused_tma"' in ds.ds_plan_describe(pl)
+        x = frames((100, 272), dt, 3, 77)
+        xo = x if dt in (ds.DS_U8, ds.DS_U8_RGB) else x.astype(np.float64)
+        want = oracle.filter_ex(xo, rh, Kh, rv, Kv, weights_h=wh, weights_v=wv)
+        assert_parity(run_fused(pl, x), want, dt, "given taps, checked build")
+    finally:
+        ds.ds_destroy(pl)
