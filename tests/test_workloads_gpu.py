@@ -103,3 +103,23 @@ def test_uhd128_2160x3840_f16_sampled(oracle):
         assert got.shape[1:] == (810, 1440)
     finally:
         ds.ds_destroy(pl)
+
+
+@pytest.mark.parametrize("ratio,K,dt", [((1, 2), 6, ds.DS_U8_RGB), ((3, 8), 8, ds.DS_F32)])
+def test_one_8k_frame_against_the_oracle(oracle, ratio, K, dt):
+    """A single 8192x8192 frame (201 MB of RGB bytes, 268 MB of floats): 64-bit
+    offsets, 32 strips per row and the adaptive band for one frame, every
+    output compared."""
+    from tests.gpu_util import assert_parity, frames, run_fused
+
+    pl = ds.ds_plan_create(8192, 8192, ratio, K, dt)
+    try:
+        x = frames((8192, 8192), dt, 1, 8192)
+        got = run_fused(pl, x)
+        if dt == ds.DS_U8_RGB:
+            want = oracle.filter_u8(x, ratio[0], ratio[1], K)
+        else:
+            want = oracle.filter_f64(x.astype(np.float64), ratio[0], ratio[1], K)
+        assert_parity(got, want, dt, "8192x8192")
+    finally:
+        ds.ds_destroy(pl)
