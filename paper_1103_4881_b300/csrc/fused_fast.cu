@@ -227,16 +227,16 @@ using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, true, 3, 8, 8, 1, tr
 using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
 using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 2, true>;
 // uint8 RGB (integer row math)
-using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 8, 2, false, 3, 8, 8, 1, true>;
+using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 8, 2, true,  3, 8, 8, 1, true>;
 using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 2, true>;
-using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, false, 2, 3, 6, 1, true>;
+using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, true,  2, 3, 6, 1, true>;
 // the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
 //                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV FPW PRO
 using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 9, 2, false, 4, 9, 8, 2, true>;
 using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 9, 2, true, 4, 9, 8, 2, true>;
 // uint8, one channel
 using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 8, 2, false, 3, 8, 8, 1, true>;
-using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, false>;
+using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, true>;
 using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, true>;
 
 // The class of an id, as a type tag: f(ClassTag<RXX>{}) for class `cls`
@@ -949,14 +949,13 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       for (int s = 0; s < NST && s < nst; ++s) issue(s);
     issued = g + (uint32_t)min(NST, nst);
     // wait for stage s; returns the stage's row-0 base, or nullptr on timeout.
-    // FIXED: the stage's columns outside the frame get their border values
-    // (only tiles whose strip needs it)
-    auto stage_wait = [&](int s, auto fixed) -> uint8_t* {
+    // The stage's columns outside the frame get their border values (only
+    // tiles whose strip needs it)
+    auto stage_wait = [&](int s) -> uint8_t* {
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
       if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (G / NST) & 1u))) return nullptr;
       uint8_t* const sb = ring + slot * Cl::RSTAGE;
-      if constexpr (decltype(fixed)::value)
-        if (fixing) apply_edge_fix<Cl>(sb, fix, lane, jd.W, xw);
+      if (fixing) apply_edge_fix<Cl>(sb, fix, lane, jd.W, xw);
       return sb;
     };
     // stage s fully read: refill its slot with stage s + NST
@@ -1008,7 +1007,7 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     // ---- prologue: pattern rows 0 .. L-Q-1 (with PRO: the lead blocks below)
 #pragma unroll
     for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps) {
-      uint8_t* sb = stage_wait(ps, std::true_type{});
+      uint8_t* sb = stage_wait(ps);
       if (!sb) {
         ok = false;
         break;
@@ -1040,18 +1039,21 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
     if constexpr (!Cl::PRO) top_fix();
     // ---- block steps, U rows (USTG stages, UBLK blocks) at a time.  A unit
     // whose blocks are all inside the tile, whose rows are all above the
-    // frame's last row and whose outputs are all inside the frame, in a strip
-    // that needs no border fix-up and has every lane active, runs a copy of
-    // the body without any of those checks.  With PRO, blocks m < 0 are the
-    // lead blocks: their rows (those above frame row 0 included, filtered
-    // from the zero fill and then overwritten) only fill the window.
+    // frame's last row and whose output rows are all inside the frame, in a
+    // group with every frame present, runs a copy of the body without any of
+    // those checks.  Both copies fix up the border columns of each stage and
+    // mask the stores of lanes past the frame's right edge, so the left and
+    // right strips of a frame run the check-free copy too.  With PRO, blocks
+    // m < 0 are the lead blocks: their rows (those above frame row 0
+    // included, filtered from the zero fill and then overwritten) only fill
+    // the window.
     auto unit = [&](auto fast, int u) {
       constexpr bool FAST = decltype(fast)::value;
 #pragma unroll
       for (int st = 0; st < Cl::USTG; ++st) {
         const int s = Cl::STG0 + u * Cl::USTG + st;
         if (!FAST && s >= nst) break;
-        uint8_t* sb = stage_wait(s, std::integral_constant<bool, !FAST>{});
+        uint8_t* sb = stage_wait(s);
         if (!sb) {
           ok = false;
           return;
@@ -1091,8 +1093,8 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
         stage_release(s);
       }
     };
-    // every lane complete, every frame of the group present
-    const bool x_inside = !fixing && nf == Cl::FPW && (tl.strip + 1) * Cl::SBLK * Cl::P <= jd.OW;
+    // every frame of the group present
+    const bool x_inside = nf == Cl::FPW;
     const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
     for (int u = 0; ok && u < nunits; ++u) {
       if constexpr (Cl::FASTPATH) {

@@ -13,7 +13,9 @@ from tests.gpu_util import assert_parity, finish, frames, out_buffer, run_fused,
 pytestmark = pytest.mark.gpu
 
 FAST_AXES = [((3, 8), 8, (3, 8), 8), ((1, 2), 6, (1, 2), 6), ((2, 3), 6, (2, 3), 6), ((3, 8), 8, (4, 9), 8)]
-SHAPES = [(72, 528), (9, 16), (41, 272), (3, 48), (200, 784)]
+# (130, 1100): two 1024-pixel strips of the one-channel 1/2 class, the second
+# ragged, with interior units in both
+SHAPES = [(72, 528), (9, 16), (41, 272), (3, 48), (200, 784), (130, 1100)]
 
 
 @pytest.fixture(scope="module")
