@@ -18,10 +18,11 @@ from typing import Iterable, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libds.so")
 # the same library built with DS_CHECK_BOUNDS (the kernel checks its own
-# indices); load it instead with use_library(CHECK_LIB_PATH)
+# indices); load it instead with use_library(CHECK_LIB_PATH), or for the whole
+# process by setting DS_CHECK_BOUNDS=1 in the environment before the import
 CHECK_LIB_PATH = os.path.join(_HERE, "libds_check.so")
+LIB_PATH = CHECK_LIB_PATH if os.environ.get("DS_CHECK_BOUNDS") == "1" else os.path.join(_HERE, "libds.so")
 
 DS_F32, DS_F16, DS_U8, DS_U8_RGB = 0, 1, 2, 3
 DS_CLAMP, DS_WRAP = 0, 1

@@ -168,3 +168,25 @@ def test_normal_build_is_not_bounds_checked():
     with pytest.raises(ds.DsError) as e:
         ds.ds_debug_bounds_probe(0)
     assert e.value.status == ds.DS_ERR_UNSUPPORTED
+
+
+def test_env_selects_the_bounds_checking_build():
+    """DS_CHECK_BOUNDS=1 in the environment makes the binding load the
+    bounds-checking library for the whole process (no GPU needed to ask)."""
+    import subprocess
+    import sys
+
+    from paper_1103_4881_b300 import build
+
+    build.build(check_bounds=True)
+    code = ("import paper_1103_4881_b300 as ds; "
+            "assert ds.LIB_PATH == ds.CHECK_LIB_PATH, ds.LIB_PATH; "
+            "assert ds.ds_bounds_checked(); print('checked')")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, DS_CHECK_BOUNDS="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "checked" in r.stdout, r.stderr
+    env["DS_CHECK_BOUNDS"] = "0"
+    code0 = "import paper_1103_4881_b300 as ds; assert not ds.ds_bounds_checked(); print('normal')"
+    r = subprocess.run([sys.executable, "-c", code0], cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "normal" in r.stdout, r.stderr
