@@ -67,30 +67,38 @@ GenParams make_params(const ds_plan* pl) {
   return g;
 }
 
-// Index i of an axis of n elements under the plan's boundary.
-__device__ __forceinline__ int fix_index(int i, int n, int wrap) {
-  if (wrap) {
+// Index i of an axis of n elements under the plan's boundary: modulo n
+// (WRAP), else clamped to the edge.  A window reaches at most one period past
+// the frame but for the tiniest frames, so the modulo takes a division only
+// then.
+template <bool WRAP>
+__device__ __forceinline__ int fix_index(int i, int n) {
+  if constexpr (WRAP) {
+    if (i < 0) i += n;
+    else if (i >= n) i -= n;
+    if ((unsigned)i < (unsigned)n) return i;
     const int m = i % n;
     return m < 0 ? m + n : m;
+  } else {
+    return clampi(i, 0, n - 1);
   }
-  return clampi(i, 0, n - 1);
 }
 
 // Horizontal dot product of output pixel o (channel c) on input row `row`.
-template <typename T>
+template <typename T, bool WRAP>
 __device__ __forceinline__ float hdot(const GenParams& g, const T* __restrict__ row, int o, int c) {
   const int j = o % g.h.p;
   const int s = (o / g.h.p) * g.h.q + g.h.b[j];
   const float* w = g.h.w + j * g.h.K;
   float acc = 0.0f;
   for (int t = 0; t < g.h.K; ++t) {
-    const int x = fix_index(s + t, g.W, g.wrap);
+    const int x = fix_index<WRAP>(s + t, g.W);
     acc = fmaf(w[t], px_to_f(row[(size_t)x * g.C + c]), acc);
   }
   return pass_round<T>(acc);
 }
 
-template <typename T>
+template <typename T, bool WRAP>
 __global__ void __launch_bounds__(256) k_fused_general(const T* __restrict__ in, T* __restrict__ out,
                                                         const __grid_constant__ GenParams g, int frame0) {
   extern __shared__ float sh[];
@@ -110,9 +118,9 @@ __global__ void __launch_bounds__(256) k_fused_general(const T* __restrict__ in,
   // (clamped or wrapped)
   for (int idx = threadIdx.x; idx < nr * ne; idx += blockDim.x) {
     const int i = idx / ne, e = idx - i * ne;
-    const int y = fix_index(ys + i, g.H, g.wrap);
+    const int y = fix_index<WRAP>(ys + i, g.H);
     const int o = ox0 + e / g.C, c = e % g.C;
-    sh[i * te + e] = hdot<T>(g, src + (size_t)y * g.W * g.C, o, c);
+    sh[i * te + e] = hdot<T, WRAP>(g, src + (size_t)y * g.W * g.C, o, c);
   }
   __syncthreads();
   // vertical pass over the shared rows
@@ -131,7 +139,7 @@ __global__ void __launch_bounds__(256) k_fused_general(const T* __restrict__ in,
 
 // Unfused horizontal pass: inter[f][y][e] for e < OW*C.  I is the
 // intermediate type (float for float dtypes, uint8 for uint8).
-template <typename T, typename I>
+template <typename T, typename I, bool WRAP>
 __global__ void __launch_bounds__(256) k_hpass(const T* __restrict__ in, I* __restrict__ inter,
                                                 const __grid_constant__ GenParams g, int frame0) {
   const int f = frame0 + blockIdx.z;
@@ -140,12 +148,12 @@ __global__ void __launch_bounds__(256) k_hpass(const T* __restrict__ in, I* __re
   const int ne = g.OW * g.C;
   if (e >= ne) return;
   const T* row = in + ((size_t)f * g.H + y) * g.W * g.C;
-  const float v = hdot<T>(g, row, e / g.C, e % g.C);
+  const float v = hdot<T, WRAP>(g, row, e / g.C, e % g.C);
   inter[((size_t)f * g.H + y) * ne + e] = (I)v;
 }
 
 // Unfused vertical pass over the intermediate.
-template <typename T, typename I>
+template <typename T, typename I, bool WRAP>
 __global__ void __launch_bounds__(256) k_vpass(const I* __restrict__ inter, T* __restrict__ out,
                                                 const __grid_constant__ GenParams g, int frame0) {
   const int f = frame0 + blockIdx.z;
@@ -159,7 +167,7 @@ __global__ void __launch_bounds__(256) k_vpass(const I* __restrict__ inter, T* _
   const I* col = inter + (size_t)f * g.H * ne + e;
   float acc = 0.0f;
   for (int t = 0; t < g.v.K; ++t) {
-    const int y = fix_index(s + t, g.H, g.wrap);
+    const int y = fix_index<WRAP>(s + t, g.H);
     acc = fmaf(w[t], (float)col[(size_t)y * ne], acc);
   }
   out[((size_t)f * g.OH + oy) * ne + e] = f_to_px<T>(pass_round<T>(acc));
@@ -167,20 +175,19 @@ __global__ void __launch_bounds__(256) k_vpass(const I* __restrict__ inter, T* _
 
 constexpr int kMaxGridZ = 65535;
 
-template <typename T>
-ds_status fused_general_t(const ds_plan* pl, const void* in, void* out, int n_frames, cudaStream_t st) {
-  const GenParams g = make_params(pl);
+template <typename T, bool WRAP>
+ds_status fused_general_t(const GenParams& g, const void* in, void* out, int n_frames, cudaStream_t st) {
   const int nr_max = (g.tob - 1) * g.v.q + g.v.L;
   const size_t smem = (size_t)nr_max * g.tox * g.C * sizeof(float);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_fused_general<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fused_general<T, WRAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "k_fused_general smem attribute");
   }
   for (int f0 = 0; f0 < n_frames; f0 += kMaxGridZ) {
     const int nf = std::min(kMaxGridZ, n_frames - f0);
     dim3 grid((g.OW + g.tox - 1) / g.tox, (g.nby + g.tob - 1) / g.tob, nf);
     log_msg(2, "k_fused_general: %d frames, grid %d x %d x %d, %zu B shared", nf, grid.x, grid.y, grid.z, smem);
-    k_fused_general<T><<<grid, 256, smem, st>>>((const T*)in, (T*)out, g, f0);
+    k_fused_general<T, WRAP><<<grid, 256, smem, st>>>((const T*)in, (T*)out, g, f0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_fused_general launch");
     count_launches(1);
@@ -188,9 +195,8 @@ ds_status fused_general_t(const ds_plan* pl, const void* in, void* out, int n_fr
   return DS_OK;
 }
 
-template <typename T, typename I>
-ds_status unfused_t(const ds_plan* pl, const void* in, void* out, int n_frames, void* ws, cudaStream_t st) {
-  const GenParams g = make_params(pl);
+template <typename T, typename I, bool WRAP>
+ds_status unfused_t(const GenParams& g, const void* in, void* out, int n_frames, void* ws, cudaStream_t st) {
   const int ne = g.OW * g.C;
   if (g.H > 65535) {
     set_error("ds_run_unfused: frames taller than 65535 rows are not supported");
@@ -200,11 +206,11 @@ ds_status unfused_t(const ds_plan* pl, const void* in, void* out, int n_frames, 
     const int nf = std::min(kMaxGridZ, n_frames - f0);
     dim3 gh((ne + 255) / 256, g.H, nf);
     log_msg(2, "k_hpass + k_vpass: %d frames", nf);
-    k_hpass<T, I><<<gh, 256, 0, st>>>((const T*)in, (I*)ws, g, f0);
+    k_hpass<T, I, WRAP><<<gh, 256, 0, st>>>((const T*)in, (I*)ws, g, f0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_hpass launch");
     dim3 gv((ne + 255) / 256, g.OH, nf);
-    k_vpass<T, I><<<gv, 256, 0, st>>>((const I*)ws, (T*)out, g, f0);
+    k_vpass<T, I, WRAP><<<gv, 256, 0, st>>>((const I*)ws, (T*)out, g, f0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_vpass launch");
     count_launches(2);
@@ -212,14 +218,26 @@ ds_status unfused_t(const ds_plan* pl, const void* in, void* out, int n_frames, 
   return DS_OK;
 }
 
+template <typename T>
+ds_status fused_general_any(const ds_plan* pl, const void* in, void* out, int n_frames, cudaStream_t st) {
+  const GenParams g = make_params(pl);
+  return g.wrap ? fused_general_t<T, true>(g, in, out, n_frames, st) : fused_general_t<T, false>(g, in, out, n_frames, st);
+}
+
+template <typename T, typename I>
+ds_status unfused_any(const ds_plan* pl, const void* in, void* out, int n_frames, void* ws, cudaStream_t st) {
+  const GenParams g = make_params(pl);
+  return g.wrap ? unfused_t<T, I, true>(g, in, out, n_frames, ws, st) : unfused_t<T, I, false>(g, in, out, n_frames, ws, st);
+}
+
 }  // namespace
 
 ds_status launch_general_fused(const ds_plan* pl, const void* in, void* out, int n_frames, cudaStream_t st) {
   switch (pl->dtype) {
-    case DS_F32: return fused_general_t<float>(pl, in, out, n_frames, st);
-    case DS_F16: return fused_general_t<__half>(pl, in, out, n_frames, st);
+    case DS_F32: return fused_general_any<float>(pl, in, out, n_frames, st);
+    case DS_F16: return fused_general_any<__half>(pl, in, out, n_frames, st);
     case DS_U8:
-    case DS_U8_RGB: return fused_general_t<uint8_t>(pl, in, out, n_frames, st);
+    case DS_U8_RGB: return fused_general_any<uint8_t>(pl, in, out, n_frames, st);
   }
   set_error("launch_general_fused: unknown dtype");
   return DS_ERR_ARG;
@@ -227,10 +245,10 @@ ds_status launch_general_fused(const ds_plan* pl, const void* in, void* out, int
 
 ds_status launch_unfused(const ds_plan* pl, const void* in, void* out, int n_frames, void* ws, cudaStream_t st) {
   switch (pl->dtype) {
-    case DS_F32: return unfused_t<float, float>(pl, in, out, n_frames, ws, st);
-    case DS_F16: return unfused_t<__half, float>(pl, in, out, n_frames, ws, st);
+    case DS_F32: return unfused_any<float, float>(pl, in, out, n_frames, ws, st);
+    case DS_F16: return unfused_any<__half, float>(pl, in, out, n_frames, ws, st);
     case DS_U8:
-    case DS_U8_RGB: return unfused_t<uint8_t, uint8_t>(pl, in, out, n_frames, ws, st);
+    case DS_U8_RGB: return unfused_any<uint8_t, uint8_t>(pl, in, out, n_frames, ws, st);
   }
   set_error("launch_unfused: unknown dtype");
   return DS_ERR_ARG;
