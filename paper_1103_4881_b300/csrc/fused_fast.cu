@@ -1094,12 +1094,12 @@ __global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__
       }
     };
     // every frame of the group present
-    const bool x_inside = nf == Cl::FPW;
+    const bool group_full = nf == Cl::FPW;
     const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
     for (int u = 0; ok && u < nunits; ++u) {
       if constexpr (Cl::FASTPATH) {
         const int mend = (u + 1) * Cl::UBLK - Cl::VBLK;  // one past the unit's last block
-        if (x_inside && mend - Cl::UBLK >= 0 && mend <= nblk && ys + (mend - 1) * Q + L - 1 < H &&
+        if (group_full && mend - Cl::UBLK >= 0 && mend <= nblk && ys + (mend - 1) * Q + L - 1 < H &&
             (rb0 + mend) * P <= jd.OH) {
           unit(std::true_type{}, u);
           continue;
