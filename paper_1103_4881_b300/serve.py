@@ -293,7 +293,13 @@ def main():
     pool = FramePool(reqs, host=True)
     srv = Server(int(args.budget_gb * (1 << 30)), args.streams, args.max_batch)
     try:
-        srv.run(reqs[:64], pool.device, realtime=False)  # warm-up: plans, kernels, allocator
+        # warm-up: one request of every (size, ratio, dtype) in the mix, so that
+        # each plan is made and each kernel class loaded before the timed runs
+        kinds = {}
+        for r in reqs:
+            kinds.setdefault((r.height, r.width, tuple(r.ratio), r.taps, r.dtype), r)
+        srv.run(list(kinds.values()), pool.device, realtime=False)
+        srv.run(reqs[:64], pool.device, realtime=False)  # and the allocator at batch sizes
         out = {"config": {"workload": "serving mix", "requests": args.requests, "rate_hz": args.rate,
                           "streams": args.streams, "max_batch": args.max_batch, "budget_gb": args.budget_gb}}
         r, _ = srv.run(reqs, pool.device, realtime=True)
