@@ -105,18 +105,19 @@ def test_uhd128_2160x3840_f16_sampled(oracle):
         ds.ds_destroy(pl)
 
 
-@pytest.mark.parametrize("ratio,K,dt", [((1, 2), 6, ds.DS_U8_RGB), ((3, 8), 8, ds.DS_F32)])
+@pytest.mark.parametrize("ratio,K,dt", [((1, 2), 6, ds.DS_U8_RGB), ((3, 8), 8, ds.DS_F32), ((3, 8), 8, ds.DS_F16),
+                                        ((2, 3), 6, ds.DS_U8)])
 def test_one_8k_frame_against_the_oracle(oracle, ratio, K, dt):
-    """A single 8192x8192 frame (201 MB of RGB bytes, 268 MB of floats): 64-bit
-    offsets, 32 strips per row and the adaptive band for one frame, every
-    output compared."""
+    """A single 8192x8192 frame (201 MB of RGB bytes, 268 MB of floats, 134 MB
+    of halves, 67 MB of one-channel bytes): 64-bit offsets, many strips per
+    row and the adaptive band for one frame, every output compared."""
     from tests.gpu_util import assert_parity, frames, run_fused
 
     pl = ds.ds_plan_create(8192, 8192, ratio, K, dt)
     try:
         x = frames((8192, 8192), dt, 1, 8192)
         got = run_fused(pl, x)
-        if dt == ds.DS_U8_RGB:
+        if dt in (ds.DS_U8_RGB, ds.DS_U8):
             want = oracle.filter_u8(x, ratio[0], ratio[1], K)
         else:
             want = oracle.filter_f64(x.astype(np.float64), ratio[0], ratio[1], K)
