@@ -2,16 +2,22 @@
 """Benchmark of the fused horizontal + vertical decimating FIR (the downscaler
 filter stage of arXiv:1103.4881, Sec. 3) on one B300 per rank.
 
-Workload (default): 64 fp32 frames of 1080x1920, uniform [0,1) plus a seeded
-smooth gradient, 3/8 decimation with 8 Lanczos-3 taps per phase -> 405x720.
-One step = one batched persistent launch over the 64 frames, replayed from a
-CUDA graph.  Inputs (531 MB per step) are larger than the 126 MB L2, so every
-step streams them from HBM.
+Headline workload (default): 128 fp16-storage frames of 2160x3840, uniform
+[0,1) plus N(0, 0.05) noise, clipped; 3/8 decimation with 8 Lanczos-3 taps
+per phase on both axes -> 810x1440 fp16, FP32 accumulation.  The plan's
+schedule (tile shape, band, CTAs per SM) comes from the autotuner (cached
+per GPU and workload).  One step = one batched persistent launch over the
+128 frames, replayed from a CUDA graph; inputs (2.1 GB per step) are far
+larger than the 126 MB L2, so every step streams them from HBM.
 
 Prints one JSON line (rank 0): frames/s, with the roofline of the fused
-kernel, the clocks seen during the timed region, the end-to-end figure
-through the host-buffer pipeline, the plain per-frame and unfused forms, and
-the CPU oracle as a baseline.  --impl reference times the CPU oracle alone.
+kernel, the clocks seen during the timed region, the error against the FP64
+oracle on a seeded sample of frames, the end-to-end figure through the
+host-buffer pipeline, the plain per-frame and unfused forms, the CPU oracle
+as a baseline, and (key "workloads") the same device-timed batched figures,
+roofline and error for the other workloads: 64 x 1080p fp32 3/8, 300 x
+1080p uint8 RGB 1/2, and the paper's 2000 CIF frames as RGB and as YUV
+4:2:0.  --impl reference times the CPU oracle alone.
 """
 from __future__ import annotations
 
@@ -29,17 +35,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6400.0
+HEADLINE = "uhd128_2160x3840_f16"
+SIDE_WORKLOADS = ("batch64_1080x1920_f32", "rgb300_1080x1920_u8", "cif2000_352x288_u8rgb", "cif2000_yuv420_u8")
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="batch64_1080x1920_f32")
+    ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--frames", type=int, default=0, help="override the workload's frame count (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip per-frame / unfused / e2e / cpu legs")
+    ap.add_argument("--no-side", action="store_true", help="skip the other workloads (key workloads)")
+    ap.add_argument("--no-tune", action="store_true", help="the plan's default schedule, not the autotuner's")
     return ap.parse_args()
 
 
@@ -64,21 +74,27 @@ def kernel_source_hash():
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("fused_fast.cu", "pixel.cuh", "internal.h", "plan.cpp"):  # kernels and their schedule
-        with open(os.path.join(ROOT, "paper_1103_4881_b300", "csrc", name), "rb") as f:
+    import glob
+
+    csrc = os.path.join(ROOT, "paper_1103_4881_b300", "csrc")
+    names = sorted(os.path.basename(f) for f in glob.glob(os.path.join(csrc, "rows*")))
+    for name in names + ["fused_fast.cu", "pixel.cuh", "internal.h", "plan.cpp"]:  # kernels and their schedule
+        with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, schedule: dict | None = None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (else None)."""
+    the current kernel source and the same schedule (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
         e = d.get(workload)
         if e and e.get("kernel_source_hash") == kernel_source_hash():
+            if schedule is not None and e.get("schedule") is not None and e["schedule"] != schedule:
+                return None
             return int(e["dram_bytes_per_launch"])
     except Exception:
         pass
@@ -228,7 +244,7 @@ def reference_arm(args, w, rank, world):
         "impl": "reference", "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w.dtype in (0, 1) else "int64", "data": "synthetic",
-        "config": workload_config(w, w.frames),
+        "config": workload_config(w, w.frames, world),
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                          "sample": "per step: the first %d rows of %d frames (all planes), one band per thread"
                                    % (rows, samples[0].shape[0])},
@@ -237,17 +253,63 @@ def reference_arm(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(w, n):
-    """The config block of the JSON line."""
+def workload_config(w, n, world=1):
+    """The config block of the JSON line (the same in both arms)."""
+    from paper_1103_4881_b300 import synth
+
+    in_bytes = n * sum(h * ww * w.channels * synth.NP_DTYPE[w.dtype]().itemsize for h, ww in w.plane_shapes())
     cfg = {"workload": w.name, "frames_per_step": n, "in": [w.height, w.width, w.channels],
            "out": list(w.out_frame_shape()) + ([1] if w.channels == 1 else []),
-           "ratio": "%d/%d" % w.ratio, "taps": w.taps}
+           "ratio": "%d/%d" % w.ratio, "taps": w.taps,
+           "l2": ("inputs larger than L2 (%.0f MB per step vs 126 MB)" if in_bytes > 126e6 else
+                  "inputs smaller than L2 (%.0f MB per step vs 126 MB): not an HBM figure") % (in_bytes / 1e6),
+           "parallelism": ("dp%d: frames sharded over ranks, no data-path collective" % world) if world > 1
+           else "single"}
     if w.ratio_v:
         cfg["ratio_v"] = "%d/%d" % w.vratio
         cfg["taps_v"] = w.vtaps
     if w.planes:
         cfg["planes"] = [list(hw) for hw in w.plane_shapes()]
     return cfg
+
+
+def sample_frames(n: int, k: int = 16, seed: int = 12345):
+    """A seeded sample of k frames plus the first and the last."""
+    import numpy as np
+
+    if n <= k + 2:
+        return list(range(n))
+    mid = np.random.default_rng(seed).choice(np.arange(1, n - 1), size=k, replace=False)
+    return sorted({0, n - 1, *mid.tolist()})
+
+
+def accuracy(w, xs, outs, a):
+    """Error against the FP64 / integer oracle on a seeded sample of frames of
+    every plane (outside any timed region): max |err| for float data (full
+    scale 1.0), mismatched bytes for uint8."""
+    import numpy as np
+    from paper_1103_4881_b300 import synth
+
+    n = xs[0].shape[0]
+    idx = sample_frames(n)
+    u8 = w.dtype in (synth.DS_U8, synth.DS_U8_RGB)
+    err, bad, total = 0.0, 0, 0
+    for x, o in zip(xs, outs):
+        got = o[idx].cpu().numpy()
+        want = oracle_filter(w, x[idx])
+        total += got.size
+        if u8:
+            bad += int(np.count_nonzero(got != want))
+        else:
+            err = max(err, float(np.abs(got.astype(np.float64) - want).max()))
+    out = {"vs": "oracle (FP64 loop nest; int64 for uint8)", "frames": [a + i for i in idx],
+           "sample": "%d seeded frames plus the first and the last, every plane" % max(0, len(idx) - 2)}
+    if u8:
+        out.update(mismatched_bytes=bad, compared_bytes=total, bound="bit-exact")
+    else:
+        out.update(max_abs_err=err, compared_values=total, bound=1e-6 if w.dtype == synth.DS_F32 else 2e-3,
+                   full_scale=1.0)
+    return out
 
 
 def main():
@@ -268,7 +330,7 @@ def main():
     import torch
 
     import paper_1103_4881_b300 as ds
-    from paper_1103_4881_b300 import build
+    from paper_1103_4881_b300 import build, shard, tune
 
     if rank == 0:
         build.build()
@@ -281,25 +343,66 @@ def main():
         pg = dist
         dist.barrier()
     dev_index = torch.cuda.current_device()
-
-    # one plan per plane (a single plane unless the workload is planar)
-    shapes = w.plane_shapes()
-    plans = [ds.ds_plan_create_ex(h, ww, w.ratio, w.taps, w.vratio, w.vtaps, w.dtype) for h, ww in shapes]
-    plan = plans[0]
-    fbytes = [ds.ds_plan_frame_bytes(pl) for pl in plans]
-    fin, fout = fbytes[0]
-    # weak scaling: the job is world x w.frames frames, each rank filters its own
-    # contiguous share (global frame indices, so no two ranks hold the same frame)
-    from paper_1103_4881_b300 import shard
-
-    a, b = shard.frame_range(w.frames * world, world, rank)
-    n = b - a
-    xs = synth.plane_frames(w, range(a, b))
-    xins = [torch.from_numpy(x).cuda() for x in xs]
-    outs = [torch.empty((n,) + w.plane_out_shape(hw), dtype=xins[0].dtype, device="cuda") for hw in shapes]
-    x, xin, out = xs[0], xins[0], outs[0]
+    peak, peak_src = measured_peak()
     stream = torch.cuda.current_stream()
     st = stream.cuda_stream
+
+    def resident(wl, a, b):
+        """Plans (one per plane), the frames [a, b) on the host and on the
+        device, and their output buffers."""
+        shapes = wl.plane_shapes()
+        plans = [ds.ds_plan_create_ex(h, ww, wl.ratio, wl.taps, wl.vratio, wl.vtaps, wl.dtype) for h, ww in shapes]
+        xs = synth.plane_frames(wl, range(a, b))
+        xins = [torch.from_numpy(x).cuda() for x in xs]
+        outs = [torch.empty((b - a,) + wl.plane_out_shape(hw), dtype=xins[0].dtype, device="cuda") for hw in shapes]
+        return plans, xs, xins, outs
+
+    def clock_warm(fn, ms=20.0):
+        # keep the GPU busy right before a timed region: after an idle gap
+        # (a sync, the clock sampler starting) its clocks take a moment to
+        # come back up, which would land inside a short timed region
+        t = time.perf_counter()
+        while (time.perf_counter() - t) * 1e3 < ms:
+            fn()
+            torch.cuda.synchronize()
+
+    def timed(fn, k, barrier=True):
+        clock_warm(fn)
+        if pg and barrier:
+            pg.barrier()
+        torch.cuda.synchronize()
+        ds.ds_launch_count()  # count the timed steps' launches only
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if pg and barrier:
+            t = torch.tensor([ms], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # weak scaling: the job is world x w.frames frames, each rank filters its own
+    # contiguous share (global frame indices, so no two ranks hold the same frame)
+    a, b = shard.frame_range(w.frames * world, world, rank)
+    n = b - a
+    plans, xs, xins, outs = resident(w, a, b)
+    fbytes = [ds.ds_plan_frame_bytes(pl) for pl in plans]
+    fin = fbytes[0][0]
+
+    # the schedule: the autotuner's choice for this GPU and workload (cached)
+    schedule = []
+    for pl, xi, o in zip(plans, xins, outs):
+        if args.no_tune:
+            schedule.append(dict(ds.ds_plan_get_schedule_ex(pl), tuned=False))
+        else:
+            r = tune.apply_or_tune(pl, xi.data_ptr(), o.data_ptr(), n, st, 10)
+            schedule.append(dict(r, tuned=True))
+        schedule[-1]["describe"] = json.loads(ds.ds_plan_describe(pl))
 
     # the step: one batched persistent launch over the n frames (of every
     # plane), replayed as a CUDA graph
@@ -314,35 +417,6 @@ def main():
     torch.cuda.synchronize()
     ds.ds_stream_check(st)
 
-    def clock_warm(fn, ms=20.0):
-        # keep the GPU busy right before a timed region: after an idle gap
-        # (a sync, the clock sampler starting) its clocks take a moment to
-        # come back up, which would land inside a short timed region
-        t = time.perf_counter()
-        while (time.perf_counter() - t) * 1e3 < ms:
-            fn()
-            torch.cuda.synchronize()
-
-    def timed(fn, k):
-        clock_warm(fn)
-        if pg:
-            pg.barrier()
-        torch.cuda.synchronize()
-        ds.ds_launch_count()  # count the timed steps' launches only
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if pg:
-            t = torch.tensor([ms], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms
-
     with ClockSampler(dev_index) as clocks:
         ms = timed(step, args.steps)
     launches = ds.ds_launch_count()
@@ -354,28 +428,28 @@ def main():
     alg_bytes = n * sum(fi + fo for fi, fo in fbytes)  # input read once + output written once, per launch
     launch_s = ms / 1e3 / args.steps
     achieved = alg_bytes / launch_s / 1e9
-    peak, peak_src = measured_peak()
+    sched_key = [{k: sc[k] for k in ("row_blocks", "ctas_per_sm", "shape")} for sc in schedule]
     # the committed capture is of the full workload's launch: none for a resized one
-    traffic = profiled_traffic(w.name) if n == synth.WORKLOADS[w.name].frames else None
+    traffic = profiled_traffic(w.name, sched_key) if n == synth.WORKLOADS[w.name].frames else None
 
     line = {
         "metric": "frames/s", "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "u8", 3: "u8"}[w.dtype], "data": "synthetic",
-        "config": dict(workload_config(w, n), **{
-                   "form": "batched persistent fused H+V kernel, CUDA graph replay",
+        "config": workload_config(w, n, world),
+        "timing": {"form": "batched persistent fused H+V kernel, CUDA graph replay",
                    "warm": "W warm-up steps, then about 20 ms more of untimed steps right before the timed region",
-                   "l2": ("inputs larger than L2 (%.0f MB per step vs 126 MB)" if n * sum(f[0] for f in fbytes) > 126e6
-                          else "inputs smaller than L2 (%.0f MB per step vs 126 MB): not an HBM figure")
-                         % (n * sum(f[0] for f in fbytes) / 1e6),
-                   "parallelism": ("dp%d: frames sharded over ranks, no data-path collective" % world) if world > 1 else "single"}),
+                   "events": "CUDA events on the launching stream around the K steps"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": peak_src,
                      "alg_bytes_per_launch": alg_bytes, "kernel_us": launch_s * 1e6},
         "clocks": clk,
         "gpu_launches": launches,
+        "schedule": schedule,
     }
 
+    if rank == 0:
+        line["accuracy"] = accuracy(w, xs, outs, a)
     if rank == 0 and not args.no_extras:
         # enough repetitions for at least 256 frames per form (a 1-frame workload
         # would otherwise time a few launches, dominated by host jitter)
@@ -386,7 +460,7 @@ def main():
                 for pl, xi, o, (fi, fo) in zip(plans, xins, outs, fbytes):
                     ds.ds_run(pl, xi.data_ptr() + i * fi, o.data_ptr() + i * fo, st)
         per_frame()
-        ms_pf = timed(per_frame, k2)
+        ms_pf = timed(per_frame, k2, barrier=False)
         # unfused two-kernel form over the batch
         wsb = max(ds.ds_plan_workspace_bytes(pl) for pl in plans) * n
         ws = torch.empty(wsb, dtype=torch.uint8, device="cuda")
@@ -394,13 +468,13 @@ def main():
             for pl, xi, o in zip(plans, xins, outs):
                 ds.ds_run_unfused(pl, xi.data_ptr(), o.data_ptr(), n, ws.data_ptr(), wsb, st)
         unfused()
-        ms_uf = timed(unfused, k2)
+        ms_uf = timed(unfused, k2, barrier=False)
         del ws
         # batched without the graph (direct launch)
         def direct():
             ds.ds_batch_run(job, st)
         direct()
-        ms_dl = timed(direct, k2)
+        ms_dl = timed(direct, k2, barrier=False)
         line["forms"] = {
             "batched_graph_fps": value / world,
             "batched_direct_fps": n * k2 / (ms_dl / 1e3),
@@ -410,7 +484,7 @@ def main():
         }
         # end to end through the C ABI with pinned host buffers (copies in the timed region)
         host_ins = [torch.from_numpy(xx).pin_memory() for xx in xs]
-        host_outs = [torch.empty((n,) + w.plane_out_shape(hw), dtype=xin.dtype).pin_memory() for hw in shapes]
+        host_outs = [torch.empty(tuple(o.shape), dtype=o.dtype).pin_memory() for o in outs]
         chunk = 4 if fin > (1 << 20) else 64  # frames per pipeline chunk
         pipes = [ds.ds_pipeline_create(pl, chunk, 3) for pl in plans]
         def e2e_step():
@@ -438,10 +512,60 @@ def main():
     ds.ds_graph_destroy(graph)
     for pl in plans:
         ds.ds_destroy(pl)
+    del xins, outs, xs
+
+    if rank == 0 and world == 1 and not args.no_side:
+        line["workloads"] = side_workloads(args, ds, synth, resident, timed, dev_index, peak)
+
     if rank == 0:
         print(json.dumps(line), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def side_workloads(args, ds, synth, resident, timed, dev_index, peak):
+    """The other workloads, each as its own batched graph launch at the
+    plan's default schedule: device time per launch, roofline against the
+    measured copy peak, DRAM traffic from the committed capture, the clocks
+    during its timed region and its error against the oracle."""
+    import torch
+
+    st = torch.cuda.current_stream().cuda_stream
+    res = {}
+    for name in SIDE_WORKLOADS:
+        if name == args.workload:
+            continue
+        wl = synth.WORKLOADS[name]
+        plans, xs, xins, outs = resident(wl, 0, wl.frames)
+        fbytes = [ds.ds_plan_frame_bytes(pl) for pl in plans]
+        alg = wl.frames * sum(fi + fo for fi, fo in fbytes)
+        g = ds.ds_graph_create([(pl, xi.data_ptr(), o.data_ptr(), wl.frames) for pl, xi, o in zip(plans, xins, outs)])
+        step = lambda: ds.ds_graph_launch(g, st)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ds.ds_stream_check(st)
+        # at least a quarter of a second of steps, so the clock sampler sees the region
+        est = timed(step, 5, barrier=False) / 5
+        k = max(args.steps, int(250.0 / max(est, 1e-3)))
+        with ClockSampler(dev_index) as clocks:
+            ms = timed(step, k, barrier=False)
+        ds.ds_stream_check(st)
+        us = ms * 1e3 / k
+        sched = [{k_: v for k_, v in ds.ds_plan_get_schedule_ex(pl).items()} for pl in plans]
+        res[name] = {
+            "frames_per_launch": wl.frames, "steps": k, "kernel_us": us, "frames_per_s": wl.frames / (us * 1e-6),
+            "alg_bytes_per_launch": alg, "achieved_gbs": alg / (us * 1e-6) / 1e9,
+            "frac": alg / (us * 1e-6) / 1e9 / peak, "traffic": profiled_traffic(name, sched),
+            "clocks": clocks.summary(), "schedule": "default (shape 0, adaptive band)",
+            "accuracy": accuracy(wl, xs, outs, 0),
+        }
+        ds.ds_graph_destroy(g)
+        for pl in plans:
+            ds.ds_destroy(pl)
+        del xs, xins, outs
+        torch.cuda.empty_cache()
+    return res
 
 
 if __name__ == "__main__":

@@ -134,8 +134,10 @@ typedef struct {
 
 ds_plan* ds_plan_create_ex(const ds_plan_desc* desc);
 
-/* Release a plan.  The caller must make sure no launch using it is still
- * running (synchronise the streams it was used on first).  NULL is ignored. */
+/* Release a plan (the end of the life of the downscaler's filter tasks,
+ * Sec. 3.A; the paper has no API, this is the plan lifecycle of the C ABI).
+ * The caller must make sure no launch using it is still running (synchronise
+ * the streams it was used on first).  NULL is ignored. */
 void ds_destroy(ds_plan* plan);
 
 /* The arguments the plan was created with (any pointer may be NULL); p, q
@@ -147,7 +149,10 @@ ds_status ds_plan_get_params(const ds_plan* plan, int* in_h, int* in_w, int* p, 
 ds_status ds_plan_get_axes(const ds_plan* plan, int* p_h, int* q_h, int* taps_h, int* p_v, int* q_v,
                            int* taps_v, int* boundary);
 
-/* Output extent floor(in*p/q) per axis and the channel count. */
+/* Output extent floor(in*p/q) per axis and the channel count: the shape of
+ * the output array of the tiler (Sec. 3.A: 352 -> 132 per line at 3/8, the
+ * output pattern of p elements per repetition).  DS_ERR_ARG on a NULL plan;
+ * NULL output pointers are skipped. */
 ds_status ds_plan_out_shape(const ds_plan* plan, int* out_h, int* out_w, int* channels);
 
 /* Input / output bytes of one frame. */
@@ -179,24 +184,64 @@ ds_status ds_plan_describe(const ds_plan* plan, char* buf, size_t len);
  * from the task multiplicity, Sec. 3.B.1): row_blocks = output row blocks
  * per tile (each block is p output rows), ctas_per_sm = resident CTAs per SM
  * of the persistent grid (0 = as many as fit).  Used by the autotuner.
- * A new plan has a per-class default band and no fixed schedule: a launch
- * whose work would not fill the GPU's pipelines at that band (one frame, a
- * small batch) then runs shorter bands.  After ds_plan_set_schedule (or
- * ds_plan_autotune) every launch uses row_blocks as given.  The schedule
- * never changes the results, only the time.
+ * A new plan has a per-class default band and no fixed band: a launch whose
+ * work would not fill the GPU's pipelines at that band (one frame, a small
+ * batch) then runs shorter bands.  After ds_plan_set_schedule every launch
+ * uses row_blocks as given.  Either way the last tiles of a launch (about
+ * two per pipeline) run at a quarter of the band, which shortens the end of
+ * the launch.  The schedule never changes the results, only the time.
  * DS_ERR_ARG for row_blocks < 1 or ctas_per_sm < 0.
  */
 ds_status ds_plan_set_schedule(ds_plan* plan, int row_blocks, int ctas_per_sm);
 ds_status ds_plan_get_schedule(const ds_plan* plan, int* row_blocks, int* ctas_per_sm);
 
 /*
- * Autotuner: time ds_run_frames(plan, in, out, n_frames) for each candidate
- * band height (output row blocks per tile) with CUDA events on `stream`,
- * `iters` launches each after one warm-up, and keep the fastest in the plan.
- * Every candidate produces identical bits.  Synchronises the stream.  The
- * chosen value and its time per launch (us) are returned if the pointers are
- * not NULL.  DS_ERR_ARG on NULL pointers, n_frames < 1 or iters < 1.
+ * The whole schedule, with the tile shape (Sec. 3.B.1, as above).  Every fast
+ * kernel class is compiled in ds_plan_tile_shapes(plan) tile shapes (the
+ * pipeline depth of a warp's shared-memory ring and the resident warps its
+ * registers are budgeted for; ds_plan_describe shows them); plans on the
+ * general kernels have none (0) and take only shape 0.
+ *   row_blocks: output row blocks per tile; 0 = the class default band,
+ *     shortened for launches too small to fill the GPU;
+ *   ctas_per_sm: resident CTAs per SM; 0 = as many as fit;
+ *   shape: 0 .. ds_plan_tile_shapes(plan) - 1 (0 = the default shape).
+ * DS_ERR_ARG on NULL, negative fields or a shape out of range.
  */
+typedef struct {
+    int row_blocks;
+    int ctas_per_sm;
+    int shape;
+} ds_schedule;
+int ds_plan_tile_shapes(const ds_plan* plan);
+ds_status ds_plan_set_schedule_ex(ds_plan* plan, const ds_schedule* schedule);
+ds_status ds_plan_get_schedule_ex(const ds_plan* plan, ds_schedule* schedule);
+
+/*
+ * Autotuner (the launch topology of Sec. 3.B.1, measured instead of derived
+ * from thresholds): time ds_run_frames(plan, in, out, n_frames) with CUDA
+ * events on `stream`, `iters` launches per candidate after one warm-up, over
+ *   1. every tile shape at the default band,
+ *   2. fixed bands at the best shape (against the default adaptive band),
+ *   3. fewer resident CTAs per SM at the best shape and band,
+ * and keep the fastest schedule in the plan.  The default schedule (shape 0,
+ * adaptive band, full occupancy) is always timed, so the result is never
+ * slower than it as measured.  Every candidate produces identical bits.
+ * `in` / `out` are the caller's device buffers for n_frames frames; they are
+ * written (out) during tuning.  Synchronises the stream.
+ * res (if not NULL): the best schedule, its time and the default's (us per
+ * launch), and the number of candidates timed.
+ * ds_plan_autotune is the same with the band and time of the result only.
+ * DS_ERR_ARG on NULL pointers, n_frames < 1 or iters < 1; on any other
+ * failure the plan keeps the schedule it had.
+ */
+typedef struct {
+    ds_schedule best;
+    float best_us;
+    float default_us;
+    int candidates;
+} ds_tune_result;
+ds_status ds_plan_autotune_ex(ds_plan* plan, const void* in, void* out, int n_frames, void* stream,
+                              int iters, ds_tune_result* res);
 ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frames, void* stream,
                            int iters, int* best_row_blocks, float* best_us);
 
@@ -205,14 +250,22 @@ ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frame
 /* ---------------------------------------------------------------------- */
 
 /*
- * Filter one frame: in (in_h x in_w x C elements) -> out (out_h x out_w x C),
- * horizontal pass then vertical pass fused in one kernel; the intermediate
- * stays in shared memory.  in and out must not overlap.
+ * Filter one frame (the downscaler's filter stage, Sec. 3: the horizontal
+ * filter over every line, then the vertical filter over every column, each
+ * a repetition of the Array-OL tiler of Sec. 3.A): in (in_h x in_w x C
+ * elements) -> out (out_h x out_w x C), both passes fused in one kernel; the
+ * intermediate stays on chip.  in and out must not overlap.
+ * Fused launches take tile-scheduling counters from a ring of 512 slots; a
+ * slot is reused only once the launch that last used it has completed (the
+ * call waits for one when all 512 are in flight).  A fused launch inside a
+ * stream capture that the caller started is refused (DS_ERR_UNSUPPORTED):
+ * capture with ds_graph_create instead.
  * DS_ERR_ARG: NULL plan / pointer.  DS_ERR_CUDA: launch failure.
  */
 ds_status ds_run(const ds_plan* plan, const void* in, void* out, void* stream);
 
-/* Filter n_frames frames stored back to back (one launch). */
+/* Filter n_frames frames stored back to back (one launch; the frames are the
+ * independent repetitions of the paper's task over its video, Sec. 3.A). */
 ds_status ds_run_frames(const ds_plan* plan, const void* in, void* out, int n_frames,
                         void* stream);
 
@@ -225,10 +278,11 @@ typedef struct {
 } ds_job;
 
 /*
- * Filter a batch of jobs of any mix of plans (sizes, ratios, dtypes) with one
- * persistent launch per kernel family (all fast-path plans share one
- * launch); jobs whose plan needs the general kernel get their own launches
- * on the same stream.  Job descriptors travel in the launch parameters: no
+ * Filter a batch of jobs of any mix of plans (sizes, ratios, dtypes): the
+ * repetitions of every job's tasks (Sec. 3.A) in one persistent launch per
+ * kernel class and tile shape (one fast class = one dtype and one ratio and
+ * tap count per axis); jobs whose plan needs the general kernel get their
+ * own launches on the same stream.  Job descriptors travel in the launch parameters: no
  * device memory is allocated.  Batches beyond the per-launch descriptor limit
  * are split into several launches.  DS_ERR_ARG: n < 0, NULL jobs with n > 0,
  * NULL plan or pointer in a job.
@@ -258,6 +312,10 @@ ds_status ds_run_unfused(const ds_plan* plan, const void* in, void* out, int n_f
  * n_frames frames (ds_plan_workspace_bytes * n_frames) exceeds it.
  * The first call on a device looks up the array's device address (host
  * set-up, no allocation): make that first call before any stream capture.
+ * The address is then kept for the life of the process; after
+ * cudaDeviceReset (or anything else that tears down the device's primary
+ * context) it is no longer valid, and this entry point must not be called
+ * again in that process.
  * All calls share the array and it keeps the last call's contents (every
  * value a call reads it has written first); calls whose launches overlap on
  * the GPU -- on different streams or from different host threads -- race on
@@ -362,7 +420,8 @@ void ds_pipeline_destroy(ds_pipeline* pipe);
 /* Misc                                                                     */
 /* ---------------------------------------------------------------------- */
 
-/* Thread-local message of the last failure on this thread ("" if none). */
+/* Thread-local message of the last failure on this thread ("" if none).
+ * Error reporting of the C ABI; the paper has no API. */
 const char* ds_last_error(void);
 
 /* Library version string. */

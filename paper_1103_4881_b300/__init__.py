@@ -39,7 +39,8 @@ ABI_SYMBOLS = (
     "ds_pipeline_create", "ds_pipeline_run", "ds_pipeline_destroy", "ds_last_error", "ds_version",
     "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static", "ds_plan_autotune",
     "ds_debug_timeout_probe", "ds_plan_create_ex", "ds_plan_get_axes", "ds_plan_get_axis_taps",
-    "ds_bounds_checked", "ds_debug_bounds_probe",
+    "ds_bounds_checked", "ds_debug_bounds_probe", "ds_plan_tile_shapes", "ds_plan_set_schedule_ex",
+    "ds_plan_get_schedule_ex", "ds_plan_autotune_ex",
 )
 
 
@@ -57,6 +58,15 @@ class ds_plan_desc(ctypes.Structure):
     _fields_ = [("in_h", ctypes.c_int), ("in_w", ctypes.c_int), ("ratio_h", ds_ratio), ("taps_h", ctypes.c_int),
                 ("ratio_v", ds_ratio), ("taps_v", ctypes.c_int), ("dtype", ctypes.c_int), ("boundary", ctypes.c_int),
                 ("weights_h", ctypes.c_void_p), ("weights_v", ctypes.c_void_p)]
+
+
+class ds_schedule(ctypes.Structure):
+    _fields_ = [("row_blocks", ctypes.c_int), ("ctas_per_sm", ctypes.c_int), ("shape", ctypes.c_int)]
+
+
+class ds_tune_result(ctypes.Structure):
+    _fields_ = [("best", ds_schedule), ("best_us", ctypes.c_float), ("default_us", ctypes.c_float),
+                ("candidates", ctypes.c_int)]
 
 
 class ds_job(ctypes.Structure):
@@ -112,6 +122,10 @@ def lib() -> ctypes.CDLL:
         "ds_plan_create_ex": (vp, [ctypes.POINTER(ds_plan_desc)]),
         "ds_plan_get_axes": (i, [vp, ip, ip, ip, ip, ip, ip, ip]),
         "ds_plan_get_axis_taps": (i, [vp, i, vp, vp, vp, vp]),
+        "ds_plan_tile_shapes": (i, [vp]),
+        "ds_plan_set_schedule_ex": (i, [vp, ctypes.POINTER(ds_schedule)]),
+        "ds_plan_get_schedule_ex": (i, [vp, ctypes.POINTER(ds_schedule)]),
+        "ds_plan_autotune_ex": (i, [vp, vp, vp, i, vp, i, ctypes.POINTER(ds_tune_result)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -244,6 +258,32 @@ def ds_plan_autotune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream
     _check(lib().ds_plan_autotune(_ptr(plan), _ptr(in_ptr), _ptr(out_ptr), n_frames, _ptr(stream), iters,
                                   ctypes.byref(rb), ctypes.byref(us)))
     return rb.value, us.value
+
+
+def ds_plan_tile_shapes(plan: int) -> int:
+    return int(lib().ds_plan_tile_shapes(_ptr(plan)))
+
+
+def ds_plan_set_schedule_ex(plan: int, row_blocks: int = 0, ctas_per_sm: int = 0, shape: int = 0) -> None:
+    """row_blocks 0 = the class default (adaptive) band; ctas_per_sm 0 = as many as fit."""
+    sc = ds_schedule(row_blocks, ctas_per_sm, shape)
+    _check(lib().ds_plan_set_schedule_ex(_ptr(plan), ctypes.byref(sc)))
+
+
+def ds_plan_get_schedule_ex(plan: int) -> dict:
+    sc = ds_schedule()
+    _check(lib().ds_plan_get_schedule_ex(_ptr(plan), ctypes.byref(sc)))
+    return {"row_blocks": sc.row_blocks, "ctas_per_sm": sc.ctas_per_sm, "shape": sc.shape}
+
+
+def ds_plan_autotune_ex(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: int = 0, iters: int = 10) -> dict:
+    """Time tile shapes, bands and CTAs per SM on the given buffers and keep the
+    fastest schedule in the plan; returns it with its time and the default's."""
+    r = ds_tune_result()
+    _check(lib().ds_plan_autotune_ex(_ptr(plan), _ptr(in_ptr), _ptr(out_ptr), n_frames, _ptr(stream), iters,
+                                     ctypes.byref(r)))
+    return {"row_blocks": r.best.row_blocks, "ctas_per_sm": r.best.ctas_per_sm, "shape": r.best.shape,
+            "us_per_launch": r.best_us, "default_us_per_launch": r.default_us, "candidates": r.candidates}
 
 
 def ds_debug_timeout_probe(limit_cycles: int, stream: int = 0) -> None:

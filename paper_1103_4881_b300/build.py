@@ -58,11 +58,16 @@ def build(force: bool = False, verbose: bool = False, check_bounds: bool = False
         common += ["-Xptxas", "-v"]
     objs = []
     procs = []
+    # an object is rebuilt when it is older than its source or any header
+    headers = [p for p in _inputs() if not p.endswith((".cu", ".cpp"))]
+    newest_header = max(os.path.getmtime(p) for p in headers)
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
+        objs.append(obj)
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
+            continue
         cmd = [nvcc()] + common + ["-c", src, "-o", obj]
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-        objs.append(obj)
     failed = False
     for cmd, p in procs:
         out, _ = p.communicate()

@@ -1,1133 +1,31 @@
-// fused_fast.cu -- the fused horizontal + vertical decimating FIR for B300.
+// fused_fast.cu -- host side of the fused horizontal + vertical kernel
+// (rows.cuh): the table of compiled classes and tile shapes, tensor maps,
+// tile schedules (band heights, launch tails), scheduling slots, launches,
+// and the device status word.
 //
-// One persistent kernel per class runs the whole filter stage of the paper's
-// downscaler (Sec. 3: horizontal filter, then vertical filter, packets of q
-// pixels -> p outputs).  Work is cut into tiles: a strip of output columns x
-// a band of output row blocks of one frame; tiles are handed to warps from a
-// per-launch counter.  Each warp runs its tile by itself:
-//
-//   lane 0 issues TMA tensor loads (cp.async.bulk.tensor.3d) of SR input rows
-//     of the strip plus its left and right halo into the warp's private ring
-//     of NST shared-memory stages, completion tracked by one mbarrier each;
-//   every input row goes through the horizontal pass in registers: each lane
-//     reads one contiguous chunk of the row (NB packets of q pixels plus the
-//     halo) with vector ld.shared and computes NB*p outputs per channel with
-//     the phase taps (kernel parameters, i.e. constant-bank operands);
-//   the results enter a sliding window of the last L filtered rows, also in
-//     registers, so the intermediate never leaves the SM (the paper's
-//     Sec. 3.B.3 removes host round trips between the two filters; this
-//     removes the device-memory round trip as well);
-//   each time q new rows have entered the window, the warp computes the p
-//     output rows of one block from it and stores them.
-//
-// Per class: a warp may split into groups of 32/FPW lanes that filter the
-// same strip and band of FPW frames (narrow frames), and the window may be
-// filled by lead blocks run through the loop body instead of a separate
-// unrolled prologue.  The row loop has no per-lane branch: lanes past the
-// frame's edge compute on in-window data with their stores masked.
-//
-// Float data accumulate in FP32 with fmaf in tap order t = 0..K-1 from 0, the
-// same sequence as the general kernels; uint8 data use exact integer dot
-// products (dp2a) whose rounding is the same integer formula; so results are
-// identical bit for bit whatever kernel, tile or batch computes them.
-//
-// Every wait on an mbarrier is bounded (2e9 SM clock cycles, about 1 s).  On
-// expiry the warp records DS_ERR_TIMEOUT in a device status word, waits
-// (bounded) for the copies it issued and leaves.
-#include <cudaTypedefs.h>
-
+// A batch is cut into one persistent launch per kernel class (dtype, ratio
+// and taps of each axis; the paper's downscaler filter, Sec. 3).  The jobs of
+// a launch travel in its __grid_constant__ parameters, with their tiles
+// numbered in job order; warps take tiles from a per-launch counter.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
-#include <type_traits>
+#include <thread>
 #include <vector>
 
-#include "internal.h"
-#include "pixel.cuh"
+#include "rows.cuh"
 
 namespace ds {
+namespace rows {
 
-__device__ int g_fast_status = 0;  // 0 = fine; 1 = wait timed out or bad class; 3 = bounds check
-// Bounds-checking builds (-DDS_CHECK_BOUNDS): the kernel checks its own shared
-// memory row reads, border writes, TMA copies and output rows against their
-// buffers, and a failed check records what failed (kind, offset) and skips
-// the access instead of making it.
-#ifdef DS_CHECK_BOUNDS
-constexpr bool kCheckBounds = true;
-#else
-constexpr bool kCheckBounds = false;
-#endif
-constexpr int kStatusBounds = 3;
-__device__ long long g_bounds_info[2];  // kind (1 row read, 2 border write, 3 output row, 4 copy), offset
-__device__ __forceinline__ void bounds_fail(int kind, long long offset) {
-  if (atomicCAS(&g_fast_status, 0, kStatusBounds) == 0) {
-    g_bounds_info[0] = kind;
-    g_bounds_info[1] = offset;
-  }
-}
-
-// Dynamic tile scheduling of the row-streaming kernel: launch slot s hands out
-// tiles from g_tile_next[s]; the last warp to finish puts both counters of
-// its slot back to zero.  Direct launches take the slots below kGraphSlot0 in
-// turn, so launches that overlap (different streams) use different counters
-// unless kGraphSlot0 launches were issued while one of them ran; launches
-// captured into a CUDA graph own a slot above it until the graph is
-// destroyed (replays of one graph are serialised by CUDA).
-constexpr int kSchedSlots = 1024;
-constexpr int kGraphSlot0 = 512;
-__device__ unsigned int g_tile_next[kSchedSlots];
-__device__ unsigned int g_warps_done[kSchedSlots];
+// The status word and scheduling counters of every launch on this GPU.
+__device__ DevState g_dev_state;
 
 namespace {
-
-constexpr int kMaxJobs = 64;                  // job descriptors per launch
-constexpr int kMaxTaps = 32;                  // p*K of the fast classes (per axis)
-constexpr long long kWaitLimitCycles = 2000000000ll;  // ~1 s at the B300's 2.03 GHz
-constexpr uint32_t kSuspendHintNs = 20000;             // a waiting thread sleeps up to 20 us per poll
-constexpr int kStatusTimeout = 1;
-
-// ---------------------------------------------------------------------------
-// compile-time geometry
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr int cfloordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
-__host__ __device__ constexpr int rup(int a, int m) { return cdiv(a, m) * m; }
-// window start of phase j: floor(((2j+1) q - p) / (2p)) - K/2 + 1
-__host__ __device__ constexpr int phase_b(int P, int Q, int K, int j) {
-  return cfloordiv((2 * j + 1) * Q - P, 2 * P) - K / 2 + 1;
-}
-__host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
-
-// The tensor maps view every row as 8-byte elements, whatever the pixel type:
-// a box row can then hold 256 x 8 bytes, so one box covers a strip's window
-// (one TMA copy per stage and frame).  Rows are a multiple of 16 bytes on
-// the fast path, and every strip's window starts on a 16-byte boundary.
-constexpr int kTmaElem = 8;
-constexpr CUtensorMapDataType kTmaType = CU_TENSOR_MAP_DATA_TYPE_UINT64;
-
-// A fast-path class: data type, channels, horizontal ratio P/Q and taps K,
-// vertical ratio PV/QV and taps KV (by default those of the horizontal axis),
-// and the tile shape -- NB packets (of Q input pixels) per lane and row, so a
-// strip is 32*NB packets wide (32/FPW*NB with frame groups); SR input rows per
-// pipeline stage, NST stages per warp;
-// FP: whether interior units run a second, check-free copy of the loop body
-// (faster for some classes, slower where the larger code costs more than the
-// checks, measured per class);
-// FPW: frames per warp -- the warp's lanes split into FPW groups of 32/FPW,
-// each filtering the same strip and band of its own frame (for narrow frames,
-// whose width is a poor multiple of 32 lanes' packets);
-// PRO: the window prologue runs through the loop body as lead blocks whose
-// outputs are dropped (less code, a few more rows filtered per tile) instead
-// of a separate unrolled copy of the row code.
-template <int ID, typename T_, int C_, int P_, int Q_, int K_, int NB_, int SR_, int NST_, bool FP_, int PV_ = P_,
-          int QV_ = Q_, int KV_ = K_, int FPW_ = 1, bool PRO_ = false>
-struct Cls {
-  using T = T_;
-  static constexpr int id = ID, C = C_, P = P_, Q = Q_, K = K_, NB = NB_;
-  static constexpr int PV = PV_, QV = QV_, KV = KV_;
-  static constexpr bool FASTPATH = FP_;             // check-free copy of the body for interior units
-  // warps (independent tile pipelines) per CTA, and the resident CTAs per SM
-  // the registers are budgeted for.  One-warp CTAs pack an SM more finely
-  // than 4-warp ones, as many as the stage rings and registers allow (32 is
-  // the most an SM takes); they measured faster or equal for every class but
-  // fp32 2/3 and one-channel 2/3, which keep 4-warp CTAs, 4 per SM
-  static constexpr int WPC = (ID == kFcF32_23 || ID == kFcU8C1_23) ? 4 : 1;
-  static constexpr int MINB = (ID == kFcF32_23 || ID == kFcU8C1_23) ? 4
-                              : (ID == kFcU8C3_CIF)                    ? 14
-                              : (ID == kFcU8C3_12)                     ? 32
-                              : (ID == kFcU8C1_CIF)                    ? 22
-                              : (ID == kFcF32_38 || ID == kFcU8C1_38)  ? 12
-                              : (ID == kFcF32_12 || ID == kFcU8C1_12)  ? 17
-                              : (ID == kFcF16_23)                      ? 18
-                                                                       : 16;
-  static constexpr int SRR = SR_;                   // input rows per stage
-  static constexpr int NST = NST_;                  // stages per warp
-  static constexpr int SZ = (int)sizeof(T);
-  static constexpr int FPW = FPW_;                  // frames per warp
-  static constexpr int LPS = 32 / FPW_;             // lanes per frame (a strip's lanes)
-  // horizontal axis: the strip, its halo columns and the lane chunks
-  static constexpr int BMIN = phase_b(P, Q, K, 0);
-  static constexpr int BMAX = phase_b(P, Q, K, P - 1);
-  static constexpr int LH = -BMIN;                  // halo pixels left of a block
-  static constexpr int RH = BMAX + K - Q;           // halo pixels right of a block
-  static constexpr int E = NB * Q * C;              // elements per lane and row
-  static constexpr int EB = E * SZ;
-  static constexpr int HLB = rup(LH * C * SZ, 16);  // left halo bytes in the window (TMA x alignment)
-  static constexpr int RHB = rup(RH * C * SZ, 16);
-  static constexpr int SBLK = LPS * NB;             // packets (blocks) per strip
-  static constexpr int SPX = SBLK * Q;              // input pixels per strip
-  static constexpr int WINB = HLB + SPX * C * SZ + RHB;
-  static constexpr int NBOX = cdiv(WINB / kTmaElem, 256);
-  static constexpr int BOXB = rup(cdiv(WINB, NBOX), 16);
-  static constexpr int BOXE = BOXB / kTmaElem;         // box width in TMA elements
-  static constexpr int BOXSTR = rup(SR_ * BOXB, 128);  // each box lands 128-B aligned
-  static constexpr int FSTR = NBOX * BOXSTR;          // one frame's window in a stage
-  static constexpr int RSTAGE = FPW_ * FSTR;
-  static constexpr int RTX = NBOX * SR_ * BOXB;        // TMA bytes per stage and frame
-  static constexpr int WARP_BYTES = NST_ * RSTAGE;
-  static constexpr int NX = (LH + NB * Q + RH) * C;    // elements one lane reads per row
-  static constexpr int VB = (EB % 16 == 0) ? 16 : ((EB % 8 == 0) ? 8 : 4);
-  static constexpr int NV = EB / VB;
-  static constexpr int HB = cdiv(LH * C * SZ, VB);     // halo vectors a lane loads before its chunk
-  static constexpr int HA = cdiv(RH * C * SZ, VB);     // ... and after it
-  static constexpr int NVT = HB + NV + HA;             // vectors per lane and row
-  static constexpr int NWT = NVT * VB / 4;             // words per lane and row
-  static constexpr int NOUT = NB * P * C;              // H outputs per lane and row
-  // vertical axis: the row stream and the register window
-  static constexpr int BMINV = phase_b(PV, QV, KV, 0);
-  static constexpr int BMAXV = phase_b(PV, QV, KV, PV - 1);
-  static constexpr int LV = BMAXV - BMINV + KV;     // pattern length (rows per block window)
-  static constexpr int LHV = -BMINV;                // halo rows above a block
-  // The stream of a tile is cut so that the window prologue (the first LV-QV
-  // pattern rows) fills whole stages, EXTRA rows being loaded before the first
-  // pattern row; after it, every group of U = lcm(SR, QV) rows is USTG stages
-  // and UBLK block steps, so each row's stage offset and window slot are
-  // compile-time constants.
-  static constexpr int PRE = LV - QV;
-  static constexpr int NPS = cdiv(PRE, SR_);
-  static constexpr int EXTRA = NPS * SR_ - PRE;
-  static constexpr int U = SR_ / cgcd(SR_, QV) * QV;
-  static constexpr int USTG = U / SR_;
-  static constexpr int UBLK = U / QV;
-  // With PRO, the stream instead starts VBLK blocks early (whole units): the
-  // lead blocks fill the window, their outputs are not computed.
-  static constexpr bool PRO = PRO_;
-  static constexpr int VBLK = PRO_ ? rup(cdiv(PRE, QV), UBLK) : 0;  // lead blocks
-  static constexpr int STG0 = PRO_ ? 0 : NPS;                         // first stage of unit 0
-  static constexpr int YOFF = PRO_ ? PRE - VBLK * QV : -EXTRA;        // stream start - first pattern row
-  // Stage 0 of a tile is loaded S0SHIFT rows later than the stream grid puts
-  // it: it starts at the first pattern row, so the EXTRA alignment rows are
-  // not read from memory (its last EXTRA rows repeat the first rows of
-  // stage 1, fetched at the same time and served from L2).
-  static constexpr int S0SHIFT = PRO_ ? 0 : EXTRA;
-  __host__ __device__ static constexpr int b(int j) { return phase_b(P, Q, K, j); }
-  __host__ __device__ static constexpr int bv(int j) { return phase_b(PV, QV, KV, j); }
-  static_assert(EB % 4 == 0, "a lane's chunk must be whole words");
-  static_assert(HB * VB <= HLB && HA * VB <= RHB, "halo vectors must lie in the loaded window");
-  static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
-  static_assert((SPX * C * SZ) % 16 == 0 && HLB % 16 == 0, "strip windows start on 16-byte boundaries");
-  static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
-  static_assert(P * K <= kMaxTaps && PV * KV <= kMaxTaps, "tap table size");
-  static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
-  static_assert(PRE > LHV, "the window prologue must reach frame row 0");
-  static_assert(LV * (SZ == 1 ? (NOUT + 3) / 4 : NOUT) <= 48, "register window too large");
-  static_assert(U <= 16, "iteration unit too long to unroll");
-  static_assert(FPW_ == 1 || FPW_ == 2 || FPW_ == 4, "frames per warp");
-  static_assert(NX == (LH + NB * Q + RH) * C, "lane window (float row math)");
-};
-
-//                 id          T       C  P  Q  K  NB SR NST FP   (PV QV KV FPW PRO)
-using RF32_38 = Cls<kFcF32_38, float,  1, 3, 8, 8, 1, 8, 2, false>;
-using RF32_12 = Cls<kFcF32_12, float,  1, 1, 2, 6, 4, 4, 3, true>;
-using RF32_23 = Cls<kFcF32_23, float,  1, 2, 3, 6, 2, 6, 3, true>;
-using RF16_38 = Cls<kFcF16_38, __half, 1, 3, 8, 8, 1, 8, 3, true, 3, 8, 8, 1, true>;
-using RF16_12 = Cls<kFcF16_12, __half, 1, 1, 2, 6, 4, 8, 3, true>;
-using RF16_23 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 2, true>;
-// uint8 RGB (integer row math)
-using RU8_38 = Cls<kFcU8C3_38, uint8_t, 3, 3, 8, 8, 1, 8, 2, true,  3, 8, 8, 1, true>;
-using RU8_12 = Cls<kFcU8C3_12, uint8_t, 3, 1, 2, 6, 4, 4, 2, true>;
-using RU8_23 = Cls<kFcU8C3_23, uint8_t, 3, 2, 3, 6, 4, 3, 3, true,  2, 3, 6, 1, true>;
-// the paper's CIF case: horizontal 3/8 K=8, vertical 4/9 K=8 (RGB, and one plane)
-//                    id           T        C  P  Q  K  NB SR NST FP     PV QV KV FPW PRO
-using RU8_CIF = Cls<kFcU8C3_CIF, uint8_t, 3, 3, 8, 8, 1, 9, 2, false, 4, 9, 8, 2, true>;
-using RU8P_CIF = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 9, 2, true, 4, 9, 8, 2, true>;
-// uint8, one channel
-using RU8P_38 = Cls<kFcU8C1_38, uint8_t, 1, 3, 8, 8, 4, 8, 2, false, 3, 8, 8, 1, true>;
-using RU8P_12 = Cls<kFcU8C1_12, uint8_t, 1, 1, 2, 6, 16, 4, 3, true>;
-using RU8P_23 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4, 3, 3, true>;
-
-// The class of an id, as a type tag: f(ClassTag<RXX>{}) for class `cls`
-// (the one place that lists them; every per-class host function goes
-// through it).  Ids without a class map to the last one's tag only to keep
-// one return type: callers check fast_class >= 0 first.
-template <class Cl_>
-struct ClassTag {
-  using type = Cl_;
-};
-template <class F>
-auto with_class(int cls, F&& f) {
-  switch (cls) {
-    case kFcF32_38: return f(ClassTag<RF32_38>{});
-    case kFcF32_12: return f(ClassTag<RF32_12>{});
-    case kFcF32_23: return f(ClassTag<RF32_23>{});
-    case kFcF16_38: return f(ClassTag<RF16_38>{});
-    case kFcF16_12: return f(ClassTag<RF16_12>{});
-    case kFcF16_23: return f(ClassTag<RF16_23>{});
-    case kFcU8C3_38: return f(ClassTag<RU8_38>{});
-    case kFcU8C3_12: return f(ClassTag<RU8_12>{});
-    case kFcU8C3_23: return f(ClassTag<RU8_23>{});
-    case kFcU8C3_CIF: return f(ClassTag<RU8_CIF>{});
-    case kFcU8C1_CIF: return f(ClassTag<RU8P_CIF>{});
-    case kFcU8C1_38: return f(ClassTag<RU8P_38>{});
-    case kFcU8C1_12: return f(ClassTag<RU8P_12>{});
-    default: return f(ClassTag<RU8P_23>{});
-  }
-}
-
-// ---------------------------------------------------------------------------
-// launch parameters
-// ---------------------------------------------------------------------------
-struct JobDesc {
-  CUtensorMap tmap;        // 3-D map: (W*C elements, H rows, n_frames)
-  void* out;
-  long long out_frame;     // elements per output frame
-  int H, W, OH, OW;
-  int nframes, cls, strips, chunks;
-  int rbc, tile_begin, tiles, out_vec;
-};
-static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor layout");
-
-// The taps of one class.  tap2h / tap2v: the Q14 taps of a uint8 class as
-// pairs of int16 for dp2a, [window-start parity][phase][pair]: for parity a,
-// pair i holds taps 2i - a (low half) and 2i + 1 - a (high half), zero
-// outside 0..K-1, so a window that starts on an odd slot is read from the
-// even slot before it.
-constexpr int kMaxPairs = 5;  // (K + 1) / 2 + 1 for K <= 8
-constexpr int kMaxPhases = 4;
-
-struct ClassTaps {
-  float taps[kMaxTaps];   // horizontal FP32 taps, or Q14 taps as floats for uint8
-  float tapsv[kMaxTaps];  // the same for the vertical axis
-  uint32_t tap2h[2][kMaxPhases][kMaxPairs];
-  uint32_t tap2v[2][kMaxPhases][kMaxPairs];
-};
-
-// Launch parameters (a __grid_constant__ kernel argument) with room for MAXJ
-// job descriptors: a small size for single jobs keeps the argument -- copied
-// by the driver at every launch -- short.
-template <int MAXJ>
-struct FastParams {
-  JobDesc jobs[MAXJ];
-  ClassTaps t;
-  int n_jobs;
-  int total_tiles;
-  int sched_slot;                  // row kernel: dynamic scheduling slot
-};
-constexpr int kFewJobs = 2;        // one job, or one job split for the launch tail
-
-// ---------------------------------------------------------------------------
-// PTX wrappers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t saddr32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(saddr32(bar)), "r"(parity), "r"(kSuspendHintNs)
-      : "memory");
-  return ok != 0;
-}
-// Wait for the phase of `parity` to complete; false after `limit` SM clock
-// cycles (about a second by default), counted from the 4th failed poll.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = kWaitLimitCycles) {
-#pragma unroll 1
-  for (int it = 0; it < 4; ++it)
-    if (mbar_try(bar, parity)) return true;
-  const long long t0 = clock64();
-  for (uint32_t it = 1;; ++it) {
-    if (mbar_try(bar, parity)) return true;
-    if ((it & 3u) == 0 && clock64() - t0 > limit) return false;
-  }
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(saddr32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr32(bar))
-      : "memory");
-}
-// ---------------------------------------------------------------------------
-// tiles
-// ---------------------------------------------------------------------------
-struct Tile {
-  int job, frame, strip, chunk;  // frame: the group of the job's frames FPW * frame .. + FPW - 1
-};
-
-template <class PR>
-__host__ __device__ __forceinline__ Tile decode_tile(const PR& prm, int t) {
-  int lo = 0, hi = prm.n_jobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prm.jobs[mid].tile_begin <= t) lo = mid;
-    else hi = mid - 1;
-  }
-  const JobDesc& jd = prm.jobs[lo];
-  const int tl = t - jd.tile_begin;
-  const int per_frame = jd.strips * jd.chunks;
-  Tile r;
-  r.job = lo;
-  r.frame = tl / per_frame;
-  const int rem = tl - r.frame * per_frame;
-  r.chunk = rem / jd.strips;  // strips vary fastest: neighbouring CTAs share halos in L2
-  r.strip = rem - r.chunk * jd.strips;
-  return r;
-}
-
-// Offset of byte `byte` of window row 0 inside a stage: boxes are stored one
-// after the other, each as SR rows of BOXB bytes (BOXSTR bytes apart), so row
-// r of the window starts r * BOXB bytes further in every box.
-template <class Cl>
-__host__ __device__ __forceinline__ int win_off(int byte) {
-  const int box = byte / Cl::BOXB;
-  return byte + box * (Cl::BOXSTR - Cl::BOXB);
-}
-
-// ---------------------------------------------------------------------------
-// consumer: horizontal pass of one row
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ float word_elem(const uint32_t* w, int byte);
-template <>
-__device__ __forceinline__ float word_elem<float>(const uint32_t* w, int byte) { return __uint_as_float(w[byte >> 2]); }
-template <>
-__device__ __forceinline__ float word_elem<__half>(const uint32_t* w, int byte) {
-  const uint32_t v = w[byte >> 2];
-  const unsigned short h = (byte & 2) ? (unsigned short)(v >> 16) : (unsigned short)(v & 0xffffu);
-  return __half2float(__ushort_as_half(h));
-}
-
-
-// Per-lane shared-memory offsets (row 0 of a stage) of the vectors the H
-// pass loads: HB halo vectors, the lane's own NV vectors, HA halo vectors,
-// consecutive in the window.  They depend only on the lane: computed once.
-template <class Cl>
-struct Offs {
-  int v[Cl::NVT];
-};
-
-template <class Cl>
-__device__ __forceinline__ Offs<Cl> thread_offs(int lane) {
-  Offs<Cl> o;
-  const int sub = lane / Cl::LPS, li = lane % Cl::LPS;  // the lane's frame in the group, its lane in the strip
-  const int first = Cl::HLB + li * Cl::EB - Cl::HB * Cl::VB;
-#pragma unroll
-  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = sub * Cl::FSTR + win_off<Cl>(first + v * Cl::VB);
-  return o;
-}
-
-// Load the lane's vectors of one window row into words w[0..NWT).
-template <class Cl>
-__device__ __forceinline__ void load_row(const uint8_t* rowbase, const Offs<Cl>& o, uint32_t* w) {
-  constexpr int WPV = Cl::VB / 4;
-#pragma unroll
-  for (int v = 0; v < Cl::NVT; ++v) {
-    const uint8_t* p = rowbase + o.v[v];
-    if constexpr (Cl::VB == 16) {
-      const uint4 x = *reinterpret_cast<const uint4*>(p);
-      w[v * WPV] = x.x; w[v * WPV + 1] = x.y; w[v * WPV + 2] = x.z; w[v * WPV + 3] = x.w;
-    } else if constexpr (Cl::VB == 8) {
-      const uint2 x = *reinterpret_cast<const uint2*>(p);
-      w[v * WPV] = x.x; w[v * WPV + 1] = x.y;
-    } else {
-      w[v] = *reinterpret_cast<const uint32_t*>(p);
-    }
-  }
-}
-
-// Clamp-to-edge in the loaded window: the columns of a warp's read range that
-// lie outside the frame (TMA filled them with zeros) get the value of the
-// first / last column of their row.  Pixel ranges [l_lo, 0) and [r_lo, r_hi).
-struct EdgeFix {
-  int l_lo, nl, r_lo, nr;  // first pixel and element counts, left and right
-};
-
-template <class Cl>
-__host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int W) {
-  const int seg0 = strip * Cl::SPX - Cl::LH;             // first pixel the warp reads
-  const int seg1 = (strip + 1) * Cl::SPX + Cl::RH;       // one past the last
-  EdgeFix f;
-  f.l_lo = seg0;
-  f.nl = seg0 < 0 ? ((seg1 < 0 ? seg1 : 0) - seg0) * Cl::C : 0;
-  f.r_lo = W > seg0 ? W : seg0;
-  const int lim = W + Cl::NB * Cl::Q + Cl::RH;  // active lanes read no further
-  const int r_hi = seg1 < lim ? seg1 : lim;
-  f.nr = r_hi > f.r_lo ? (r_hi - f.r_lo) * Cl::C : 0;
-  return f;
-}
-
-// Applied to all SR rows of a stage at once: each element's source and
-// destination offsets are worked out once for the stage (one copy of this
-// code per stage wait, not per row).
-template <class Cl>
-__device__ __forceinline__ void apply_edge_fix(uint8_t* stagebase, const EdgeFix& f, int lane, int W, int xw) {
-  using T = typename Cl::T;
-  const int n = f.nl + f.nr;  // elements to fix per row of a frame window
-  for (int e2 = lane; e2 < Cl::FPW * n; e2 += 32) {
-    int sub = 0;  // e2 / n, for at most 4 frames
-    if constexpr (Cl::FPW > 1) sub = (e2 >= n) + (Cl::FPW > 2 ? (e2 >= 2 * n) + (e2 >= 3 * n) : 0);
-    const int e = e2 - sub * n;
-    const bool left = e < f.nl;
-    const int k = left ? e : e - f.nl;
-    const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
-    const int src = sub * Cl::FSTR + win_off<Cl>(((left ? 0 : W - 1) * Cl::C + c - xw) * Cl::SZ);
-    const int dst = sub * Cl::FSTR + win_off<Cl>((px * Cl::C + c - xw) * Cl::SZ);
-#pragma unroll
-    for (int r = 0; r < Cl::SRR; ++r) {
-      if constexpr (kCheckBounds) {  // both elements inside this stage
-        const int lo = r * Cl::BOXB + (src < dst ? src : dst), hi = r * Cl::BOXB + (src > dst ? src : dst);
-        if (lo < 0 || hi + Cl::SZ > Cl::RSTAGE) {
-          bounds_fail(2, lo < 0 ? lo : hi);
-          continue;
-        }
-      }
-      *reinterpret_cast<T*>(stagebase + r * Cl::BOXB + dst) =
-          *reinterpret_cast<const T*>(stagebase + r * Cl::BOXB + src);
-    }
-  }
-  // these generic-proxy writes must land before the TMA refills the stage
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncwarp();
-}
-
-// Horizontal pass of one window row whose words the thread has loaded (see
-// load_row): NB packets of Q pixels per thread, each giving P outputs per
-// channel, pass-rounded, in o[(n*P + j)*C + c].
-template <class Cl>
-__device__ __forceinline__ void hcompute(const uint32_t* w, const float* __restrict__ taps, float* o) {
-  using T = typename Cl::T;
-  float x[Cl::NX];
-  constexpr int first = Cl::HB * Cl::VB - Cl::LH * Cl::C * Cl::SZ;  // byte of the first halo element in w
-#pragma unroll
-  for (int e = 0; e < Cl::NX; ++e) x[e] = word_elem<T>(w, first + e * Cl::SZ);
-#pragma unroll
-  for (int n = 0; n < Cl::NB; ++n) {
-#pragma unroll
-    for (int j = 0; j < Cl::P; ++j) {
-#pragma unroll
-      for (int c = 0; c < Cl::C; ++c) {
-        float acc = 0.0f;
-#pragma unroll
-        for (int t = 0; t < Cl::K; ++t)
-          acc = fmaf(taps[j * Cl::K + t], x[(n * Cl::Q + Cl::b(j) - Cl::BMIN + t) * Cl::C + c], acc);
-        o[(n * Cl::P + j) * Cl::C + c] = pass_round<T>(acc);
-      }
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// row-streaming kernel: one self-contained pipeline per warp
-// ---------------------------------------------------------------------------
-// Rows above / below the frame are never loaded: their window slots take a
-// copy of the first / last filtered row (clamp-to-edge); columns outside the
-// frame are fixed up in shared memory.  Warps synchronise with nothing but
-// their own TMA completions.
-
-// Store n_valid (<= N) consecutive output values with the widest aligned stores.
-template <typename T, int N>
-__device__ __forceinline__ void store_run(T* o, const float* v, int n_valid) {
-  constexpr int BYTES = N * (int)sizeof(T);
-  const uintptr_t a = reinterpret_cast<uintptr_t>(o);
-  if (n_valid >= N) {
-    if constexpr (sizeof(T) == 4) {
-      if constexpr (BYTES % 16 == 0) {
-        if ((a & 15) == 0) {
-#pragma unroll
-          for (int i = 0; i < N / 4; ++i)
-            reinterpret_cast<float4*>(o)[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-          return;
-        }
-      }
-      if constexpr (BYTES % 8 == 0) {
-        if ((a & 7) == 0) {
-#pragma unroll
-          for (int i = 0; i < N / 2; ++i) reinterpret_cast<float2*>(o)[i] = make_float2(v[2 * i], v[2 * i + 1]);
-          return;
-        }
-      }
-    } else if constexpr (sizeof(T) == 2) {
-      if constexpr (N % 2 == 0) {
-        if ((a & 3) == 0) {
-#pragma unroll
-          for (int i = 0; i < N / 2; ++i) reinterpret_cast<__half2*>(o)[i] = __floats2half2_rn(v[2 * i], v[2 * i + 1]);
-          return;
-        }
-      }
-    } else {
-      if constexpr (N % 2 == 0) {
-        if ((a & 1) == 0) {
-#pragma unroll
-          for (int i = 0; i < N / 2; ++i)
-            reinterpret_cast<unsigned short*>(o)[i] =
-                (unsigned short)((uint32_t)f_to_px<T>(v[2 * i]) | ((uint32_t)f_to_px<T>(v[2 * i + 1]) << 8));
-          return;
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (i < n_valid) o[i] = f_to_px<T>(v[i]);
-}
-
-// ---------------------------------------------------------------------------
-// row math of the row-streaming kernel
-// ---------------------------------------------------------------------------
-// What one row of the register window holds, how the H pass fills it from a
-// loaded input row and how the V pass turns the window into P output rows.
-
-template <class Cl, bool INT = (sizeof(typename Cl::T) == 1)>
-struct RowMath;
-
-// Float data: FP32 values, FMA chains in tap order.
-template <class Cl>
-struct RowMath<Cl, false> {
-  using T = typename Cl::T;
-  static constexpr int N = Cl::NOUT;
-  struct Row {
-    float v[N];
-  };
-  template <class PR>
-  __device__ static __forceinline__ void h(const uint32_t* w, const PR& prm, Row& r) {
-    hcompute<Cl>(w, prm.t.taps, r.v);
-  }
-  __device__ static __forceinline__ void copy(Row& d, const Row& s) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) d.v[k] = s.v[k];
-  }
-  // the PV output rows of block rr from the window (CHECK: rows past OH are
-  // skipped; without it the caller knows they are all inside)
-  template <bool CHECK, class PR>
-  __device__ static __forceinline__ void v(const Row (&win)[Cl::LV], const PR& prm, T* obase, long long rowe,
-                                           int rr, int OH, int n_valid) {
-    const float* taps = prm.t.tapsv;
-#pragma unroll
-    for (int jv = 0; jv < Cl::PV; ++jv) {
-      const int oy = rr * Cl::PV + jv;
-      if (!CHECK || oy < OH) {
-        float acc[N];
-#pragma unroll
-        for (int k = 0; k < N; ++k) acc[k] = 0.0f;
-#pragma unroll
-        for (int tt = 0; tt < Cl::KV; ++tt) {
-          const float wt = taps[jv * Cl::KV + tt];
-#pragma unroll
-          for (int k = 0; k < N; ++k) acc[k] = fmaf(wt, win[Cl::bv(jv) - Cl::BMINV + tt].v[k], acc[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < N; ++k) acc[k] = pass_round<T>(acc[k]);
-        store_run<T, N>(obase + (long long)oy * rowe, acc, n_valid);
-      }
-    }
-  }
-};
-
-// dp2a: c + a.lo16 * b.byte(2h) + a.hi16 * b.byte(2h+1), taps signed,
-// pixels unsigned; h = 0 (.lo) or 1 (.hi).
-template <int HALF>
-__device__ __forceinline__ int dp2a(uint32_t taps, uint32_t px, int c) {
-  int d;
-  if constexpr (HALF == 0) asm("dp2a.lo.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(taps), "r"(px), "r"(c));
-  else asm("dp2a.hi.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(taps), "r"(px), "r"(c));
-  return d;
-}
-
-// Bytes p0..p3 of the word array w as one word, byte k = byte pk; p0 is the
-// lowest position and p3 the highest, and the words they span (at most four)
-// are all inside the array.
-// The positions are compile-time constants after unrolling, so the selectors
-// fold and only the words that hold one of the bytes are read.
-__device__ __forceinline__ uint32_t gather4(const uint32_t* w, int p0, int p1, int p2, int p3) {
-  const int pos[4] = {p0, p1, p2, p3};
-  const int a = p0 >> 2, top = (p3 >> 2) - a;
-  unsigned s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int wi = (pos[k] >> 2) - a, by = pos[k] & 3;
-    if (wi <= 1) {
-      s1 |= (unsigned)(wi * 4 + by) << (4 * k);
-      s3 |= (unsigned)k << (4 * k);
-    } else {
-      s2 |= (unsigned)((wi - 2) * 4 + by) << (4 * k);
-      s3 |= (unsigned)(4 + (top == 2 ? by : k)) << (4 * k);
-    }
-  }
-  if (top == 0) return __byte_perm(w[a], w[a], s1);
-  const uint32_t r1 = __byte_perm(w[a], w[a + 1], s1);
-  if (top == 1) return r1;
-  if (top == 2) return __byte_perm(r1, w[a + 2], s3);
-  return __byte_perm(r1, __byte_perm(w[a + 2], w[a + 3], s2), s3);
-}
-
-// (acc + 2^13) >> 14 has been taken by starting acc at 2^13: a floor shift.
-// The clamp to [0, 255] happens when the values are packed.
-__device__ __forceinline__ int u8_round(int acc) { return acc >> 14; }
-
-// Four shifted sums as the bytes of one word (v0 lowest), each saturated to
-// [0, 255]: two saturating pack conversions (each converts two s32 values to
-// u8 and places them below the low half of its third operand).
-__device__ __forceinline__ uint32_t pack4(int v0, int v1, int v2, int v3) {
-  uint32_t hi, d;
-  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(hi) : "r"(v3), "r"(v2), "r"(0u));
-  asm("cvt.pack.sat.u8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(v1), "r"(v0), "r"(hi));
-  return d;
-}
-
-// Store the first n_valid (<= N) of a lane's N output bytes (packed 4 to a
-// word in w).  Every lane of a warp takes the same path: wide stores when N
-// is a multiple of 4 (so all lanes share the row's alignment), byte stores
-// otherwise or at a frame's right edge.
-template <int N>
-__device__ __forceinline__ void store_bytes(uint8_t* o, const uint32_t* w, int n_valid) {
-  if constexpr (N % 4 == 0) {
-    const uintptr_t a = reinterpret_cast<uintptr_t>(o);
-    if (n_valid >= N) {
-      if constexpr (N % 16 == 0) {
-        if ((a & 15) == 0) {
-#pragma unroll
-          for (int i = 0; i < N / 16; ++i)
-            reinterpret_cast<uint4*>(o)[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
-          return;
-        }
-      }
-      if constexpr (N % 8 == 0) {
-        if ((a & 7) == 0) {
-#pragma unroll
-          for (int i = 0; i < N / 8; ++i) reinterpret_cast<uint2*>(o)[i] = make_uint2(w[2 * i], w[2 * i + 1]);
-          return;
-        }
-      }
-      if ((a & 3) == 0) {
-#pragma unroll
-        for (int i = 0; i < N / 4; ++i) reinterpret_cast<uint32_t*>(o)[i] = w[i];
-        return;
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (i < n_valid) o[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
-}
-
-// uint8 data: exact integer arithmetic with packed bytes.  A window row holds
-// the lane's NOUT horizontal results as bytes (4 per word, in output order).
-// The H pass first gathers each channel's pixels into words of 4 consecutive
-// pixels, then every output is K/2 (+1 for a window starting on an odd
-// pixel) dp2a steps over pixel pairs against the int16 tap pairs; the V pass
-// interleaves the bytes of window rows 2m and 2m+1 column by column and does
-// the same over row pairs.  Sums start at 2^13, so (acc + 2^13) >> 14 is a
-// plain shift; the results are the bits of the float kernels and the oracle.
-template <class Cl>
-struct RowMath<Cl, true> {
-  using T = uint8_t;
-  static constexpr int C = Cl::C, Q = Cl::Q, P = Cl::P, K = Cl::K, BMIN = Cl::BMIN;  // horizontal
-  static constexpr int PV = Cl::PV, KV = Cl::KV, LV = Cl::LV, BMINV = Cl::BMINV;      // vertical
-  static constexpr int N = Cl::NOUT;
-  static constexpr int NW = (N + 3) / 4;
-  static constexpr int NXP = Cl::LH + Cl::NB * Q + Cl::RH;  // window pixels of a lane
-  static constexpr int NPR = (LV + 2) / 2;                  // window row pairs (+1 slot of pad)
-  static_assert(Cl::HB * Cl::VB >= Cl::LH * C, "pixel slot 0 must be a loaded byte");
-  static_assert(Cl::HB * Cl::VB - Cl::LH * C + NXP * C <= Cl::NVT * Cl::VB, "gathered bytes must be loaded");
-  static_assert(P <= kMaxPhases && PV <= kMaxPhases &&
-                    (K + 2) / 2 <= kMaxPairs && (KV + 2) / 2 <= kMaxPairs, "tap pair table");
-  struct Row {
-    uint32_t w[NW];
-  };
-  __device__ static __forceinline__ void copy(Row& d, const Row& s) {
-#pragma unroll
-    for (int k = 0; k < NW; ++k) d.w[k] = s.w[k];
-  }
-  template <class PR>
-  __device__ static __forceinline__ uint32_t tp(const PR& prm, int par, int j, int i) {
-    return prm.t.tap2h[par][j][i];
-  }
-  template <class PR>
-  __device__ static __forceinline__ uint32_t tpv(const PR& prm, int par, int j, int i) {
-    return prm.t.tap2v[par][j][i];
-  }
-  template <class PR>
-  __device__ static __forceinline__ void h(const uint32_t* w, const PR& prm, Row& r) {
-    constexpr int first = Cl::HB * Cl::VB - Cl::LH * C;  // byte of pixel slot 0, channel 0
-    auto pos = [&](int slot, int c) { return first + (slot < NXP ? slot : NXP - 1) * C + c; };  // pads: any byte
-    int v[N];
-    if constexpr (C == 3) {
-      // Pixel pair m (slots 2m, 2m+1): one word holds its R pair (low half)
-      // and G pair (high half) -- five consecutive bytes, so one byte_perm --
-      // and another its B pair (low half).
-      constexpr int NPW = (NXP + 2) / 2;
-      uint32_t rg[NPW], bb[NPW];
-#pragma unroll
-      for (int m = 0; m < NPW; ++m) {
-        rg[m] = gather4(w, pos(2 * m, 0), pos(2 * m + 1, 0), pos(2 * m, 1), pos(2 * m + 1, 1));
-        bb[m] = gather4(w, pos(2 * m, 2), pos(2 * m + 1, 2), pos(2 * m + 1, 2), pos(2 * m + 1, 2));
-      }
-#pragma unroll
-      for (int n = 0; n < Cl::NB; ++n)
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-          const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
-          const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            int acc = 8192;
-#pragma unroll
-            for (int i = 0; i < npair; ++i) {
-              const int m = pr0 + i;
-              acc = (c == 1) ? dp2a<1>(tp(prm, par, j, i), rg[m], acc)
-                             : dp2a<0>(tp(prm, par, j, i), c == 0 ? rg[m] : bb[m], acc);
-            }
-            v[(n * P + j) * C + c] = u8_round(acc);
-          }
-        }
-    } else {
-      // one channel word per 4 consecutive pixel slots (pairs 2k, 2k+1)
-      constexpr int NCW = (NXP + 1 + 3) / 4;  // channel words (+1: odd-start pad)
-      uint32_t cw[C][NCW];
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int k = 0; k < NCW; ++k)
-          cw[c][k] = gather4(w, pos(4 * k, c), pos(4 * k + 1, c), pos(4 * k + 2, c), pos(4 * k + 3, c));
-#pragma unroll
-      for (int n = 0; n < Cl::NB; ++n)
-#pragma unroll
-        for (int j = 0; j < P; ++j) {
-          const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
-          const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            int acc = 8192;
-#pragma unroll
-            for (int i = 0; i < npair; ++i) {
-              const int pi = pr0 + i;
-              acc = (pi & 1) ? dp2a<1>(tp(prm, par, j, i), cw[c][pi >> 1], acc)
-                             : dp2a<0>(tp(prm, par, j, i), cw[c][pi >> 1], acc);
-            }
-            v[(n * P + j) * C + c] = u8_round(acc);
-          }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < NW; ++k) {
-      const int e = 4 * k;
-      r.w[k] = pack4(v[e], e + 1 < N ? v[e + 1] : 0, e + 2 < N ? v[e + 2] : 0, e + 3 < N ? v[e + 3] : 0);
-    }
-  }
-  template <bool CHECK, class PR>
-  __device__ static __forceinline__ void v(const Row (&win)[LV], const PR& prm, T* obase, long long rowe,
-                                           int rr, int OH, int n_valid) {
-    // one word column g (4 output columns) at a time: row-pair words
-    // pl = bytes 0,1 of rows 2m and 2m+1 interleaved, ph = bytes 2,3
-    uint32_t o[PV][NW];
-#pragma unroll
-    for (int g = 0; g < NW; ++g) {
-      uint32_t pl[NPR], ph[NPR];
-#pragma unroll
-      for (int m = 0; m < NPR; ++m) {
-        const int r0 = 2 * m < LV ? 2 * m : LV - 1, r1 = 2 * m + 1 < LV ? 2 * m + 1 : LV - 1;
-        pl[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x5140u);
-        ph[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x7362u);
-      }
-#pragma unroll
-      for (int jv = 0; jv < PV; ++jv) {
-        const int s0 = Cl::bv(jv) - BMINV;
-        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (KV + par + 1) / 2;
-        int v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          int acc = 8192;
-#pragma unroll
-          for (int i = 0; i < npair; ++i) {
-            const uint32_t word = (e & 2) ? ph[pr0 + i] : pl[pr0 + i];
-            acc = (e & 1) ? dp2a<1>(tpv(prm, par, jv, i), word, acc) : dp2a<0>(tpv(prm, par, jv, i), word, acc);
-          }
-          v[e] = u8_round(acc);
-        }
-        o[jv][g] = pack4(v[0], v[1], v[2], v[3]);
-      }
-    }
-#pragma unroll
-    for (int jv = 0; jv < PV; ++jv) {
-      const int oy = rr * PV + jv;
-      if (!CHECK || oy < OH) store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
-    }
-  }
-};
-
-template <class Cl, int WPC, int MINB, int MAXJ>
-__global__ void __launch_bounds__(WPC * 32, MINB) k_rows(const __grid_constant__ FastParams<MAXJ> prm) {
-  using T = typename Cl::T;
-  using RM = RowMath<Cl>;
-  using Row = typename RM::Row;
-  // L, Q, P: the vertical axis (row stream, window, output rows); the
-  // horizontal one is Cl::P / Cl::Q / Cl::K
-  constexpr int L = Cl::LV, Q = Cl::QV, P = Cl::PV, SR = Cl::SRR, NST = Cl::NST;
-  extern __shared__ uint8_t smem_raw[];
-  // 128-byte aligned start, derived from the __shared__ array by an offset
-  // (not through an integer cast) so that every access stays a shared-memory
-  // access (ld.shared / st.shared), not a generic one
-  uint8_t* smem = smem_raw + ((128u - (saddr32(smem_raw) & 127u)) & 127u);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint8_t* const ring = smem + warp * Cl::WARP_BYTES;
-  uint64_t* const full = reinterpret_cast<uint64_t*>(smem + WPC * Cl::WARP_BYTES) + warp * NST;
-  if constexpr (kCheckBounds) {
-    // poison the ring (all-ones bytes: NaN for float data) so that a read of
-    // staging memory before its copy lands shows up in the results
-    for (int i = lane; i < Cl::WARP_BYTES / 4; i += 32) reinterpret_cast<uint32_t*>(ring)[i] = 0xffffffffu;
-    __syncwarp();
-  }
-  if (lane == 0) {
-    for (int s = 0; s < NST; ++s) mbar_init(&full[s], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncwarp();
-  const Offs<Cl> of = thread_offs<Cl>(lane);
-  const unsigned nwarps = gridDim.x * WPC;
-  unsigned* const next = &g_tile_next[prm.sched_slot];
-  // the first tile of every warp is its warp index (so the launch does not
-  // start with every warp hitting one counter); later ones come from the
-  // counter, offset by the number of warps
-  auto next_tile = [&]() -> int {
-    unsigned t = 0;
-    if (lane == 0) t = nwarps + atomicAdd(next, 1u);
-    return (int)__shfl_sync(0xffffffffu, t, 0);
-  };
-  uint32_t g = 0;       // this warp's stage counter over all its tiles (mbarrier phases)
-  uint32_t issued = 0;  // one past the last stage issued
-  bool ok = true;
-  for (int t = (int)(blockIdx.x * WPC + warp); ok && t < prm.total_tiles; t = next_tile()) {
-    const Tile tl = decode_tile(prm, t);
-    const JobDesc& jd = prm.jobs[tl.job];
-    if (jd.cls != Cl::id) {
-      ok = false;
-      break;
-    }
-    const int H = jd.H;
-    const int nby = (jd.OH + P - 1) / P;
-    const int rb0 = tl.chunk * jd.rbc;
-    const int nblk = min(jd.rbc, nby - rb0);
-    const int ys = rb0 * Q + Cl::BMINV;  // first pattern row; < 0 only for the top band (then == BMINV)
-    const int nst = Cl::STG0 + ((nblk + Cl::VBLK) * Q + SR - 1) / SR;
-    const int ystream = ys + Cl::YOFF;  // frame row of stage 0's first row
-    const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;  // window start, in elements
-    const int xt = xw * Cl::SZ / kTmaElem;                          // ... in TMA elements (exact)
-    const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
-    const bool fixing = fix.nl + fix.nr > 0;
-    const int frame0 = tl.frame * Cl::FPW;              // the group's first frame
-    const int nf = Cl::FPW == 1 ? 1 : min(Cl::FPW, jd.nframes - frame0);  // frames in the group
-    const int sub = lane / Cl::LPS;                     // this lane's frame in the group
-    const int blk0 = tl.strip * Cl::SBLK + (lane % Cl::LPS) * Cl::NB;
-    const bool active = sub < nf && blk0 * Cl::P < jd.OW;
-    // elements this lane stores per output row (none for an inactive lane,
-    // which runs the same code on in-window data with its stores masked)
-    const int n_valid = active ? jd.OW * Cl::C - blk0 * Cl::P * Cl::C : 0;
-    T* const obase = reinterpret_cast<T*>(jd.out) + (long long)(frame0 + sub) * jd.out_frame +
-                     (long long)blk0 * Cl::P * Cl::C;
-    const long long rowe = (long long)jd.OW * Cl::C;
-
-    auto issue = [&](int s) {  // stage s of the tile into slot (g + s) mod NST
-      const uint32_t G = g + (uint32_t)s, slot = G % NST;
-      if constexpr (kCheckBounds) {  // frames of the job, window start on 16 bytes
-        if (frame0 < 0 || frame0 + nf > jd.nframes || (xt * kTmaElem) % 16 != 0) {
-          bounds_fail(4, (long long)xt * kTmaElem);
-          mbar_expect_tx(&full[slot], 0u);  // completes the phase with no copy
-          return;
-        }
-      }
-      mbar_expect_tx(&full[slot], (uint32_t)(nf * Cl::RTX));
-      for (int f = 0; f < nf; ++f)
-#pragma unroll
-        for (int bx = 0; bx < Cl::NBOX; ++bx)
-          tma_load_3d(ring + slot * Cl::RSTAGE + f * Cl::FSTR + bx * Cl::BOXSTR, &jd.tmap, &full[slot],
-                      xt + bx * Cl::BOXE, ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0), frame0 + f);
-    };
-    if (lane == 0)
-      for (int s = 0; s < NST && s < nst; ++s) issue(s);
-    issued = g + (uint32_t)min(NST, nst);
-    // wait for stage s; returns the stage's row-0 base, or nullptr on timeout.
-    // The stage's columns outside the frame get their border values (only
-    // tiles whose strip needs it)
-    auto stage_wait = [&](int s) -> uint8_t* {
-      const uint32_t G = g + (uint32_t)s, slot = G % NST;
-      if (!__all_sync(0xffffffffu, mbar_wait(&full[slot], (G / NST) & 1u))) return nullptr;
-      uint8_t* const sb = ring + slot * Cl::RSTAGE;
-      if (fixing) apply_edge_fix<Cl>(sb, fix, lane, jd.W, xw);
-      return sb;
-    };
-    // stage s fully read: refill its slot with stage s + NST
-    auto stage_release = [&](int s) {
-      __syncwarp();
-      if (s + NST < nst) {
-        if (lane == 0) issue(s + NST);
-        issued = g + (uint32_t)(s + NST + 1);
-      }
-    };
-    // H pass of one loaded row into a window row
-    // every vector a lane reads of a row lies in the warp's ring
-    auto row_ok = [&](const uint8_t* rowbase) -> bool {
-      if constexpr (kCheckBounds) {
-#pragma unroll
-        for (int v = 0; v < Cl::NVT; ++v) {
-          const long long off = (long long)(rowbase - ring) + of.v[v];
-          if (off < 0 || off + Cl::VB > Cl::WARP_BYTES) {
-            bounds_fail(1, off);
-            return false;
-          }
-        }
-      }
-      return true;
-    };
-    // the output rows of block rr this lane stores lie in its frame
-    auto store_ok = [&](int rr) -> bool {
-      if constexpr (kCheckBounds) {
-        if (n_valid > 0) {
-          const long long first = (long long)blk0 * Cl::P * Cl::C + (long long)rr * P * rowe;
-          const int last_row = min(rr * P + P, jd.OH) - 1 - rr * P;
-          const long long last = first + (long long)last_row * rowe + min(n_valid, Cl::NOUT) - 1;
-          if (first < 0 || last >= jd.out_frame || frame0 + sub >= jd.nframes) {
-            bounds_fail(3, first < 0 ? first : last);
-            return false;
-          }
-        }
-      }
-      return true;
-    };
-    auto hrow_regs = [&](uint8_t* rowbase, Row& o) {
-      if (!row_ok(rowbase)) return;
-      uint32_t w[Cl::NWT];
-      load_row<Cl>(rowbase, of, w);
-      RM::h(w, prm, o);
-    };
-
-    Row win[L];
-    // ---- prologue: pattern rows 0 .. L-Q-1 (with PRO: the lead blocks below)
-#pragma unroll
-    for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps) {
-      uint8_t* sb = stage_wait(ps);
-      if (!sb) {
-        ok = false;
-        break;
-      }
-#pragma unroll
-      for (int r = 0; r < SR; ++r) {
-        // pattern row index: stage 0 holds pattern rows 0.. (S0SHIFT), and
-        // its last EXTRA rows repeat rows of stage 1
-        const int i = ps == 0 ? r - Cl::EXTRA + Cl::S0SHIFT : ps * SR + r - Cl::EXTRA;
-        if (i < 0 || (ps == 0 && r >= SR - Cl::S0SHIFT)) continue;
-        const int y = ys + i;
-        if (y < 0) continue;                    // top band: filled from frame row 0 below
-        if (i > 0 && y >= H) {
-          RM::copy(win[i], win[i - 1]);
-        } else {
-          hrow_regs(sb + r * Cl::BOXB, win[i]);
-        }
-      }
-      stage_release(ps);
-    }
-    if (!ok) break;
-    // top band (ys == BMINV): slots 0..LHV-1 are frame row 0, held in slot LHV
-    auto top_fix = [&]() {
-      if (ys < 0) {
-#pragma unroll
-        for (int i = 0; i < Cl::LHV; ++i) RM::copy(win[i], win[Cl::LHV]);
-      }
-    };
-    if constexpr (!Cl::PRO) top_fix();
-    // ---- block steps, U rows (USTG stages, UBLK blocks) at a time.  A unit
-    // whose blocks are all inside the tile, whose rows are all above the
-    // frame's last row and whose output rows are all inside the frame, in a
-    // group with every frame present, runs a copy of the body without any of
-    // those checks.  Both copies fix up the border columns of each stage and
-    // mask the stores of lanes past the frame's right edge, so the left and
-    // right strips of a frame run the check-free copy too.  With PRO, blocks
-    // m < 0 are the lead blocks: their rows (those above frame row 0
-    // included, filtered from the zero fill and then overwritten) only fill
-    // the window.
-    auto unit = [&](auto fast, int u) {
-      constexpr bool FAST = decltype(fast)::value;
-#pragma unroll
-      for (int st = 0; st < Cl::USTG; ++st) {
-        const int s = Cl::STG0 + u * Cl::USTG + st;
-        if (!FAST && s >= nst) break;
-        uint8_t* sb = stage_wait(s);
-        if (!sb) {
-          ok = false;
-          return;
-        }
-#pragma unroll
-        for (int r = 0; r < SR; ++r) {
-          const int ru = st * SR + r;       // row within the unit
-          const int bq = ru / Q, q = ru - bq * Q;
-          const int m = u * Cl::UBLK + bq - Cl::VBLK;  // block step
-          if (FAST || m < nblk) {
-            const int i = L - Q + q;
-            if constexpr (FAST) {
-              uint32_t w[Cl::NWT];
-              if (row_ok(sb + r * Cl::BOXB)) load_row<Cl>(sb + r * Cl::BOXB, of, w);
-              RM::h(w, prm, win[i]);
-            } else {
-              // rows below the frame's last repeat it (filtered from the zero
-              // fill, then replaced: a select, not a branch)
-              const int y = ys + m * Q + i;
-              hrow_regs(sb + r * Cl::BOXB, win[i]);
-              if (y >= H) RM::copy(win[i], win[i - 1]);
-            }
-            if (q == Q - 1) {
-              // the window holds block m's pattern: its P output rows
-              if constexpr (FAST) {
-                if (store_ok(rb0 + m)) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
-              } else if (!Cl::PRO || m >= 0) {
-                if (store_ok(rb0 + m)) RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
-              }
-#pragma unroll
-              for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
-              if constexpr (!FAST && Cl::PRO)
-                if (m == -1) top_fix();
-            }
-          }
-        }
-        stage_release(s);
-      }
-    };
-    // every frame of the group present
-    const bool group_full = nf == Cl::FPW;
-    const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
-    for (int u = 0; ok && u < nunits; ++u) {
-      if constexpr (Cl::FASTPATH) {
-        const int mend = (u + 1) * Cl::UBLK - Cl::VBLK;  // one past the unit's last block
-        if (group_full && mend - Cl::UBLK >= 0 && mend <= nblk && ys + (mend - 1) * Q + L - 1 < H &&
-            (rb0 + mend) * P <= jd.OH) {
-          unit(std::true_type{}, u);
-          continue;
-        }
-      }
-      unit(std::false_type{}, u);
-    }
-    g += (uint32_t)nst;
-  }
-  if (!ok) {
-    // a wait gave up (or a job of the wrong class): record it and leave no
-    // copy in flight
-    if (lane == 0) {
-      atomicCAS(&g_fast_status, 0, kStatusTimeout);
-      for (uint32_t G = (issued > (uint32_t)NST ? issued - NST : 0); G < issued; ++G)
-        mbar_wait(&full[G % NST], (G / NST) & 1u);
-    }
-  }
-  // the last warp out resets the slot for its next launch
-  if (lane == 0) {
-    __threadfence();
-    if (atomicAdd(&g_warps_done[prm.sched_slot], 1u) == nwarps - 1) {
-      g_tile_next[prm.sched_slot] = 0;
-      g_warps_done[prm.sched_slot] = 0;
-      __threadfence();
-    }
-  }
-}
 
 // Exercise of the timeout path: one warp waits, with the kernels' bounded
 // wait, on an mbarrier that nothing will ever complete (no copy is issued
@@ -1141,7 +39,7 @@ __global__ void k_timeout_probe(long long limit) {
   }
   __syncwarp();
   const bool ok = __all_sync(0xffffffffu, mbar_wait(&bar, 0u, limit));
-  if (!ok && threadIdx.x == 0) atomicCAS(&g_fast_status, 0, kStatusTimeout);
+  if (!ok && threadIdx.x == 0) atomicCAS(&g_dev_state.status, 0, kStatusTimeout);
 }
 
 // Exercise of the bounds-check report (bounds-checking builds): one thread
@@ -1150,26 +48,47 @@ __global__ void k_timeout_probe(long long limit) {
 __global__ void k_bounds_probe() {
   if (threadIdx.x == 0) {
     const long long off = 64, size = 64;
-    if (off + 1 > size) bounds_fail(9, off);
+    if (off + 1 > size) bounds_fail(&g_dev_state, 9, off);
   }
 }
 
 // ---------------------------------------------------------------------------
-// host side
+// compiled classes and shapes
 // ---------------------------------------------------------------------------
-struct HostGeom {
-  int sblk, spx, p, q, pv, boxe, sr, sz, c, fpw;
-  CUtensorMapDataType dt;
-};
-
-template <class Cl>
-HostGeom host_geom() {
-  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW, kTmaType};
+const RowsTable& table() {
+  static RowsTable t = {};
+  static std::once_flag once;
+  std::call_once(once, [] {
+    register_f32(t);
+    register_f16(t);
+    register_u8rgb(t);
+    register_u8c1(t);
+    register_cif(t);
+  });
+  return t;
 }
 
-// Geometry of the kernel that runs class `cls`.
-HostGeom geom_of(int cls) {
-  return with_class(cls, [](auto tag) { return host_geom<typename decltype(tag)::type>(); });
+const RowsEntry& entry(int cls, int shape) {
+  const RowsEntry& e = table()[cls][shape >= 0 && shape < kShapes ? shape : 0];
+  return e.present ? e : table()[cls][0];
+}
+
+const RowsEntry& entry_of(const ds_plan* pl) { return entry(pl->fast_class, pl->shape); }
+
+// Device address of g_dev_state on the current device (the array's name is
+// only a host-side stand-in in host code), looked up once per device.
+DevState* dev_state() {
+  static DevState* addr[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_dev_state) != cudaSuccess) return nullptr;
+    addr[dev] = static_cast<DevState*>(p);
+  }
+  return addr[dev];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1185,28 +104,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-struct KernelInfo {
-  const void* fn;
-  int smem;
-  int threads;
-};
-
-// Registers are budgeted for Cl::MINB resident CTAs (of Cl::WPC warps) per SM.
-template <class Cl>
-KernelInfo rows_info(bool few) {
-  constexpr int smem = 128 + Cl::WPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  const void* fn = few ? reinterpret_cast<const void*>(&k_rows<Cl, Cl::WPC, Cl::MINB, kFewJobs>)
-                       : reinterpret_cast<const void*>(&k_rows<Cl, Cl::WPC, Cl::MINB, kMaxJobs>);
-  return KernelInfo{fn, smem, Cl::WPC * 32};
-}
-
-// The kernel that runs class `cls` (all jobs of a launch share the class)
-// with room for kFewJobs (few) or kMaxJobs job descriptors.
-KernelInfo kernel_for(int cls, bool few) {
-  return with_class(cls, [few](auto tag) { return rows_info<typename decltype(tag)::type>(few); });
-}
-
-// Occupancy per kernel, computed once per process (one device).
+// Resident CTAs per SM of a kernel, computed once per kernel (one device).
 int ctas_per_sm(const KernelInfo& ki) {
   static std::mutex mu;
   static std::vector<std::pair<const void*, int>> cache;
@@ -1299,7 +197,7 @@ const ClassTaps& class_taps(int cls) {
 // Tile geometry of a job (everything but the tensor map).  `band`: output
 // row blocks per tile, 0 = the plan's.
 void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, int band = 0) {
-  const HostGeom hg = geom_of(pl->fast_class);
+  const HostGeom& hg = entry_of(pl).geom;
   jd.out = out;
   jd.out_frame = (long long)pl->out_frame_elems();
   jd.H = pl->in_h;
@@ -1317,9 +215,23 @@ void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, 
   jd.out_vec = (((uintptr_t)out & 3u) == 0 && ((size_t)pl->out_w * pl->channels) % 4 == 0) ? 1 : 0;
 }
 
-ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
+// The tensor map of a job's input: 3-D (row bytes / 8 eight-byte elements, H
+// rows, n frames), boxes of the shape's strip window by its stage rows.
+// Plans keep the maps of their last few (input, frame count, shape) in a
+// small cache, so repeated launches on the same buffers skip the encode.
+ds_status job_tensor_map(const FastJob& job, CUtensorMap* out) {
   const ds_plan* pl = job.plan;
-  const HostGeom hg = geom_of(pl->fast_class);
+  TmapCache* tc = pl->tmaps.get();
+  if (tc) {
+    std::lock_guard<std::mutex> lock(tc->mu);
+    for (TmapCache::Entry& e : tc->e)
+      if (e.used && e.in == job.in && e.n_frames == job.n_frames && e.shape == pl->shape) {
+        e.stamp = ++tc->clock;
+        std::memcpy(out, &e.map, sizeof(CUtensorMap));
+        return DS_OK;
+      }
+  }
+  const HostGeom& hg = entry_of(pl).geom;
   auto enc = encode_fn();
   if (!enc) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -1330,14 +242,36 @@ ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
   cuuint64_t strides[2] = {row_bytes, row_bytes * (cuuint64_t)pl->in_h};
   cuuint32_t box[3] = {(cuuint32_t)hg.boxe, (cuuint32_t)hg.sr, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(&jd.tmap, hg.dt, 3, const_cast<void*>(job.in), dims, strides, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = enc(out, hg.dt, 3, const_cast<void*>(job.in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     set_error("cuTensorMapEncodeTiled failed (%d) for a %dx%d frame", (int)r, pl->in_h, pl->in_w);
     return DS_ERR_CUDA;
   }
-  fill_job_geometry(jd, pl, job.out, job.n_frames, band);
+  if (tc) {
+    std::lock_guard<std::mutex> lock(tc->mu);
+    TmapCache::Entry* victim = &tc->e[0];
+    for (TmapCache::Entry& e : tc->e) {
+      if (!e.used) {
+        victim = &e;
+        break;
+      }
+      if (e.stamp < victim->stamp) victim = &e;
+    }
+    victim->used = true;
+    victim->in = job.in;
+    victim->n_frames = job.n_frames;
+    victim->shape = pl->shape;
+    victim->stamp = ++tc->clock;
+    std::memcpy(&victim->map, out, sizeof(CUtensorMap));
+  }
+  return DS_OK;
+}
+
+ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
+  ds_status s = job_tensor_map(job, &jd.tmap);
+  if (s != DS_OK) return s;
+  fill_job_geometry(jd, job.plan, job.out, job.n_frames, band);
   return DS_OK;
 }
 
@@ -1346,11 +280,11 @@ ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
 // order, so:
 //  - a launch with fewer block rows of work than the GPU has pipelines
 //    finishes sooner with shorter bands: the band is cut to
-//    ceil(block rows / pipelines), never above the plans' own value;
+//    ceil(block rows / pipelines), never above the plans' own value (plans
+//    whose band the caller or the autotuner fixed keep theirs);
 //  - the launch ends when the last warp finishes its last tile, so the work
 //    at the end (about two tiles per pipeline) runs at a quarter of the band,
 //    the last job being split by frames where the boundary falls inside it.
-// Plans with a caller-set (or autotuned) schedule keep theirs, unsplit.
 struct BandedJob {
   FastJob job;
   int band;  // 0 = the plan's
@@ -1366,7 +300,7 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
   // units: block rows of one strip of a group of fpw frames (one warp's work per block step)
   auto geometry = [](const FastJob& j, long long& per_group, long long& groups, int& fpw) {
     const ds_plan* pl = j.plan;
-    const HostGeom hg = geom_of(pl->fast_class);
+    const HostGeom& hg = entry_of(pl).geom;
     const long long nbx = (pl->out_w + hg.p - 1) / hg.p, nby = (pl->out_h + hg.pv - 1) / hg.pv;
     fpw = hg.fpw;
     per_group = (nbx + hg.sblk - 1) / hg.sblk * nby;
@@ -1374,22 +308,18 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
   };
   long long units = 0;
   int cap = 0;
-  bool fixed = false;
   for (int i = 0; i < n; ++i) {
     long long pg = 0, ng = 0;
     int f = 1;
     geometry(jobs[i], pg, ng, f);
     units += pg * ng;
-    fixed = fixed || jobs[i].plan->schedule_set;
-    cap = std::max(cap, jobs[i].plan->row_blocks);
-  }
-  if (fixed) {
-    for (int i = 0; i < n; ++i) out[i] = BandedJob{jobs[i], 0};
-    return n;
+    if (!jobs[i].plan->schedule_set) cap = std::max(cap, jobs[i].plan->row_blocks);
   }
   pipelines = std::max(1, pipelines);
-  const int band = (int)std::max<long long>(1, std::min<long long>(cap, (units + pipelines - 1) / pipelines));
-  for (int i = 0; i < n; ++i) out[i] = BandedJob{jobs[i], band};
+  const int adaptive = (int)std::max<long long>(1, std::min<long long>(cap, (units + pipelines - 1) / pipelines));
+  for (int i = 0; i < n; ++i)
+    out[i] = BandedJob{jobs[i], jobs[i].plan->schedule_set ? std::max(1, jobs[i].plan->row_blocks) : adaptive};
+  const int band = out[n - 1].band;
   if (band < 4) return n;
   // walk back from the last job, giving each tail level its units (whole
   // jobs, or the last groups of a job split in two)
@@ -1404,7 +334,7 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
       geometry(out[i].job, pg, ng, f);
       const long long whole = pg * ng;
       if (acc + whole <= target || ng < 2) {
-        out[i].band = lband;
+        out[i].band = std::min(out[i].band, lband);
         acc += whole;
         --i;
         continue;
@@ -1414,14 +344,15 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
       // stays at the end); the head stays at index i for the next level
       const long long kg = std::min<long long>(ng - 1, (target - acc + pg - 1) / pg);
       const FastJob j = out[i].job;
+      const int head_band = out[i].band;
       size_t fin = 0, fout = 0;
       ds_plan_frame_bytes(j.plan, &fin, &fout);
       const int head = (int)(ng - kg) * f;
       for (int m = count; m > i + 1; --m) out[m] = out[m - 1];
-      out[i] = BandedJob{FastJob{j.plan, j.in, j.out, head}, band};
+      out[i] = BandedJob{FastJob{j.plan, j.in, j.out, head}, head_band};
       out[i + 1] = BandedJob{FastJob{j.plan, static_cast<const uint8_t*>(j.in) + (size_t)head * fin,
                                      static_cast<uint8_t*>(j.out) + (size_t)head * fout, j.n_frames - head},
-                             lband};
+                             std::min(head_band, lband)};
       ++count;
       acc = target;
     }
@@ -1429,161 +360,18 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
   return count;
 }
 
-// ---------------------------------------------------------------------------
-// host-side check of the kernel's index arithmetic
-// ---------------------------------------------------------------------------
-// Host-side walk of the row-streaming kernel over every tile of one frame:
-// TMA x coordinates are 16-byte aligned; every shared-memory read of the H
-// pass (vector chunks, halo words, clamped border pixels) stays inside the
-// loaded window and never straddles a box; the shared-memory footprint fits;
-// a replay of the stream and register-window logic on frame-row indices --
-// every V block must see exactly the clamped rows of its window, every
-// stream row must be the next frame row in order, every output element is
-// written once.
-template <class Cl, int WPC>
-std::string check_rows(const JobDesc& jd) {
-  char buf[256];
-  auto fail = [&](const char* what, int a, int b) {
-    std::snprintf(buf, sizeof(buf), "rows class %d: %s (%d, %d)", Cl::id, what, a, b);
-    return std::string(buf);
-  };
-  constexpr int smem = 128 + WPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  if (smem > 227 * 1024) return fail("shared memory above 227 KB", smem, 0);
-  if (Cl::BOXSTR < Cl::SRR * Cl::BOXB || Cl::BOXSTR % 128 != 0) return fail("stage layout", Cl::BOXSTR, 0);
-  if (Cl::LPS * Cl::FPW != 32) return fail("lanes per frame", Cl::LPS, Cl::FPW);
-  const int win = Cl::NBOX * Cl::BOXB;
-  // L, Q, P: the vertical axis; PH: the horizontal phases per packet
-  constexpr int L = Cl::LV, Q = Cl::QV, P = Cl::PV, PH = Cl::P;
-  std::vector<int> written((size_t)jd.OH * jd.OW * Cl::C, 0);
-  const int nby = (jd.OH + P - 1) / P;
-  for (int chunk = 0; chunk < jd.chunks; ++chunk) {
-    for (int strip = 0; strip < jd.strips; ++strip) {
-      const int rb0 = chunk * jd.rbc;
-      const int nblk = std::min(jd.rbc, nby - rb0);
-      if (nblk < 1) return fail("empty tile", chunk, strip);
-      const int ys = rb0 * Q + Cl::BMINV;
-      const int ye = (rb0 + nblk - 1) * Q + Cl::BMINV + L;
-      const int y0 = std::max(ys, 0), nrow = std::min(ye, jd.H) - y0;
-      if (nrow < 1) return fail("empty stream", ys, ye);
-      if (ys < 0 && ys != Cl::BMINV) return fail("top band offset", ys, 0);
-      const int xw = strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;
-      if ((xw * Cl::SZ) % kTmaElem != 0) return fail("window start not a whole TMA element", xw, 0);
-      for (int bx = 0; bx < Cl::NBOX; ++bx) {
-        const long long xb = (long long)(xw * Cl::SZ / kTmaElem + bx * Cl::BOXE) * kTmaElem;
-        if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", xw, bx);
-      }
-      const EdgeFix fx = edge_fix<Cl>(strip, jd.W);
-      for (int e = 0; e < fx.nl + fx.nr; ++e) {
-        const bool left = e < fx.nl;
-        const int k2 = left ? e : e - fx.nl;
-        const int px = (left ? fx.l_lo : fx.r_lo) + k2 / Cl::C, c = k2 % Cl::C;
-        const int src = (left ? 0 : jd.W - 1) * Cl::C + c - xw, dst = px * Cl::C + c - xw;
-        if (src < 0 || (src + 1) * Cl::SZ > win || dst < 0 || (dst + 1) * Cl::SZ > win)
-          return fail("edge fix outside the window", src, dst);
-      }
-      // every frame of a warp's group has the same window layout: lanes li of the strip
-      for (int lane = 0; lane < Cl::LPS; ++lane) {
-        const int first = Cl::HLB + lane * Cl::EB - Cl::HB * Cl::VB;
-        for (int v = 0; v < Cl::NVT; ++v) {
-          const int b0 = first + v * Cl::VB;
-          if (b0 < 0 || b0 + Cl::VB > win || b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB)
-            return fail("vector read", lane, b0);
-        }
-        const int blk0 = strip * Cl::SBLK + lane * Cl::NB, px0 = blk0 * Cl::Q;
-        if (blk0 * PH >= jd.OW) continue;
-        for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
-          if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lane, px);
-          if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lane, px);
-        }
-      }
-      // replay of the stream and window on frame-row indices: stage s holds
-      // frame rows ystream + s*SR .. + SR - 1
-      const int nst = Cl::STG0 + ((nblk + Cl::VBLK) * Q + Cl::SRR - 1) / Cl::SRR;
-      const int ystream = ys + Cl::YOFF;
-      int wrow[64];
-      int sr = 0;  // rows consumed from the stream, checked against their position
-      auto take = [&](int s, int r, int i) -> std::string {
-        if (s >= nst) return fail("stage beyond the tile", s, nst);
-        wrow[i] = ystream + s * Cl::SRR + r + (s == 0 ? Cl::S0SHIFT : 0);
-        ++sr;
-        return std::string();
-      };
-      for (int ps = 0; ps < (Cl::PRO ? 0 : Cl::NPS); ++ps)
-        for (int r = 0; r < Cl::SRR; ++r) {
-          const int i = ps == 0 ? r - Cl::EXTRA + Cl::S0SHIFT : ps * Cl::SRR + r - Cl::EXTRA;
-          if (i < 0 || (ps == 0 && r >= Cl::SRR - Cl::S0SHIFT)) continue;
-          const int y = ys + i;
-          if (y < 0) continue;
-          if (i > 0 && y >= jd.H) { wrow[i] = wrow[i - 1]; continue; }
-          std::string e = take(ps, r, i);
-          if (!e.empty()) return e;
-          if (wrow[i] != y) return fail("prologue row mismatch", i, wrow[i]);
-        }
-      if (ys < 0 && !Cl::PRO)
-        for (int i = 0; i < Cl::LHV; ++i) wrow[i] = wrow[Cl::LHV];
-      const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
-      for (int u = 0; u < nunits; ++u)
-        for (int st = 0; st < Cl::USTG; ++st) {
-          const int s = Cl::STG0 + u * Cl::USTG + st;
-          if (s >= nst) break;
-          for (int r = 0; r < Cl::SRR; ++r) {
-            const int ru = st * Cl::SRR + r, bq = ru / Q, q = ru - bq * Q, m = u * Cl::UBLK + bq - Cl::VBLK;
-            if (m >= nblk) continue;
-            const int i = L - Q + q, y = ys + m * Q + i;
-            if (y >= jd.H) wrow[i] = wrow[i - 1];
-            else {
-              std::string e = take(s, r, i);
-              if (!e.empty()) return e;
-              if (wrow[i] != y) return fail("stream row mismatch", i, wrow[i]);
-            }
-            if (q != Q - 1) continue;
-            if (m < 0) {  // a lead block: no outputs, the window moves on
-              for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
-              if (m == -1 && ys < 0)
-                for (int i2 = 0; i2 < Cl::LHV; ++i2) wrow[i2] = wrow[Cl::LHV];
-              continue;
-            }
-            const int rr = rb0 + m;
-            for (int i2 = 0; i2 < L; ++i2) {
-              int want = rr * Q + Cl::BMINV + i2;
-              want = want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want);
-              if (wrow[i2] != want) return fail("window row mismatch", i2, wrow[i2]);
-            }
-            for (int lane = 0; lane < Cl::LPS; ++lane) {
-              const int blk0 = strip * Cl::SBLK + lane * Cl::NB;
-              if (blk0 * PH >= jd.OW) continue;
-              const int nv = std::min(Cl::NOUT, jd.OW * Cl::C - blk0 * PH * Cl::C);
-              for (int jv = 0; jv < P; ++jv) {
-                const int oy = rr * P + jv;
-                if (oy >= jd.OH) continue;
-                for (int k = 0; k < nv; ++k) written[((size_t)oy * jd.OW) * Cl::C + (size_t)blk0 * PH * Cl::C + k]++;
-              }
-            }
-            for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
-          }
-        }
-      // with lead blocks every stream row above the frame's end is filtered (those above row 0 too)
-      const int want_rows = Cl::PRO ? std::min(ye, jd.H) - ystream : nrow;
-      if (sr != want_rows) return fail("stream rows left over", sr, want_rows);
-    }
-  }
-  for (size_t i = 0; i < written.size(); ++i)
-    if (written[i] != 1) return fail("output element written != 1 times", (int)i, written[i]);
-  return std::string();
-}
-
 std::string check_plan(const ds_plan* pl) {
   if (pl->fast_class < 0 || pl->fast_class >= kFcCount) return std::string();
   JobDesc jd;
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);
-  return with_class(pl->fast_class, [&jd](auto tag) {
-    using Cl = typename decltype(tag)::type;
-    return check_rows<Cl, Cl::WPC>(jd);
-  });
+  return entry_of(pl).check(jd);
 }
 
-// Scheduling slots owned by live graphs.
+// ---------------------------------------------------------------------------
+// scheduling slots
+// ---------------------------------------------------------------------------
+// Slots owned by live graphs.
 std::mutex g_slot_mu;
 bool g_slot_used[kSchedSlots - kGraphSlot0] = {};
 
@@ -1595,6 +383,68 @@ int take_graph_slot() {
       return kGraphSlot0 + i;
     }
   return -1;
+}
+
+// Slots of direct launches, per device: each slot's counters serve one launch
+// at a time.  A launch takes a slot whose last launch has completed (its
+// event, recorded on the launch's stream right after it, has fired) and that
+// no other host thread is launching on right now; when every slot is busy
+// the host waits for the oldest one.
+struct DirectSlots {
+  std::mutex mu;
+  cudaEvent_t ev[kGraphSlot0] = {};
+  bool pending[kGraphSlot0] = {};
+  int next = 0;
+};
+
+DirectSlots* direct_slots() {
+  static DirectSlots* per_dev[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!per_dev[dev]) per_dev[dev] = new (std::nothrow) DirectSlots();  // held until the process exits
+  return per_dev[dev];
+}
+
+ds_status take_direct_slot(DirectSlots* ds_, int* slot) {
+  for (;;) {
+    cudaEvent_t wait_on = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(ds_->mu);
+      for (int k = 0; k < kGraphSlot0; ++k) {
+        const int s = (ds_->next + k) % kGraphSlot0;
+        if (ds_->pending[s]) continue;
+        if (!ds_->ev[s]) {
+          cudaError_t e = cudaEventCreateWithFlags(&ds_->ev[s], cudaEventDisableTiming);
+          if (e != cudaSuccess) return cuda_fail(e, "k_rows: slot event");
+        } else {
+          cudaError_t q = cudaEventQuery(ds_->ev[s]);
+          if (q == cudaErrorNotReady) continue;
+          if (q != cudaSuccess) return cuda_fail(q, "k_rows: slot event query");
+        }
+        ds_->pending[s] = true;
+        ds_->next = (s + 1) % kGraphSlot0;
+        *slot = s;
+        return DS_OK;
+      }
+      // every slot is busy: wait for the one that comes next in turn
+      const int s = ds_->next;
+      if (!ds_->pending[s]) wait_on = ds_->ev[s];
+    }
+    if (wait_on) {
+      cudaError_t e = cudaEventSynchronize(wait_on);
+      if (e != cudaSuccess) return cuda_fail(e, "k_rows: waiting for a scheduling slot");
+    } else {
+      std::this_thread::yield();
+    }
+  }
+}
+
+void give_direct_slot(DirectSlots* ds_, int slot, cudaStream_t st, bool launched) {
+  std::lock_guard<std::mutex> lock(ds_->mu);
+  if (launched) cudaEventRecord(ds_->ev[slot], st);
+  ds_->pending[slot] = false;
 }
 
 // Fill the launch parameters and launch.
@@ -1613,6 +463,9 @@ ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, cons
   prm.n_jobs = nb;
   prm.total_tiles = tiles;
   if (tiles == 0) return DS_OK;
+  prm.dev = dev_state();
+  if (!prm.dev) return cuda_fail(cudaGetLastError(), "k_rows: device state address");
+  DirectSlots* direct = nullptr;
   if (g_capture_slots) {
     const int slot = take_graph_slot();
     if (slot < 0) {
@@ -1622,51 +475,93 @@ ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, cons
     g_capture_slots->push_back(slot);
     prm.sched_slot = slot;
   } else {
-    static std::atomic<unsigned> slot_counter{0};
-    prm.sched_slot = (int)(slot_counter.fetch_add(1) % kGraphSlot0);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      set_error("fused launch inside a stream capture the library did not start: capture with ds_graph_create, "
+                "which gives each captured launch a scheduling slot of its own");
+      return DS_ERR_UNSUPPORTED;
+    }
+    direct = direct_slots();
+    if (!direct) {
+      set_error("k_rows: no scheduling slots for this device");
+      return DS_ERR_UNSUPPORTED;
+    }
+    ds_status s = take_direct_slot(direct, &prm.sched_slot);
+    if (s != DS_OK) return s;
   }
   const int grid = std::min((tiles + per_cta - 1) / per_cta, sm_count() * occ);
   log_msg(2, "k_rows class %d: %d jobs, %d tiles, grid %d x %d threads, %d B shared, slot %d", cls, nb, tiles, grid,
           ki.threads, ki.smem, prm.sched_slot);
   void* args[] = {&prm};
   cudaError_t e = cudaLaunchKernel(ki.fn, dim3(grid), dim3(ki.threads), args, (size_t)ki.smem, st);
+  if (direct) give_direct_slot(direct, prm.sched_slot, st, e == cudaSuccess);
   if (e != cudaSuccess) return cuda_fail(e, "k_rows launch");
   count_launches(1);
   return DS_OK;
 }
 
 ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
-  // launch_fast groups jobs by class and tap table: a plan with given taps
-  // launches with its own tables, every other plan with its class's
-  const int cls = jobs[0].plan->fast_class;
+  // launch_fast groups jobs by class, tile shape and tap table: a plan with
+  // given taps launches with its own tables, every other plan with its class's
+  const ds_plan* pl0 = jobs[0].plan;
+  const int cls = pl0->fast_class;
   static thread_local ClassTaps given;
-  if (jobs[0].plan->given_taps) plan_taps(jobs[0].plan, given);
-  const ClassTaps& taps = jobs[0].plan->given_taps ? given : class_taps(cls);
-  int want_ctas = jobs[0].plan->ctas_per_sm;
+  if (pl0->given_taps) plan_taps(pl0, given);
+  const ClassTaps& taps = pl0->given_taps ? given : class_taps(cls);
+  int want_ctas = pl0->ctas_per_sm;
   for (int i = 0; i < n; ++i) want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
-  // both instantiations of a class have the same shape and occupancy
-  const KernelInfo big = kernel_for(cls, false);
-  int occ = ctas_per_sm(big);
+  // both instantiations of a class and shape have the same footprint and occupancy
+  const RowsEntry& re = entry_of(pl0);
+  int occ = ctas_per_sm(re.many);
   if (occ <= 0) {
-    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", big.smem);
+    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", re.many.smem);
     return DS_ERR_UNSUPPORTED;
   }
   if (want_ctas > 0) occ = std::min(occ, want_ctas);
   BandedJob banded[kMaxJobs];
-  const int nb = plan_bands(jobs, n, sm_count() * occ * (big.threads / 32), banded);
+  const int nb = plan_bands(jobs, n, sm_count() * occ * (re.many.threads / 32), banded);
   if (nb <= kFewJobs) {
     static thread_local FastParams<kFewJobs> few;
-    const KernelInfo ki = kernel_for(cls, true);
-    if (ctas_per_sm(ki) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
-    return launch_with(few, ki, cls, taps, banded, nb, occ, st);
+    if (ctas_per_sm(re.few) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
+    return launch_with(few, re.few, cls, taps, banded, nb, occ, st);
   }
   static thread_local FastParams<kMaxJobs> many;  // ~17 KB: not on the caller's stack
-  return launch_with(many, big, cls, taps, banded, nb, occ, st);
+  return launch_with(many, re.many, cls, taps, banded, nb, occ, st);
 }
 
 }  // namespace
+}  // namespace rows
+
+using namespace rows;
 
 int fast_max_jobs_per_launch() { return kMaxJobs; }
+
+int fast_tile_shapes(int cls) {
+  if (cls < 0 || cls >= kFcCount) return 0;
+  int n = 0;
+  for (int s = 0; s < kShapes; ++s)
+    if (table()[cls][s].present) n = s + 1;
+  return n;
+}
+
+bool fast_shape_info(int cls, int shape, FastShapeInfo* out) {
+  if (cls < 0 || cls >= kFcCount || shape < 0 || shape >= fast_tile_shapes(cls)) return false;
+  const RowsEntry& e = table()[cls][shape];
+  out->packets_per_lane = e.nb;
+  out->stage_rows = e.sr;
+  out->stages = e.nst;
+  out->warps_per_cta = e.wpc;
+  out->ctas_per_sm_budget = e.minb;
+  out->strip_pixels = e.geom.spx;
+  out->frames_per_warp = e.geom.fpw;
+  out->smem_per_cta = e.many.smem;
+  return true;
+}
+
+int fast_ctas_per_sm(const ds_plan* pl) {
+  if (pl->fast_class < 0) return 0;
+  return ctas_per_sm(entry_of(pl).many);
+}
 
 thread_local std::vector<int>* g_capture_slots = nullptr;
 
@@ -1676,35 +571,50 @@ void release_graph_slots(const std::vector<int>& slots) {
     if (s >= kGraphSlot0 && s < kSchedSlots) g_slot_used[s - kGraphSlot0] = false;
 }
 
-// One launch per class present (each kernel is specialised for its class),
-// at most kMaxJobs descriptors per launch.
+// One launch per class and tile shape present (each kernel is specialised
+// for its class), at most kMaxJobs descriptors per launch.
 ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
-  // one group per class for the plans with the library's taps, one per plan
-  // with given taps (its own tap tables)
-  std::vector<FastJob> group;
-  auto launch_group = [&]() -> ds_status {
-    for (size_t i = 0; i < group.size(); i += kMaxJobs) {
-      ds_status s = launch_chunk(group.data() + i, (int)std::min<size_t>(kMaxJobs, group.size() - i), st);
+  // one group per (class, shape) for the plans with the library's taps, one
+  // per plan with given taps (its own tap tables)
+  FastJob group[kMaxJobs];
+  int ng = 0;
+  auto flush = [&]() -> ds_status {
+    ds_status s = ng > 0 ? launch_chunk(group, ng, st) : DS_OK;
+    ng = 0;
+    return s;
+  };
+  auto add = [&](const FastJob& j) -> ds_status {
+    group[ng++] = j;
+    return ng == kMaxJobs ? flush() : DS_OK;
+  };
+  if (n == 1) {  // the common single-job case: no grouping
+    ds_status s = add(jobs[0]);
+    return s != DS_OK ? s : flush();
+  }
+  for (int cls = 0; cls < kFcCount; ++cls)
+    for (int shape = 0; shape < kShapes; ++shape) {
+      for (int i = 0; i < n; ++i) {
+        const ds_plan* pl = jobs[i].plan;
+        if (pl->fast_class == cls && pl->shape == shape && !pl->given_taps) {
+          ds_status s = add(jobs[i]);
+          if (s != DS_OK) return s;
+        }
+      }
+      ds_status s = flush();
       if (s != DS_OK) return s;
     }
-    return DS_OK;
-  };
-  for (int cls = 0; cls < kFcCount; ++cls) {
-    group.clear();
-    for (int i = 0; i < n; ++i)
-      if (jobs[i].plan->fast_class == cls && !jobs[i].plan->given_taps) group.push_back(jobs[i]);
-    ds_status s = launch_group();
-    if (s != DS_OK) return s;
-  }
-  std::vector<const ds_plan*> done;
   for (int i = 0; i < n; ++i) {
     const ds_plan* pl = jobs[i].plan;
-    if (!pl->given_taps || std::find(done.begin(), done.end(), pl) != done.end()) continue;
-    done.push_back(pl);
-    group.clear();
+    if (!pl->given_taps) continue;
+    bool seen = false;
+    for (int k = 0; k < i && !seen; ++k) seen = jobs[k].plan == pl;
+    if (seen) continue;
     for (int k = i; k < n; ++k)
-      if (jobs[k].plan == pl) group.push_back(jobs[k]);
-    ds_status s = launch_group();
+      if (jobs[k].plan == pl) {
+        ds_status s = add(jobs[k]);
+        if (s != DS_OK) return s;
+      }
+    ds_status s = flush();
     if (s != DS_OK) return s;
   }
   return DS_OK;
@@ -1733,22 +643,24 @@ ds_status debug_check_plan(const ds_plan* pl, std::string& msg) {
   return msg.empty() ? DS_OK : DS_ERR_ARG;
 }
 
+// The status word and, after a failed bounds check, its record; the word is
+// cleared by the read.  The scheduling counters need no reset here: every
+// warp of a launch, one that gave up a wait included, reaches the end of the
+// kernel, where the last one out resets its slot.
 ds_status read_device_status(int* status, long long* info) {
+  DevState* dev = dev_state();
+  if (!dev) return cuda_fail(cudaGetLastError(), "device state address");
   int v = 0, zero = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(&v, g_fast_status, sizeof(int));
+  cudaError_t e = cudaMemcpy(&v, &dev->status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
   info[0] = info[1] = 0;
   if (v == kStatusBounds) {
-    e = cudaMemcpyFromSymbol(info, g_bounds_info, 2 * sizeof(long long));
+    e = cudaMemcpy(info, dev->bounds_info, 2 * sizeof(long long), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "reading the bounds-check record");
   }
   if (v != 0) {
-    e = cudaMemcpyToSymbol(g_fast_status, &zero, sizeof(int));
+    e = cudaMemcpy(&dev->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "clearing the device status word");
-    // a kernel that gave up may have left its scheduling slot unreset
-    static const unsigned zeros[kSchedSlots] = {};
-    cudaMemcpyToSymbol(g_tile_next, zeros, sizeof(zeros));
-    cudaMemcpyToSymbol(g_warps_done, zeros, sizeof(zeros));
   }
   *status = v;
   return DS_OK;

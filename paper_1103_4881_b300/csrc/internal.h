@@ -6,6 +6,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -39,6 +40,22 @@ enum FastClass : int {
   kFcCount
 };
 
+// The last few tensor maps a plan's launches used, keyed by input pointer,
+// frame count and tile shape (a plan is immutable but its launches may come
+// from several host threads at once: the cache has its own lock).
+struct TmapCache {
+  struct Entry {
+    alignas(64) CUtensorMap map;
+    const void* in = nullptr;
+    int n_frames = 0, shape = 0;
+    bool used = false;
+    unsigned long long stamp = 0;
+  };
+  std::mutex mu;
+  Entry e[8];
+  unsigned long long clock = 0;
+};
+
 }  // namespace ds
 
 struct ds_plan {
@@ -64,8 +81,11 @@ struct ds_plan {
   int ctas_per_sm = 0;                       // persistent grid: 0 = occupancy
   bool schedule_set = false;                 // row_blocks fixed by the caller or the autotuner;
                                              // else a launch too small to fill the GPU uses
-                                             // shorter bands (more tiles)
+                                             // shorter bands (more tiles).  Either way the
+                                             // launch's last tiles run at a quarter band
+  int shape = 0;                             // compiled tile shape of the fast class
   bool force_general = false;                // DS_NO_TMA or unsupported alignment
+  std::unique_ptr<ds::TmapCache> tmaps;      // fast plans: recent tensor maps
 
   size_t in_frame_elems() const { return (size_t)in_h * in_w * channels; }
   size_t out_frame_elems() const { return (size_t)out_h * out_w * channels; }
@@ -104,6 +124,15 @@ ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t stream);
 extern thread_local std::vector<int>* g_capture_slots;
 void release_graph_slots(const std::vector<int>& slots);
 int fast_max_jobs_per_launch();
+// Tile shapes compiled for fast class `cls` (0 for none), what shape `shape`
+// is, and the resident CTAs per SM of a plan's kernel at its current shape.
+struct FastShapeInfo {
+  int packets_per_lane, stage_rows, stages, warps_per_cta, ctas_per_sm_budget;
+  int strip_pixels, frames_per_warp, smem_per_cta;
+};
+int fast_tile_shapes(int cls);
+bool fast_shape_info(int cls, int shape, FastShapeInfo* out);
+int fast_ctas_per_sm(const ds_plan* plan);
 // reads and clears the status word (1: a wait gave up, 3: a bounds check
 // failed, with kind and offset in info)
 ds_status read_device_status(int* status, long long* info);

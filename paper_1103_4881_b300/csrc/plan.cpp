@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 
 #include "internal.h"
@@ -137,6 +138,11 @@ int default_row_blocks(int fast_class) {
     case kFcU8C1_23: return 20;
     default: return 0;
   }
+}
+
+int default_band(int fast_class) {
+  const int b = default_row_blocks(fast_class);
+  return b > 0 ? b : 8;
 }
 }  // namespace
 
@@ -292,8 +298,10 @@ ds_plan* create_plan(const ds_plan_desc& d, const char* who) {
   // launch)
   pl->fast_class = (d.boundary == DS_CLAMP)
                        ? fast_class_of(pl->p, pl->q, pl->K, pl->pv, pl->qv, pl->Kv, d.dtype) : kFcNone;
-  pl->row_blocks = default_row_blocks(pl->fast_class);
-  if (pl->row_blocks == 0) pl->row_blocks = 8;
+  pl->row_blocks = default_band(pl->fast_class);
+  if (pl->fast_class >= 0) {
+    pl->tmaps.reset(new (std::nothrow) TmapCache());  // without it every launch encodes its maps
+  }
   const char* no_tma = std::getenv("DS_NO_TMA");
   pl->force_general = (no_tma && no_tma[0] && no_tma[0] != '0');
   log_msg(1, "plan %dx%dx%d dtype %d: h %d/%d K%d, v %d/%d K%d, %s%s -> %s (class %d, band %d)", pl->in_h,
@@ -420,6 +428,35 @@ ds_status ds_plan_get_schedule(const ds_plan* pl, int* row_blocks, int* ctas_per
   return DS_OK;
 }
 
+int ds_plan_tile_shapes(const ds_plan* pl) {
+  if (!pl || pl->fast_class < 0) return 0;
+  return fast_tile_shapes(pl->fast_class);
+}
+
+ds_status ds_plan_set_schedule_ex(ds_plan* pl, const ds_schedule* sc) {
+  if (!pl || !sc || sc->row_blocks < 0 || sc->ctas_per_sm < 0 || sc->shape < 0 ||
+      sc->shape >= std::max(1, ds_plan_tile_shapes(pl))) {
+    set_error("ds_plan_set_schedule_ex: bad arguments (shape must be below ds_plan_tile_shapes)");
+    return DS_ERR_ARG;
+  }
+  pl->schedule_set = sc->row_blocks > 0;
+  pl->row_blocks = sc->row_blocks > 0 ? sc->row_blocks : default_band(pl->fast_class);
+  pl->ctas_per_sm = sc->ctas_per_sm;
+  pl->shape = sc->shape;
+  return DS_OK;
+}
+
+ds_status ds_plan_get_schedule_ex(const ds_plan* pl, ds_schedule* sc) {
+  if (!pl || !sc) {
+    set_error("ds_plan_get_schedule_ex: NULL argument");
+    return DS_ERR_ARG;
+  }
+  sc->row_blocks = pl->schedule_set ? pl->row_blocks : 0;
+  sc->ctas_per_sm = pl->ctas_per_sm;
+  sc->shape = pl->shape;
+  return DS_OK;
+}
+
 ds_status ds_plan_describe(const ds_plan* pl, char* buf, size_t len) {
   if (!pl || !buf || len == 0) {
     set_error("ds_plan_describe: bad arguments");
@@ -430,14 +467,25 @@ ds_status ds_plan_describe(const ds_plan* pl, char* buf, size_t len) {
                                 "u8rgb_h3_8_v4_9_k8", "u8_h3_8_v4_9_k8", "u8_3_8_k8", "u8_1_2_k6", "u8_2_3_k6"};
   static_assert(sizeof(names) / sizeof(names[0]) == kFcCount, "a name per fast class");
   const bool fast = pl->fast_class >= 0 && !pl->force_general;
+  FastShapeInfo si{};
+  char shape[256] = "null";
+  if (pl->fast_class >= 0 && fast_shape_info(pl->fast_class, pl->shape, &si))
+    std::snprintf(shape, sizeof(shape),
+                  "{\"index\": %d, \"of\": %d, \"packets_per_lane\": %d, \"strip_pixels\": %d, "
+                  "\"frames_per_warp\": %d, \"stage_rows\": %d, \"stages\": %d, \"warps_per_cta\": %d, "
+                  "\"ctas_per_sm_budget\": %d, \"smem_per_cta\": %d}",
+                  pl->shape, fast_tile_shapes(pl->fast_class), si.packets_per_lane, si.strip_pixels,
+                  si.frames_per_warp, si.stage_rows, si.stages, si.warps_per_cta, si.ctas_per_sm_budget,
+                  si.smem_per_cta);
   std::snprintf(buf, len,
                 "{\"kernel\": \"%s\", \"class\": \"%s\", \"in\": [%d, %d, %d], \"out\": [%d, %d, %d], "
                 "\"ratio\": [%d, %d], \"taps\": %d, \"ratio_v\": [%d, %d], \"taps_v\": %d, "
-                "\"boundary\": \"%s\", \"given_taps\": %s, \"row_blocks\": %d, \"ctas_per_sm\": %d}",
+                "\"boundary\": \"%s\", \"given_taps\": %s, \"row_blocks\": %d, \"band\": \"%s\", "
+                "\"ctas_per_sm\": %d, \"tile_shape\": %s}",
                 fast ? "fused_tma" : "fused_general", pl->fast_class >= 0 ? names[pl->fast_class] : "general",
                 pl->in_h, pl->in_w, pl->channels, pl->out_h, pl->out_w, pl->channels, pl->p, pl->q, pl->K, pl->pv,
                 pl->qv, pl->Kv, pl->boundary == DS_WRAP ? "wrap" : "clamp", pl->given_taps ? "true" : "false",
-                pl->row_blocks, pl->ctas_per_sm);
+                pl->row_blocks, pl->schedule_set ? "fixed" : "adaptive", pl->ctas_per_sm, shape);
   return DS_OK;
 }
 

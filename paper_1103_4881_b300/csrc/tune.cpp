@@ -1,12 +1,16 @@
-// tune.cpp -- autotuner of the fused kernel's tile schedule.
+// tune.cpp -- autotuner of the fused kernel's launch topology.
 //
 // The paper derives the launch topology of each repetitive task from its
 // multiplicity with fixed threshold levels (Sec. 3.B.1, "Launch Topology").
-// Here the topology is measured instead: every candidate band height (output
-// row blocks per tile) is timed on the caller's buffers with CUDA events and
-// the fastest is kept in the plan.  Every candidate computes the same bits
-// (the per-output accumulation order does not depend on the tiling), so the
-// choice only moves time.
+// Here it is measured instead, on the caller's buffers with CUDA events:
+//   1. every compiled tile shape of the plan's class, at the default band;
+//   2. at the best shape, fixed band heights (output row blocks per tile) up
+//      to the plan's block rows, against the default adaptive band;
+//   3. at the best shape and band, fewer resident CTAs per SM than fit.
+// The default schedule (shape 0, adaptive band, full occupancy) is always a
+// candidate, so the tuned schedule is never slower than it as measured here.
+// Every candidate computes the same bits (the per-output accumulation order
+// does not depend on the tiling), so the choice only moves time.
 #include <algorithm>
 #include <vector>
 
@@ -14,64 +18,116 @@
 
 using namespace ds;
 
+namespace {
+
+// Time `iters` launches of the plan's current schedule after one warm-up, in
+// microseconds per launch.
+ds_status time_schedule(ds_plan* plan, const void* in, void* out, int n_frames, cudaStream_t st, int iters,
+                        cudaEvent_t e0, cudaEvent_t e1, float* us) {
+  ds_status s = ds_run_frames(plan, in, out, n_frames, st);
+  if (s != DS_OK) return s;
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < iters && s == DS_OK; ++i) s = ds_run_frames(plan, in, out, n_frames, st);
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (s != DS_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "ds_plan_autotune: timing");
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  *us = ms * 1000.0f / iters;
+  return DS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
-ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frames, void* stream, int iters,
-                           int* best_row_blocks, float* best_us) {
+ds_status ds_plan_autotune_ex(ds_plan* plan, const void* in, void* out, int n_frames, void* stream, int iters,
+                              ds_tune_result* res) {
   clear_error();
   if (!plan || !in || !out || n_frames < 1 || iters < 1) {
     set_error("ds_plan_autotune: bad arguments");
     return DS_ERR_ARG;
   }
-  const int nby = (plan->out_h + plan->p - 1) / plan->p;
-  std::vector<int> cand;
-  for (int c : {3, 4, 6, 8, 10, 12, 16, 20, 24, 34, 48, 64})
-    if (c <= nby) cand.push_back(c);
-  if (cand.empty() || cand.back() < nby) cand.push_back(std::min(nby, 96));
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     if (e0) cudaEventDestroy(e0);
     return cuda_fail(cudaGetLastError(), "ds_plan_autotune: events");
   }
-  const int keep_rb = plan->row_blocks, keep_ctas = plan->ctas_per_sm;
-  const bool keep_set = plan->schedule_set;
-  plan->schedule_set = true;  // time each candidate as given
-  int best = keep_rb;
-  float best_t = 1e30f;
+  ds_schedule keep{};
+  ds_plan_get_schedule_ex(plan, &keep);
+  ds_schedule best{0, 0, 0};
+  float best_us = 1e30f, default_us = 0.0f;
+  int tried = 0;
   ds_status s = DS_OK;
-  for (int c : cand) {
-    plan->row_blocks = c;
-    s = ds_run_frames(plan, in, out, n_frames, stream);  // warm-up
-    if (s != DS_OK) break;
-    cudaEventRecord(e0, st);
-    for (int i = 0; i < iters && s == DS_OK; ++i) s = ds_run_frames(plan, in, out, n_frames, stream);
-    cudaEventRecord(e1, st);
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (s != DS_OK) break;
-    if (e != cudaSuccess) {
-      s = cuda_fail(e, "ds_plan_autotune: timing");
-      break;
-    }
-    float ms = 0.0f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_t) {
-      best_t = ms;
+  auto trial = [&](const ds_schedule& c) -> ds_status {
+    ds_status r = ds_plan_set_schedule_ex(plan, &c);
+    if (r != DS_OK) return r;
+    float us = 0.0f;
+    r = time_schedule(plan, in, out, n_frames, st, iters, e0, e1, &us);
+    if (r != DS_OK) return r;
+    ++tried;
+    if (c.row_blocks == 0 && c.ctas_per_sm == 0 && c.shape == 0) default_us = us;
+    if (us < best_us) {
+      best_us = us;
       best = c;
+    }
+    return DS_OK;
+  };
+  // 1. tile shapes at the default band (shape 0 first: the default schedule)
+  const int shapes = std::max(1, ds_plan_tile_shapes(plan));
+  for (int sh = 0; sh < shapes && s == DS_OK; ++sh) s = trial(ds_schedule{0, 0, sh});
+  if (plan->fast_class >= 0) {
+    // 2. fixed bands at the best shape, up to the plan's block rows (vertical axis)
+    const int nby = (plan->out_h + plan->pv - 1) / plan->pv;
+    std::vector<int> bands;
+    for (int c : {2, 3, 4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64})
+      if (c <= nby) bands.push_back(c);
+    if (bands.empty() || bands.back() < nby) bands.push_back(std::min(nby, 96));
+    const int shape = best.shape;
+    for (int b : bands) {
+      if (s != DS_OK) break;
+      s = trial(ds_schedule{b, 0, shape});
+    }
+    // 3. fewer resident CTAs per SM at the best shape and band
+    if (s == DS_OK) {
+      ds_schedule at{best.row_blocks, 0, best.shape};
+      ds_plan_set_schedule_ex(plan, &at);
+      const int occ = fast_ctas_per_sm(plan);
+      std::vector<int> ctas;
+      for (int c : {occ - 1, occ - 2, (occ * 3) / 4, occ / 2})
+        if (c >= 1 && c < occ && std::find(ctas.begin(), ctas.end(), c) == ctas.end()) ctas.push_back(c);
+      const ds_schedule base = best;
+      for (int c : ctas) {
+        if (s != DS_OK) break;
+        s = trial(ds_schedule{base.row_blocks, c, base.shape});
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  plan->ctas_per_sm = keep_ctas;
   if (s != DS_OK) {
-    plan->row_blocks = keep_rb;
-    plan->schedule_set = keep_set;
+    ds_plan_set_schedule_ex(plan, &keep);
     return s;
   }
-  plan->row_blocks = best;
-  plan->schedule_set = true;
-  if (best_row_blocks) *best_row_blocks = best;
-  if (best_us) *best_us = best_t * 1000.0f / iters;
+  ds_plan_set_schedule_ex(plan, &best);
+  if (res) {
+    res->best = best;
+    res->best_us = best_us;
+    res->default_us = default_us;
+    res->candidates = tried;
+  }
+  return DS_OK;
+}
+
+ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frames, void* stream, int iters,
+                           int* best_row_blocks, float* best_us) {
+  ds_tune_result r{};
+  ds_status s = ds_plan_autotune_ex(plan, in, out, n_frames, stream, iters, &r);
+  if (s != DS_OK) return s;
+  if (best_row_blocks) *best_row_blocks = plan->row_blocks;
+  if (best_us) *best_us = r.best_us;
   return DS_OK;
 }
 

@@ -8,6 +8,8 @@ benchmark and the CPU oracle all see the same pixels).
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass
 
 import numpy as np
@@ -118,10 +120,21 @@ def frame(w: Workload, i: int) -> np.ndarray:
     raise ValueError(w.content)
 
 
+def _each(fn, idx):
+    """[fn(i) for i in idx], on several threads for long lists (every frame has
+    its own generator, and numpy's fills run without the interpreter lock, so
+    the frames are the same whatever the thread count)."""
+    idx = list(idx)
+    if len(idx) < 8:
+        return [fn(i) for i in idx]
+    with ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        return list(ex.map(fn, idx))
+
+
 def frames(w: Workload, idx=None) -> np.ndarray:
     """Frames idx (default: all) stacked as (n, H, W[, C]) (the first plane)."""
     idx = range(w.frames) if idx is None else idx
-    return np.stack([frame(w, i) for i in idx])
+    return np.stack(_each(lambda i: frame(w, i), idx))
 
 
 def plane_frames(w: Workload, idx=None):
@@ -132,8 +145,8 @@ def plane_frames(w: Workload, idx=None):
     out = []
     for k, (h, ww) in enumerate(w.planes):
         shape = (h, ww) if w.channels == 1 else (h, ww, w.channels)
-        out.append(np.stack([np.random.default_rng(w.seed + 1_000_003 * k + i).integers(0, 256, shape, dtype=np.uint8)
-                             for i in idx]))
+        out.append(np.stack(_each(
+            lambda i: np.random.default_rng(w.seed + 1_000_003 * k + i).integers(0, 256, shape, dtype=np.uint8), idx)))
     return out
 
 

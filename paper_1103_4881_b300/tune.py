@@ -1,8 +1,10 @@
-"""Persistent cache of autotuned tile schedules (host-side file IO only).
+"""Persistent cache of autotuned schedules (host-side file IO only).
 
-The tuning itself is ``ds_plan_autotune`` in the library (CUDA events over
-candidate band heights).  The cache keeps its choice per GPU model, SM count,
-dtype, ratio, taps, frame size and batch size, in the JSON file named by
+The tuning itself is ``ds_plan_autotune_ex`` in the library: CUDA events over
+the compiled tile shapes of the plan's class, band heights and resident CTAs
+per SM (the launch topology that the paper derives from thresholds, Sec.
+3.B.1).  The cache keeps its choice per GPU model, SM count, dtype, the ratio
+and taps of both axes, frame size and batch size, in the JSON file named by
 ``DS_TUNE_CACHE`` (default ``~/.cache/ds_tune.json``), so a process that has
 tuned once reuses the result.
 """
@@ -30,7 +32,9 @@ def _device_tag() -> str:
 
 def key(plan: int, n_frames: int, device_tag: str | None = None) -> str:
     in_h, in_w, p, q, taps, dtype = ds.ds_plan_get_params(plan)
-    return "%s|dt%d|%d/%d|K%d|%dx%d|n%d" % (device_tag or _device_tag(), dtype, p, q, taps, in_h, in_w, n_frames)
+    _, (pv, qv, kv), bnd = ds.ds_plan_get_axes(plan)
+    return "%s|dt%d|%d/%d|K%d|v%d/%dK%d|b%d|%dx%d|n%d" % (device_tag or _device_tag(), dtype, p, q, taps, pv, qv, kv,
+                                                         bnd, in_h, in_w, n_frames)
 
 
 def load() -> dict:
@@ -50,18 +54,22 @@ def save(cache: dict) -> None:
     os.replace(tmp, path)
 
 
-def apply_or_tune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: int = 0, iters: int = 10) -> int:
-    """Set the plan's band height from the cache, tuning (and caching) on a miss.
-    Returns the band height in use."""
-    k = key(plan, n_frames)
+def apply_or_tune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: int = 0, iters: int = 10,
+                  device_tag: str | None = None) -> dict:
+    """Set the plan's schedule from the cache, tuning (and caching) on a miss.
+    Returns the schedule in use: row_blocks (0 = adaptive default band),
+    ctas_per_sm (0 = as many as fit), shape, and on a miss the measured
+    times (us per launch) of it and of the default schedule.  device_tag:
+    the GPU part of the cache key (default: the current device's)."""
+    k = key(plan, n_frames, device_tag)
+    with _lock:
+        e = load().get(k)
+    if e and all(f in e for f in ("row_blocks", "ctas_per_sm", "shape")):
+        ds.ds_plan_set_schedule_ex(plan, int(e["row_blocks"]), int(e["ctas_per_sm"]), int(e["shape"]))
+        return dict(e, cached=True)
+    r = ds.ds_plan_autotune_ex(plan, in_ptr, out_ptr, n_frames, stream, iters)
     with _lock:
         cache = load()
-        if k in cache:
-            ds.ds_plan_set_schedule(plan, int(cache[k]["row_blocks"]), 0)
-            return int(cache[k]["row_blocks"])
-    rb, us = ds.ds_plan_autotune(plan, in_ptr, out_ptr, n_frames, stream, iters)
-    with _lock:
-        cache = load()
-        cache[k] = {"row_blocks": rb, "us_per_launch": us}
+        cache[k] = r
         save(cache)
-    return rb
+    return dict(r, cached=False)

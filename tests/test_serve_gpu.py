@@ -95,14 +95,18 @@ def test_autotune_keeps_bits_and_caches(oracle, dt, tmp_path, monkeypatch):
         np.testing.assert_array_equal(out.cpu().numpy(), want)
         np.testing.assert_array_equal(run_fused(pl, x), want)
         assert_parity(want, oracle_out(oracle, x, 3, 8, 8, dt), dt)
-        # cache: a second plan of the same key takes the stored band without timing
-        assert tune.apply_or_tune(pl, xd.data_ptr(), out.data_ptr(), n, stream(), 2) >= 1  # miss: tunes
+        # cache: a second plan of the same key takes the stored schedule without timing
+        first = tune.apply_or_tune(pl, xd.data_ptr(), out.data_ptr(), n, stream(), 2)  # miss: tunes
+        assert not first["cached"] and first["us_per_launch"] <= first["default_us_per_launch"]
+        np.testing.assert_array_equal(run_fused(pl, x), want)
         pl2 = ds.ds_plan_create(H, W, (3, 8), 8, dt)
         try:
             ds.ds_plan_set_schedule(pl2, 1, 0)
             got = tune.apply_or_tune(pl2, 0, 0, n)  # a cache hit touches no buffer
-            assert got == tune.load()[tune.key(pl2, n)]["row_blocks"]
-            assert ds.ds_plan_get_schedule(pl2)[0] == got
+            stored = tune.load()[tune.key(pl2, n)]
+            assert got["cached"] and got["shape"] == stored["shape"] and got["row_blocks"] == stored["row_blocks"]
+            assert ds.ds_plan_get_schedule_ex(pl2) == {k: stored[k] for k in ("row_blocks", "ctas_per_sm", "shape")}
+            np.testing.assert_array_equal(run_fused(pl2, x), want)
         finally:
             ds.ds_destroy(pl2)
     finally:

@@ -23,14 +23,42 @@ def test_cache_key_and_round_trip(tmp_path, monkeypatch):
     assert tune.load() == {}
     a = ds.ds_plan_create(1080, 1920, (3, 8), 8, ds.DS_F32)
     b = ds.ds_plan_create(1080, 1920, (3, 8), 8, ds.DS_F16)
+    c = ds.ds_plan_create_ex(1080, 1920, (3, 8), 8, (4, 9), 8, ds.DS_F32)
     try:
+        assert tune.key(a, 64, "GPU|148") != tune.key(c, 64, "GPU|148")  # the vertical axis is in the key
         ka, kb = tune.key(a, 64, "GPU|148"), tune.key(b, 64, "GPU|148")
         assert ka != kb and ka != tune.key(a, 1, "GPU|148") and ka != tune.key(a, 64, "GPU|132")
         assert "1080x1920" in ka and "3/8" in ka
-        tune.save({ka: {"row_blocks": 8, "us_per_launch": 130.0}})
+        tune.save({ka: {"row_blocks": 8, "ctas_per_sm": 0, "shape": 1, "us_per_launch": 130.0}})
         assert tune.load()[ka]["row_blocks"] == 8
+        # a hit sets the plan's whole schedule without touching a GPU
+        got = tune.apply_or_tune(a, 0, 0, 64, device_tag="GPU|148")
+        assert got["cached"] and ds.ds_plan_get_schedule_ex(a) == {"row_blocks": 8, "ctas_per_sm": 0, "shape": 1}
         (tmp_path / "sub" / "tune.json").write_text("{not json")
         assert tune.load() == {}
     finally:
         ds.ds_destroy(a)
         ds.ds_destroy(b)
+        ds.ds_destroy(c)
+
+
+def test_schedule_ex_round_trip_and_checks():
+    pl = ds.ds_plan_create(1080, 1920, (3, 8), 8, ds.DS_F16)
+    gp = ds.ds_plan_create(100, 100, (3, 4), 4, ds.DS_F32)  # general kernels: no compiled shapes
+    try:
+        assert ds.ds_plan_tile_shapes(pl) >= 2 and ds.ds_plan_tile_shapes(gp) == 0
+        assert ds.ds_plan_get_schedule_ex(pl) == {"row_blocks": 0, "ctas_per_sm": 0, "shape": 0}
+        ds.ds_plan_set_schedule_ex(pl, 12, 3, 1)
+        assert ds.ds_plan_get_schedule_ex(pl) == {"row_blocks": 12, "ctas_per_sm": 3, "shape": 1}
+        assert '"index": 1' in ds.ds_plan_describe(pl) and '"band": "fixed"' in ds.ds_plan_describe(pl)
+        ds.ds_plan_set_schedule_ex(pl, 0, 0, 0)  # back to the default, adaptive band
+        assert '"band": "adaptive"' in ds.ds_plan_describe(pl)
+        for bad in [(-1, 0, 0), (0, -1, 0), (0, 0, -1), (0, 0, ds.ds_plan_tile_shapes(pl))]:
+            with pytest.raises(ds.DsError):
+                ds.ds_plan_set_schedule_ex(pl, *bad)
+        with pytest.raises(ds.DsError):
+            ds.ds_plan_set_schedule_ex(gp, 0, 0, 1)
+        ds.ds_plan_set_schedule_ex(gp, 0, 0, 0)
+    finally:
+        ds.ds_destroy(pl)
+        ds.ds_destroy(gp)

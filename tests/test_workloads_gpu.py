@@ -1,7 +1,7 @@
 """Full-size workloads on the GPU, in the launch configuration the benchmark
 uses (one batched launch over all frames of the workload), checked against
-the CPU oracle on every frame (fp32 batch) or on a seeded sample of frames
-that always includes the first and the last (the large uint8 / fp16 batches).
+the CPU oracle on every frame (fp32 batch) or on a seeded sample of 16
+frames plus the first and the last (the large uint8 / fp16 batches).
 """
 import numpy as np
 import pytest
@@ -82,7 +82,7 @@ def test_rgb300_1080x1920_u8_sampled(oracle):
     w = synth.WORKLOADS["rgb300_1080x1920_u8"]
     pl, x, xd, out = _run_workload(w)
     try:
-        idx = _sample(w, 10, 3)
+        idx = _sample(w, 16, 3)
         got = out[idx].cpu().numpy()
         want = oracle_out(oracle, x[idx], w.ratio[0], w.ratio[1], w.taps, w.dtype)
         assert_parity(got, want, w.dtype, w.name)
@@ -95,7 +95,7 @@ def test_uhd128_2160x3840_f16_sampled(oracle):
     w = synth.WORKLOADS["uhd128_2160x3840_f16"]
     pl, x, xd, out = _run_workload(w)
     try:
-        idx = _sample(w, 6, 4)
+        idx = _sample(w, 16, 4)
         got = out[idx].cpu().numpy()
         want = oracle_out(oracle, x[idx], w.ratio[0], w.ratio[1], w.taps, w.dtype)
         err = assert_parity(got, want, w.dtype, w.name)
@@ -124,3 +124,32 @@ def test_one_8k_frame_against_the_oracle(oracle, ratio, K, dt):
         assert_parity(got, want, dt, "8192x8192")
     finally:
         ds.ds_destroy(pl)
+
+
+@pytest.mark.parametrize("name", ["cif2000_352x288_u8rgb", "cif2000_yuv420_u8"])
+def test_cif2000_every_frame_in_the_bench_configuration(oracle, name):
+    """The paper's case (Sec. 3): 2000 CIF frames (RGB, or YUV 4:2:0 as three
+    plane jobs), one plan per plane, the whole batch in one captured graph as
+    the benchmark runs it; every output byte of every plane against the
+    oracle."""
+    import torch
+
+    w = synth.WORKLOADS[name]
+    shapes = w.plane_shapes()
+    plans = [ds.ds_plan_create_ex(h, ww, w.ratio, w.taps, w.vratio, w.vtaps, w.dtype) for h, ww in shapes]
+    try:
+        xs = synth.plane_frames(w)
+        ins = [torch.from_numpy(x).cuda() for x in xs]
+        outs = [out_buffer(pl, w.frames) for pl in plans]
+        g = ds.ds_graph_create([(pl, i.data_ptr(), o.data_ptr(), w.frames) for pl, i, o in zip(plans, ins, outs)])
+        try:
+            ds.ds_graph_launch(g, stream())
+            finish()
+        finally:
+            ds.ds_graph_destroy(g)
+        for x, o in zip(xs, outs):
+            want = oracle.filter_ex(x, w.ratio, w.taps, w.vratio, w.vtaps)
+            assert_parity(o.cpu().numpy(), want, w.dtype, "%s plane %s" % (name, x.shape[1:]))
+    finally:
+        for pl in plans:
+            ds.ds_destroy(pl)
