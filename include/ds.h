@@ -417,6 +417,66 @@ ds_status ds_pipeline_run(ds_pipeline* pipe, const void* in, void* out, int n_fr
 void ds_pipeline_destroy(ds_pipeline* pipe);
 
 /* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of single-frame requests                    */
+/* ---------------------------------------------------------------------- */
+
+/*
+ * A request loop over a stream of frames (the paper applies its downscaler
+ * to a video, frame after frame, and measures the whole application,
+ * transfers included, Sec. 4; the paper has no serving API, this is the
+ * C ABI's).  A request is one frame of any plan.  ds_server_run admits
+ * queued requests while a stream slot is free and their bytes fit the
+ * memory budget, launches each admitted group as one ds_batch_run on the
+ * slot's stream, and keeps admitting as slots and memory free up, so groups
+ * overlap on the device.  Plans stay resident in the caller's hands; the
+ * server owns its streams, events and (copy mode) one device arena per slot.
+ * The request path allocates nothing.
+ *
+ * ds_server_create: budget in bytes (inputs plus outputs of the admitted
+ * requests; in the copy mode split into n_streams equal arenas, allocated at
+ * the first copy-mode run), 1..64 stream slots, at most max_batch requests
+ * per group.  NULL on error.  ds_server_destroy waits for its streams.
+ */
+typedef struct ds_server ds_server;
+
+typedef struct {
+    const ds_plan* plan;
+    const void* in;    /* one frame: device memory, or host memory with DS_SERVE_COPIES (pinned
+                          memory overlaps the copies) */
+    void* out;         /* likewise */
+    double arrival_s;  /* seconds after the start of the run (with DS_SERVE_REALTIME) */
+} ds_request;
+
+typedef struct {
+    int completed, batches, max_batch, max_queue;
+    long long launches;          /* kernel launches made by the run */
+    double wall_s;
+    size_t peak_admitted_bytes;
+} ds_serve_stats;
+
+enum {
+    DS_SERVE_REALTIME = 1, /* requests arrive at their arrival_s; else all at once (saturation) */
+    DS_SERVE_COPIES = 2,   /* in / out are host buffers: H2D copy, kernels, D2H copy per group */
+    DS_SERVE_PLAIN = 4     /* the baseline: one plain fused launch per request on one stream */
+};
+
+ds_server* ds_server_create(size_t mem_budget_bytes, int n_streams, int max_batch);
+
+/*
+ * Serve n requests and return when all have completed.  latency_ms (NULL or
+ * [n]): arrival -> observed completion of each request, in milliseconds
+ * (with DS_SERVE_PLAIN: the end of the run, which waits once).  stats (NULL
+ * or one): counts, the wall time and the launches.  DS_ERR_ARG for NULL
+ * buffers, unknown flags or a request larger than the budget (copy mode:
+ * than a slot's arena); DS_ERR_NOMEM if the arenas cannot be allocated;
+ * DS_ERR_CUDA if a launch or copy fails (in-flight work is waited for
+ * before returning).
+ */
+ds_status ds_server_run(ds_server* server, const ds_request* reqs, int n, int flags, double* latency_ms,
+                        ds_serve_stats* stats);
+void ds_server_destroy(ds_server* server);
+
+/* ---------------------------------------------------------------------- */
 /* Misc                                                                     */
 /* ---------------------------------------------------------------------- */
 

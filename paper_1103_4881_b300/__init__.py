@@ -40,8 +40,9 @@ ABI_SYMBOLS = (
     "ds_launch_count", "ds_static_workspace_bytes", "ds_run_unfused_static", "ds_plan_autotune",
     "ds_debug_timeout_probe", "ds_plan_create_ex", "ds_plan_get_axes", "ds_plan_get_axis_taps",
     "ds_bounds_checked", "ds_debug_bounds_probe", "ds_plan_tile_shapes", "ds_plan_set_schedule_ex",
-    "ds_plan_get_schedule_ex", "ds_plan_autotune_ex",
+    "ds_plan_get_schedule_ex", "ds_plan_autotune_ex", "ds_server_create", "ds_server_run", "ds_server_destroy",
 )
+DS_SERVE_REALTIME, DS_SERVE_COPIES, DS_SERVE_PLAIN = 1, 2, 4
 
 
 class DsError(RuntimeError):
@@ -67,6 +68,17 @@ class ds_schedule(ctypes.Structure):
 class ds_tune_result(ctypes.Structure):
     _fields_ = [("best", ds_schedule), ("best_us", ctypes.c_float), ("default_us", ctypes.c_float),
                 ("candidates", ctypes.c_int)]
+
+
+class ds_request(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("arrival_s", ctypes.c_double)]
+
+
+class ds_serve_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int), ("batches", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("max_queue", ctypes.c_int), ("launches", ctypes.c_longlong), ("wall_s", ctypes.c_double),
+                ("peak_admitted_bytes", ctypes.c_size_t)]
 
 
 class ds_job(ctypes.Structure):
@@ -126,6 +138,10 @@ def lib() -> ctypes.CDLL:
         "ds_plan_set_schedule_ex": (i, [vp, ctypes.POINTER(ds_schedule)]),
         "ds_plan_get_schedule_ex": (i, [vp, ctypes.POINTER(ds_schedule)]),
         "ds_plan_autotune_ex": (i, [vp, vp, vp, i, vp, i, ctypes.POINTER(ds_tune_result)]),
+        "ds_server_create": (vp, [sz, i, i]),
+        "ds_server_run": (i, [vp, ctypes.POINTER(ds_request), i, i, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ds_serve_stats)]),
+        "ds_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -284,6 +300,31 @@ def ds_plan_autotune_ex(plan: int, in_ptr: int, out_ptr: int, n_frames: int, str
                                      ctypes.byref(r)))
     return {"row_blocks": r.best.row_blocks, "ctas_per_sm": r.best.ctas_per_sm, "shape": r.best.shape,
             "us_per_launch": r.best_us, "default_us_per_launch": r.default_us, "candidates": r.candidates}
+
+
+def ds_server_create(mem_budget_bytes: int, n_streams: int, max_batch: int) -> int:
+    h = lib().ds_server_create(int(mem_budget_bytes), n_streams, max_batch)
+    if not h:
+        raise DsError(DS_ERR_ARG, ds_last_error())
+    return h
+
+
+def ds_server_run(server: int, requests, flags: int):
+    """requests: a ds_request array (or a sequence of (plan, in_ptr, out_ptr,
+    arrival_s)); returns (latency_ms numpy array, stats dict)."""
+    if not isinstance(requests, ctypes.Array):
+        requests = (ds_request * len(requests))(*[ds_request(_ptr(p), _ptr(a), _ptr(b), float(t))
+                                                  for p, a, b, t in requests])
+    n = len(requests)
+    lat = np.zeros(max(n, 1), dtype=np.float64)
+    st = ds_serve_stats()
+    _check(lib().ds_server_run(_ptr(server), requests, n, flags,
+                               lat.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(st)))
+    return lat[:n], {f: getattr(st, f) for f, _ in ds_serve_stats._fields_}
+
+
+def ds_server_destroy(server: int) -> None:
+    lib().ds_server_destroy(_ptr(server))
 
 
 def ds_debug_timeout_probe(limit_cycles: int, stream: int = 0) -> None:

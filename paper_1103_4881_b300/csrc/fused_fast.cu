@@ -213,6 +213,7 @@ void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, 
   jd.chunks = (nby + jd.rbc - 1) / jd.rbc;
   jd.tiles = jd.strips * jd.chunks * ((n_frames + hg.fpw - 1) / hg.fpw);  // per group of fpw frames
   jd.out_vec = (((uintptr_t)out & 3u) == 0 && ((size_t)pl->out_w * pl->channels) % 4 == 0) ? 1 : 0;
+  jd.wrap = pl->boundary == DS_WRAP ? 1 : 0;
 }
 
 // The tensor map of a job's input: 3-D (row bytes / 8 eight-byte elements, H
@@ -269,9 +270,14 @@ ds_status job_tensor_map(const FastJob& job, CUtensorMap* out) {
 }
 
 ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
-  ds_status s = job_tensor_map(job, &jd.tmap);
-  if (s != DS_OK) return s;
+  if (job.plan->boundary == DS_WRAP) {
+    std::memset(&jd.tmap, 0, sizeof(jd.tmap));  // modular tilers copy rows by themselves
+  } else {
+    ds_status s = job_tensor_map(job, &jd.tmap);
+    if (s != DS_OK) return s;
+  }
   fill_job_geometry(jd, job.plan, job.out, job.n_frames, band);
+  jd.in = static_cast<const uint8_t*>(job.in);
   return DS_OK;
 }
 
@@ -475,12 +481,6 @@ ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, cons
     g_capture_slots->push_back(slot);
     prm.sched_slot = slot;
   } else {
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
-      set_error("fused launch inside a stream capture the library did not start: capture with ds_graph_create, "
-                "which gives each captured launch a scheduling slot of its own");
-      return DS_ERR_UNSUPPORTED;
-    }
     direct = direct_slots();
     if (!direct) {
       set_error("k_rows: no scheduling slots for this device");
@@ -510,23 +510,31 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   const ClassTaps& taps = pl0->given_taps ? given : class_taps(cls);
   int want_ctas = pl0->ctas_per_sm;
   for (int i = 0; i < n; ++i) want_ctas = std::max(want_ctas, jobs[i].plan->ctas_per_sm);
-  // both instantiations of a class and shape have the same footprint and occupancy
+  // the jobs of a launch share the boundary: the kernel is compiled for one
   const RowsEntry& re = entry_of(pl0);
-  int occ = ctas_per_sm(re.many);
+  const bool wrap = pl0->boundary == DS_WRAP;
+  if (wrap && !re.has_wrap) {
+    set_error("fused kernel class %d shape %d is not compiled for modular tilers", cls, pl0->shape);
+    return DS_ERR_UNSUPPORTED;
+  }
+  const KernelInfo& kfew = wrap ? re.few_wrap : re.few;
+  const KernelInfo& kmany = wrap ? re.many_wrap : re.many;
+  // both instantiations of a class and shape have the same footprint and occupancy
+  int occ = ctas_per_sm(kmany);
   if (occ <= 0) {
-    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", re.many.smem);
+    set_error("fused kernel does not fit on this device (%d bytes of shared memory)", kmany.smem);
     return DS_ERR_UNSUPPORTED;
   }
   if (want_ctas > 0) occ = std::min(occ, want_ctas);
   BandedJob banded[kMaxJobs];
-  const int nb = plan_bands(jobs, n, sm_count() * occ * (re.many.threads / 32), banded);
+  const int nb = plan_bands(jobs, n, sm_count() * occ * (kmany.threads / 32), banded);
   if (nb <= kFewJobs) {
     static thread_local FastParams<kFewJobs> few;
-    if (ctas_per_sm(re.few) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
-    return launch_with(few, re.few, cls, taps, banded, nb, occ, st);
+    if (ctas_per_sm(kfew) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
+    return launch_with(few, kfew, cls, taps, banded, nb, occ, st);
   }
   static thread_local FastParams<kMaxJobs> many;  // ~17 KB: not on the caller's stack
-  return launch_with(many, re.many, cls, taps, banded, nb, occ, st);
+  return launch_with(many, kmany, cls, taps, banded, nb, occ, st);
 }
 
 }  // namespace
@@ -558,6 +566,16 @@ bool fast_shape_info(int cls, int shape, FastShapeInfo* out) {
   return true;
 }
 
+bool fast_wrap_fits(int cls, int in_w) {
+  if (cls < 0 || cls >= kFcCount) return false;
+  const RowsEntry& e = table()[cls][0];  // modular tilers: tile shape 0
+  if (!e.present || !e.has_wrap) return false;
+  // the row copies of a strip's window reach at most one period past either
+  // end of the row: the row is at least a strip and its halo
+  const long long row = (long long)in_w * e.geom.c * e.geom.sz;
+  return row >= (long long)e.geom.spx * e.geom.c * e.geom.sz + e.geom.rhb && row >= e.geom.hlb;
+}
+
 int fast_ctas_per_sm(const ds_plan* pl) {
   if (pl->fast_class < 0) return 0;
   return ctas_per_sm(entry_of(pl).many);
@@ -572,37 +590,42 @@ void release_graph_slots(const std::vector<int>& slots) {
 }
 
 // One launch per class and tile shape present (each kernel is specialised
-// for its class), at most kMaxJobs descriptors per launch.
+// for its class), at most kMaxJobs descriptors per launch, one after the
+// other on the caller's stream.  (Running them concurrently on side streams
+// made the serving mix about 5 % slower: the serving loop already overlaps
+// batches on several streams.)
 ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
-  // one group per (class, shape) for the plans with the library's taps, one
-  // per plan with given taps (its own tap tables)
-  FastJob group[kMaxJobs];
-  int ng = 0;
-  auto flush = [&]() -> ds_status {
-    ds_status s = ng > 0 ? launch_chunk(group, ng, st) : DS_OK;
-    ng = 0;
-    return s;
-  };
-  auto add = [&](const FastJob& j) -> ds_status {
-    group[ng++] = j;
-    return ng == kMaxJobs ? flush() : DS_OK;
-  };
-  if (n == 1) {  // the common single-job case: no grouping
-    ds_status s = add(jobs[0]);
-    return s != DS_OK ? s : flush();
-  }
-  for (int cls = 0; cls < kFcCount; ++cls)
-    for (int shape = 0; shape < kShapes; ++shape) {
-      for (int i = 0; i < n; ++i) {
-        const ds_plan* pl = jobs[i].plan;
-        if (pl->fast_class == cls && pl->shape == shape && !pl->given_taps) {
-          ds_status s = add(jobs[i]);
-          if (s != DS_OK) return s;
-        }
-      }
-      ds_status s = flush();
-      if (s != DS_OK) return s;
+  if (!g_capture_slots) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+      set_error("fused launch inside a stream capture the library did not start: capture with ds_graph_create, "
+                "which gives each captured launch a scheduling slot of its own");
+      return DS_ERR_UNSUPPORTED;
     }
+  }
+  if (n == 1) return launch_chunk(jobs, 1, st);  // the common single-job case
+  // the groups: one per (class, shape, boundary) for the plans with the
+  // library's taps, one per plan with given taps (its own tap tables), at
+  // most kMaxJobs jobs each
+  std::vector<FastJob> order;
+  std::vector<int> bounds{0};
+  order.reserve(n);
+  auto close_group = [&]() {
+    if ((int)order.size() > bounds.back()) bounds.push_back((int)order.size());
+  };
+  auto add = [&](const FastJob& j) {
+    order.push_back(j);
+    if ((int)order.size() - bounds.back() == kMaxJobs) close_group();
+  };
+  for (int cls = 0; cls < kFcCount; ++cls)
+    for (int shape = 0; shape < kShapes; ++shape)
+      for (int bnd : {DS_CLAMP, DS_WRAP}) {
+        for (int i = 0; i < n; ++i) {
+          const ds_plan* pl = jobs[i].plan;
+          if (pl->fast_class == cls && pl->shape == shape && pl->boundary == bnd && !pl->given_taps) add(jobs[i]);
+        }
+        close_group();
+      }
   for (int i = 0; i < n; ++i) {
     const ds_plan* pl = jobs[i].plan;
     if (!pl->given_taps) continue;
@@ -610,14 +633,13 @@ ds_status launch_fast(const FastJob* jobs, int n, cudaStream_t st) {
     for (int k = 0; k < i && !seen; ++k) seen = jobs[k].plan == pl;
     if (seen) continue;
     for (int k = i; k < n; ++k)
-      if (jobs[k].plan == pl) {
-        ds_status s = add(jobs[k]);
-        if (s != DS_OK) return s;
-      }
-    ds_status s = flush();
-    if (s != DS_OK) return s;
+      if (jobs[k].plan == pl) add(jobs[k]);
+    close_group();
   }
-  return DS_OK;
+  ds_status s = DS_OK;
+  for (size_t g = 0; g + 1 < bounds.size() && s == DS_OK; ++g)
+    s = launch_chunk(order.data() + bounds[g], bounds[g + 1] - bounds[g], st);
+  return s;
 }
 
 ds_status launch_timeout_probe(long long limit_cycles, cudaStream_t st) {

@@ -45,7 +45,7 @@ enum FastClass : int {
 // from several host threads at once: the cache has its own lock).
 struct TmapCache {
   struct Entry {
-    alignas(64) CUtensorMap map;
+    CUtensorMap map;  // 64-byte aligned by its type
     const void* in = nullptr;
     int n_frames = 0, shape = 0;
     bool used = false;
@@ -133,6 +133,9 @@ struct FastShapeInfo {
 int fast_tile_shapes(int cls);
 bool fast_shape_info(int cls, int shape, FastShapeInfo* out);
 int fast_ctas_per_sm(const ds_plan* plan);
+// Whether the fast kernel of class `cls` runs modular tilers on rows of
+// in_w pixels (they have tile shape 0 only).
+bool fast_wrap_fits(int cls, int in_w);
 // reads and clears the status word (1: a wait gave up, 3: a bounds check
 // failed, with kind and offset in info)
 ds_status read_device_status(int* status, long long* info);

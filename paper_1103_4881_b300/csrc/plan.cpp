@@ -294,10 +294,11 @@ ds_plan* create_plan(const ds_plan_desc& d, const char* who) {
     delete pl;
     return nullptr;
   }
-  // the fast kernels take clamp-to-edge (a plan's given taps travel with its
+  // the fast kernels take clamp-to-edge, and modular tilers on frames at
+  // least a strip and its halo wide (a plan's given taps travel with its
   // launch)
-  pl->fast_class = (d.boundary == DS_CLAMP)
-                       ? fast_class_of(pl->p, pl->q, pl->K, pl->pv, pl->qv, pl->Kv, d.dtype) : kFcNone;
+  pl->fast_class = fast_class_of(pl->p, pl->q, pl->K, pl->pv, pl->qv, pl->Kv, d.dtype);
+  if (d.boundary == DS_WRAP && !fast_wrap_fits(pl->fast_class, pl->in_w)) pl->fast_class = kFcNone;
   pl->row_blocks = default_band(pl->fast_class);
   if (pl->fast_class >= 0) {
     pl->tmaps.reset(new (std::nothrow) TmapCache());  // without it every launch encodes its maps
@@ -430,6 +431,7 @@ ds_status ds_plan_get_schedule(const ds_plan* pl, int* row_blocks, int* ctas_per
 
 int ds_plan_tile_shapes(const ds_plan* pl) {
   if (!pl || pl->fast_class < 0) return 0;
+  if (pl->boundary == DS_WRAP) return 1;  // modular tilers: tile shape 0 only
   return fast_tile_shapes(pl->fast_class);
 }
 
@@ -474,7 +476,7 @@ ds_status ds_plan_describe(const ds_plan* pl, char* buf, size_t len) {
                   "{\"index\": %d, \"of\": %d, \"packets_per_lane\": %d, \"strip_pixels\": %d, "
                   "\"frames_per_warp\": %d, \"stage_rows\": %d, \"stages\": %d, \"warps_per_cta\": %d, "
                   "\"ctas_per_sm_budget\": %d, \"smem_per_cta\": %d}",
-                  pl->shape, fast_tile_shapes(pl->fast_class), si.packets_per_lane, si.strip_pixels,
+                  pl->shape, ds_plan_tile_shapes(pl), si.packets_per_lane, si.strip_pixels,
                   si.frames_per_warp, si.stage_rows, si.stages, si.warps_per_cta, si.ctas_per_sm_budget,
                   si.smem_per_cta);
   std::snprintf(buf, len,

@@ -215,6 +215,7 @@ struct Cls {
   static_assert(BOXE <= 256 && BOXB % 16 == 0, "TMA box limits");
   static_assert((SPX * C * SZ) % 16 == 0 && HLB % 16 == 0, "strip windows start on 16-byte boundaries");
   static_assert(NBOX * BOXB >= WINB, "boxes must cover the window");
+  static_assert(NBOX == 1 && BOXB == WINB, "one box per window row: the row copies of modular tilers rely on it");
   static_assert(P * K <= kMaxTaps && PV * KV <= kMaxTaps, "tap table size");
   static_assert(BOXB % VB == 0 && HLB % VB == 0, "vector loads must not straddle boxes");
   static_assert(PRE > LHV, "the window prologue must reach frame row 0");
@@ -228,12 +229,14 @@ struct Cls {
 // launch parameters
 // ---------------------------------------------------------------------------
 struct JobDesc {
-  CUtensorMap tmap;        // 3-D map: (W*C elements, H rows, n_frames)
+  CUtensorMap tmap;        // 3-D map: (W*C elements, H rows, n_frames); clamped tilers
   void* out;
   long long out_frame;     // elements per output frame
   int H, W, OH, OW;
   int nframes, cls, strips, chunks;
   int rbc, tile_begin, tiles, out_vec;
+  const uint8_t* in;       // the frames, for the row copies of modular tilers
+  int wrap;                // 1: modular tilers (launched on the WRAP kernels)
 };
 static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor layout");
 
@@ -277,6 +280,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr32(bar)), "r"(bytes) : "memory");
 }
+// Count `bytes` of the current phase's expected transactions as done (no copy).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(saddr32(bar)), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -307,6 +314,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(saddr32(bar))
       : "memory");
 }
+// One contiguous global -> shared copy (16-byte aligned addresses, a size that
+// is a multiple of 16), completing `bytes` on the mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          saddr32(dst)),
+      "l"(src), "r"(bytes), "r"(saddr32(bar))
+      : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // tiles
 // ---------------------------------------------------------------------------
@@ -600,6 +617,7 @@ __device__ __forceinline__ int dp2a(uint32_t taps, uint32_t px, int c) {
 // The positions are compile-time constants after unrolling, so the selectors
 // fold and only the words that hold one of the bytes are read.
 __device__ __forceinline__ uint32_t gather4(const uint32_t* w, int p0, int p1, int p2, int p3) {
+  if ((p0 & 3) == 0 && p1 == p0 + 1 && p2 == p0 + 2 && p3 == p0 + 3) return w[p0 >> 2];  // a whole word
   const int pos[4] = {p0, p1, p2, p3};
   const int a = p0 >> 2, top = (p3 >> 2) - a;
   unsigned s1 = 0, s2 = 0, s3 = 0;
@@ -742,19 +760,29 @@ struct RowMath<Cl, true> {
           }
         }
     } else {
-      // one channel word per 4 consecutive pixel slots (pairs 2k, 2k+1)
-      constexpr int NCW = (NXP + 1 + 3) / 4;  // channel words (+1: odd-start pad)
+      // one channel word per 4 consecutive pixel slots (pairs 2k, 2k+1).  For
+      // one channel the slots start D pixels left of the lane's window, so
+      // that slot 0 is the first byte of a loaded word and every channel
+      // word is a loaded word as it is (no byte_perm); the D extra slots
+      // only ever meet zero taps.
+      constexpr int D = (C == 1) ? (first & 3) : 0;
+      constexpr int first1 = first - D, loaded = Cl::NVT * Cl::VB;
+      auto pos1 = [&](int slot, int c) {
+        const int p = C == 1 ? first1 + slot : first + (slot < NXP ? slot : NXP - 1) * C + c;
+        return p < loaded ? p : loaded - 1;  // past the loaded bytes: pads, any byte
+      };
+      constexpr int NCW = (NXP + D + 1 + 3) / 4;  // channel words (+1: odd-start pad)
       uint32_t cw[C][NCW];
 #pragma unroll
       for (int c = 0; c < C; ++c)
 #pragma unroll
         for (int k = 0; k < NCW; ++k)
-          cw[c][k] = gather4(w, pos(4 * k, c), pos(4 * k + 1, c), pos(4 * k + 2, c), pos(4 * k + 3, c));
+          cw[c][k] = gather4(w, pos1(4 * k, c), pos1(4 * k + 1, c), pos1(4 * k + 2, c), pos1(4 * k + 3, c));
 #pragma unroll
       for (int n = 0; n < Cl::NB; ++n)
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          const int s0 = n * Q + Cl::b(j) - BMIN;  // first window slot of the output
+          const int s0 = n * Q + Cl::b(j) - BMIN + D;  // first window slot of the output
           const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (K + par + 1) / 2;
 #pragma unroll
           for (int c = 0; c < C; ++c) {
@@ -794,9 +822,10 @@ struct RowMath<Cl, true> {
       for (int jv = 0; jv < PV; ++jv) {
         const int s0 = Cl::bv(jv) - BMINV;
         const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (KV + par + 1) / 2;
-        int v[4];
+        int v[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
+          if (4 * g + e >= N) continue;  // past the lane's outputs: never stored, not computed
           int acc = 8192;
 #pragma unroll
           for (int i = 0; i < npair; ++i) {
@@ -816,7 +845,8 @@ struct RowMath<Cl, true> {
   }
 };
 
-template <class Cl, int MAXJ>
+// WRAP: modular tilers (every job of the launch has them), else clamp-to-edge.
+template <class Cl, int MAXJ, bool WRAP>
 __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_constant__ FastParams<MAXJ> prm) {
   using T = typename Cl::T;
   using RM = RowMath<Cl>;
@@ -875,7 +905,8 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;  // window start, in elements
     const int xt = xw * Cl::SZ / kTmaElem;                          // ... in TMA elements (exact)
     const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
-    const bool fixing = fix.nl + fix.nr > 0;
+    constexpr bool wrap = WRAP;
+    const bool fixing = !wrap && fix.nl + fix.nr > 0;
     const int frame0 = tl.frame * Cl::FPW;              // the group's first frame
     const int nf = Cl::FPW == 1 ? 1 : min(Cl::FPW, jd.nframes - frame0);  // frames in the group
     const int sub = lane / Cl::LPS;                     // this lane's frame in the group
@@ -904,8 +935,46 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
           tma_load_3d(ring + slot * Cl::RSTAGE + f * Cl::FSTR + bx * Cl::BOXSTR, &jd.tmap, &full[slot],
                       xt + bx * Cl::BOXE, ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0), frame0 + f);
     };
-    if (lane == 0)
-      for (int s = 0; s < NST && s < nst; ++s) issue(s);
+    // Modular tilers: every row of a stage is copied by itself from frame row
+    // (y mod H), the window's bytes left of the row from the row's last bytes
+    // and those past its end from its first bytes (one 1-D bulk copy each,
+    // lane k taking row k); so the stage holds the window modulo the frame
+    // and no border needs fixing.  The plan only takes this path when a
+    // window spans less than one period of the row.
+    const long long rowb = (long long)jd.W * Cl::C * Cl::SZ;
+    auto issue_wrap = [&](int s) {  // all lanes
+      const uint32_t G = g + (uint32_t)s, slot = G % NST;
+      if (lane == 0) mbar_expect_tx(&full[slot], (uint32_t)(nf * SR * Cl::WINB));
+      __syncwarp();
+      const long long lo = (long long)xw * Cl::SZ, hi = lo + Cl::WINB;  // window bytes within the row
+      for (int k = lane; k < nf * SR; k += 32) {
+        const int f = k / SR, r = k - f * SR;
+        int y = (ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0) + r) % H;
+        if (y < 0) y += H;
+        const uint8_t* row = jd.in + ((long long)(frame0 + f) * H + y) * rowb;
+        uint8_t* dst = ring + slot * Cl::RSTAGE + f * Cl::FSTR + r * Cl::BOXB;
+        const long long m0 = lo > 0 ? lo : 0, m1 = hi < rowb ? hi : rowb;
+        if constexpr (kCheckBounds) {
+          const long long off = (long long)(dst - ring);
+          const bool bad = off < 0 || off + Cl::WINB > Cl::WARP_BYTES || frame0 + f >= jd.nframes ||
+                           -lo > rowb || hi - rowb > rowb || m1 <= m0;
+          if (bad) {  // skip the row's copies and take their bytes off the barrier's count
+            bounds_fail(prm.dev, 4, off);
+            mbar_complete_tx(&full[slot], (uint32_t)Cl::WINB);
+            continue;
+          }
+        }
+        if (lo < 0) bulk_load(dst, row + rowb + lo, (uint32_t)(-lo), &full[slot]);
+        bulk_load(dst + (m0 - lo), row + m0, (uint32_t)(m1 - m0), &full[slot]);
+        if (hi > rowb) bulk_load(dst + (rowb - lo), row, (uint32_t)(hi - rowb), &full[slot]);
+      }
+    };
+    if constexpr (WRAP) {
+      for (int s = 0; s < NST && s < nst; ++s) issue_wrap(s);
+    } else {
+      if (lane == 0)
+        for (int s = 0; s < NST && s < nst; ++s) issue(s);
+    }
     issued = g + (uint32_t)min(NST, nst);
     // wait for stage s; returns the stage's row-0 base, or nullptr on timeout.
     // The stage's columns outside the frame get their border values (only
@@ -921,7 +990,8 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     auto stage_release = [&](int s) {
       __syncwarp();
       if (s + NST < nst) {
-        if (lane == 0) issue(s + NST);
+        if constexpr (WRAP) issue_wrap(s + NST);
+        else if (lane == 0) issue(s + NST);
         issued = g + (uint32_t)(s + NST + 1);
       }
     };
@@ -978,8 +1048,8 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
         const int i = ps == 0 ? r - Cl::EXTRA + Cl::S0SHIFT : ps * SR + r - Cl::EXTRA;
         if (i < 0 || (ps == 0 && r >= SR - Cl::S0SHIFT)) continue;
         const int y = ys + i;
-        if (y < 0) continue;                    // top band: filled from frame row 0 below
-        if (i > 0 && y >= H) {
+        if (y < 0 && !wrap) continue;           // top band: filled from frame row 0 below
+        if (i > 0 && y >= H && !wrap) {
           RM::copy(win[i], win[i - 1]);
         } else {
           hrow_regs(sb + r * Cl::BOXB, win[i]);
@@ -989,8 +1059,9 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     }
     if (!ok) break;
     // top band (ys == BMINV): slots 0..LHV-1 are frame row 0, held in slot LHV
+    // (modular tilers: they hold the frame's last rows, as loaded)
     auto top_fix = [&]() {
-      if (ys < 0) {
+      if (ys < 0 && !wrap) {
 #pragma unroll
         for (int i = 0; i < Cl::LHV; ++i) RM::copy(win[i], win[Cl::LHV]);
       }
@@ -1030,10 +1101,11 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
               RM::h(w, prm, win[i]);
             } else {
               // rows below the frame's last repeat it (filtered from the zero
-              // fill, then replaced: a select, not a branch)
+              // fill, then replaced: a select, not a branch); modular tilers
+              // loaded the frame's first rows there
               const int y = ys + m * Q + i;
               hrow_regs(sb + r * Cl::BOXB, win[i]);
-              if (y >= H) RM::copy(win[i], win[i - 1]);
+              if (y >= H && !wrap) RM::copy(win[i], win[i - 1]);
             }
             if (q == Q - 1) {
               // the window holds block m's pattern: its P output rows
@@ -1097,6 +1169,7 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
 struct HostGeom {
   int sblk, spx, p, q, pv, boxe, sr, sz, c, fpw;
   CUtensorMapDataType dt;
+  int hlb, rhb;  // halo bytes of a strip's window, left and right
 };
 
 struct KernelInfo {
@@ -1109,24 +1182,26 @@ struct KernelInfo {
 // kernel with room for kFewJobs or kMaxJobs job descriptors, the host replay
 // of its index arithmetic, and its shape for descriptions.
 struct RowsEntry {
-  bool present;
+  bool present, has_wrap;     // has_wrap: compiled for modular tilers too
   HostGeom geom;
-  KernelInfo few, many;
+  KernelInfo few, many;       // clamp-to-edge
+  KernelInfo few_wrap, many_wrap;
   std::string (*check)(const JobDesc& jd);
   int nb, sr, nst, wpc, minb;
 };
 
 template <class Cl>
 HostGeom host_geom() {
-  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW, kTmaType};
+  return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW, kTmaType,
+                  Cl::HLB, Cl::RHB};
 }
 
 // Registers are budgeted for Cl::MINB resident CTAs (of Cl::WPC warps) per SM.
-template <class Cl>
+template <class Cl, bool WRAP>
 KernelInfo rows_info(bool few) {
   constexpr int smem = 128 + Cl::WPC * (Cl::WARP_BYTES + Cl::NST * 8);
-  const void* fn = few ? reinterpret_cast<const void*>(&k_rows<Cl, kFewJobs>)
-                       : reinterpret_cast<const void*>(&k_rows<Cl, kMaxJobs>);
+  const void* fn = few ? reinterpret_cast<const void*>(&k_rows<Cl, kFewJobs, WRAP>)
+                       : reinterpret_cast<const void*>(&k_rows<Cl, kMaxJobs, WRAP>);
   return KernelInfo{fn, smem, Cl::WPC * 32};
 }
 
@@ -1174,8 +1249,18 @@ std::string check_rows(const JobDesc& jd) {
         const long long xb = (long long)(xw * Cl::SZ / kTmaElem + bx * Cl::BOXE) * kTmaElem;
         if (((xb % 16) + 16) % 16 != 0) return fail("TMA x not 16-byte aligned", xw, bx);
       }
+      const bool wrap = jd.wrap != 0;
+      auto wrapped = [&](int y) { return ((y % jd.H) + jd.H) % jd.H; };
+      if (wrap) {
+        // the row copies of modular tilers: 16-byte aligned pieces that fill
+        // the window exactly, each at most one period of the row away
+        const long long rowb = (long long)jd.W * Cl::C * Cl::SZ, lo = (long long)xw * Cl::SZ, hi = lo + Cl::WINB;
+        const long long m0 = std::max(lo, 0LL), m1 = std::min(hi, rowb);
+        if (rowb % 16 || lo % 16 || hi % 16) return fail("row copy not 16-byte aligned", (int)lo, (int)hi);
+        if (-lo > rowb || hi - rowb > rowb || m1 <= m0) return fail("row copy beyond one period", (int)lo, (int)hi);
+      }
       const EdgeFix fx = edge_fix<Cl>(strip, jd.W);
-      for (int e = 0; e < fx.nl + fx.nr; ++e) {
+      for (int e = 0; e < (wrap ? 0 : fx.nl + fx.nr); ++e) {
         const bool left = e < fx.nl;
         const int k2 = left ? e : e - fx.nl;
         const int px = (left ? fx.l_lo : fx.r_lo) + k2 / Cl::C, c = k2 % Cl::C;
@@ -1192,7 +1277,7 @@ std::string check_rows(const JobDesc& jd) {
             return fail("vector read", lane, b0);
         }
         const int blk0 = strip * Cl::SBLK + lane * Cl::NB, px0 = blk0 * Cl::Q;
-        if (blk0 * PH >= jd.OW) continue;
+        if (blk0 * PH >= jd.OW || wrap) continue;
         for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
           if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lane, px);
           if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lane, px);
@@ -1207,6 +1292,7 @@ std::string check_rows(const JobDesc& jd) {
       auto take = [&](int s, int r, int i) -> std::string {
         if (s >= nst) return fail("stage beyond the tile", s, nst);
         wrow[i] = ystream + s * Cl::SRR + r + (s == 0 ? Cl::S0SHIFT : 0);
+        if (wrap) wrow[i] = wrapped(wrow[i]);
         ++sr;
         return std::string();
       };
@@ -1215,13 +1301,13 @@ std::string check_rows(const JobDesc& jd) {
           const int i = ps == 0 ? r - Cl::EXTRA + Cl::S0SHIFT : ps * Cl::SRR + r - Cl::EXTRA;
           if (i < 0 || (ps == 0 && r >= Cl::SRR - Cl::S0SHIFT)) continue;
           const int y = ys + i;
-          if (y < 0) continue;
-          if (i > 0 && y >= jd.H) { wrow[i] = wrow[i - 1]; continue; }
+          if (y < 0 && !wrap) continue;
+          if (i > 0 && y >= jd.H && !wrap) { wrow[i] = wrow[i - 1]; continue; }
           std::string e = take(ps, r, i);
           if (!e.empty()) return e;
-          if (wrow[i] != y) return fail("prologue row mismatch", i, wrow[i]);
+          if (wrow[i] != (wrap ? wrapped(y) : y)) return fail("prologue row mismatch", i, wrow[i]);
         }
-      if (ys < 0 && !Cl::PRO)
+      if (ys < 0 && !Cl::PRO && !wrap)
         for (int i = 0; i < Cl::LHV; ++i) wrow[i] = wrow[Cl::LHV];
       const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
       for (int u = 0; u < nunits; ++u)
@@ -1232,23 +1318,23 @@ std::string check_rows(const JobDesc& jd) {
             const int ru = st * Cl::SRR + r, bq = ru / Q, q = ru - bq * Q, m = u * Cl::UBLK + bq - Cl::VBLK;
             if (m >= nblk) continue;
             const int i = L - Q + q, y = ys + m * Q + i;
-            if (y >= jd.H) wrow[i] = wrow[i - 1];
+            if (y >= jd.H && !wrap) wrow[i] = wrow[i - 1];
             else {
               std::string e = take(s, r, i);
               if (!e.empty()) return e;
-              if (wrow[i] != y) return fail("stream row mismatch", i, wrow[i]);
+              if (wrow[i] != (wrap ? wrapped(y) : y)) return fail("stream row mismatch", i, wrow[i]);
             }
             if (q != Q - 1) continue;
             if (m < 0) {  // a lead block: no outputs, the window moves on
               for (int i2 = 0; i2 < L - Q; ++i2) wrow[i2] = wrow[i2 + Q];
-              if (m == -1 && ys < 0)
+              if (m == -1 && ys < 0 && !wrap)
                 for (int i2 = 0; i2 < Cl::LHV; ++i2) wrow[i2] = wrow[Cl::LHV];
               continue;
             }
             const int rr = rb0 + m;
             for (int i2 = 0; i2 < L; ++i2) {
               int want = rr * Q + Cl::BMINV + i2;
-              want = want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want);
+              want = wrap ? wrapped(want) : (want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want));
               if (wrow[i2] != want) return fail("window row mismatch", i2, wrow[i2]);
             }
             for (int lane = 0; lane < Cl::LPS; ++lane) {
@@ -1265,7 +1351,7 @@ std::string check_rows(const JobDesc& jd) {
           }
         }
       // with lead blocks every stream row above the frame's end is filtered (those above row 0 too)
-      const int want_rows = Cl::PRO ? std::min(ye, jd.H) - ystream : nrow;
+      const int want_rows = wrap ? (Cl::PRO ? ye - ystream : ye - ys) : (Cl::PRO ? std::min(ye, jd.H) - ystream : nrow);
       if (sr != want_rows) return fail("stream rows left over", sr, want_rows);
     }
   }
@@ -1274,10 +1360,18 @@ std::string check_rows(const JobDesc& jd) {
   return std::string();
 }
 
-template <class Cl>
+// with_wrap: also compile the class for modular tilers (tile shape 0 only:
+// the clamp kernels are the ones the tuner chooses among)
+template <class Cl, bool WITH_WRAP>
 RowsEntry make_entry() {
-  return RowsEntry{true, host_geom<Cl>(), rows_info<Cl>(true), rows_info<Cl>(false), &check_rows<Cl>,
-                   Cl::NB, Cl::SRR, Cl::NST, Cl::WPC, Cl::MINB};
+  RowsEntry e{true, WITH_WRAP, host_geom<Cl>(), rows_info<Cl, false>(true), rows_info<Cl, false>(false),
+              KernelInfo{nullptr, 0, 0}, KernelInfo{nullptr, 0, 0}, &check_rows<Cl>,
+              Cl::NB, Cl::SRR, Cl::NST, Cl::WPC, Cl::MINB};
+  if constexpr (WITH_WRAP) {
+    e.few_wrap = rows_info<Cl, true>(true);
+    e.many_wrap = rows_info<Cl, true>(false);
+  }
+  return e;
 }
 
 // Tile shapes compiled per class, and the table of every (class, shape).

@@ -3,7 +3,8 @@
 // K=8): uint8 RGB, and one uint8 plane (the planes of YUV 4:2:0).  Two
 // frames per warp (16-lane strips), since a 352-pixel row is 44 packets.
 // Each in two tile shapes: shape 0 is the default measured on a B300, shape
-// 1 the other pipeline depth (a candidate of the autotuner).
+// 1 the other pipeline depth (a candidate of the autotuner); shape 0 also
+// for modular tilers.
 #include "rows.cuh"
 
 namespace ds {
@@ -17,10 +18,10 @@ using U8P_CIF_1 = Cls<kFcU8C1_CIF, uint8_t, 1, 3, 8, 8, 1, 9, 3, true,  4, 9, 8,
 }  // namespace
 
 void register_cif(RowsTable& t) {
-  t[kFcU8C3_CIF][0] = make_entry<U8_CIF_0>();
-  t[kFcU8C3_CIF][1] = make_entry<U8_CIF_1>();
-  t[kFcU8C1_CIF][0] = make_entry<U8P_CIF_0>();
-  t[kFcU8C1_CIF][1] = make_entry<U8P_CIF_1>();
+  t[kFcU8C3_CIF][0] = make_entry<U8_CIF_0, true>();
+  t[kFcU8C3_CIF][1] = make_entry<U8_CIF_1, false>();
+  t[kFcU8C1_CIF][0] = make_entry<U8P_CIF_0, true>();
+  t[kFcU8C1_CIF][1] = make_entry<U8P_CIF_1, false>();
 }
 
 }  // namespace rows

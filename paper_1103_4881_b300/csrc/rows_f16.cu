@@ -1,7 +1,7 @@
 // rows_f16.cu -- the fused kernel's fp16-storage classes (3/8 K=8, 1/2 K=6,
 // 2/3 K=6; FP32 accumulation), each in two tile shapes: shape 0 is the
 // default measured on a B300, shape 1 the other pipeline depth (a candidate
-// of the autotuner).
+// of the autotuner); shape 0 also for modular tilers.
 #include "rows.cuh"
 
 namespace ds {
@@ -17,12 +17,12 @@ using F16_23_1 = Cls<kFcF16_23, __half, 1, 2, 3, 6, 2, 6, 3, true, 2, 3, 6, 1, f
 }  // namespace
 
 void register_f16(RowsTable& t) {
-  t[kFcF16_38][0] = make_entry<F16_38_0>();
-  t[kFcF16_38][1] = make_entry<F16_38_1>();
-  t[kFcF16_12][0] = make_entry<F16_12_0>();
-  t[kFcF16_12][1] = make_entry<F16_12_1>();
-  t[kFcF16_23][0] = make_entry<F16_23_0>();
-  t[kFcF16_23][1] = make_entry<F16_23_1>();
+  t[kFcF16_38][0] = make_entry<F16_38_0, true>();
+  t[kFcF16_38][1] = make_entry<F16_38_1, false>();
+  t[kFcF16_12][0] = make_entry<F16_12_0, true>();
+  t[kFcF16_12][1] = make_entry<F16_12_1, false>();
+  t[kFcF16_23][0] = make_entry<F16_23_0, true>();
+  t[kFcF16_23][1] = make_entry<F16_23_1, false>();
 }
 
 }  // namespace rows

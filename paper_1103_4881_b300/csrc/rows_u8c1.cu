@@ -1,7 +1,8 @@
 // rows_u8c1.cu -- the fused kernel's one-channel uint8 classes (3/8 K=8,
 // 1/2 K=6, 2/3 K=6; Q14 taps, exact integer arithmetic), each in two tile
 // shapes: shape 0 is the default measured on a B300, shape 1 the other
-// pipeline depth (a candidate of the autotuner).
+// pipeline depth (a candidate of the autotuner); shape 0 also for modular
+// tilers.
 #include "rows.cuh"
 
 namespace ds {
@@ -17,12 +18,12 @@ using U8P_23_1 = Cls<kFcU8C1_23, uint8_t, 1, 2, 3, 6, 4,  3, 2, true,  2, 3, 6, 
 }  // namespace
 
 void register_u8c1(RowsTable& t) {
-  t[kFcU8C1_38][0] = make_entry<U8P_38_0>();
-  t[kFcU8C1_38][1] = make_entry<U8P_38_1>();
-  t[kFcU8C1_12][0] = make_entry<U8P_12_0>();
-  t[kFcU8C1_12][1] = make_entry<U8P_12_1>();
-  t[kFcU8C1_23][0] = make_entry<U8P_23_0>();
-  t[kFcU8C1_23][1] = make_entry<U8P_23_1>();
+  t[kFcU8C1_38][0] = make_entry<U8P_38_0, true>();
+  t[kFcU8C1_38][1] = make_entry<U8P_38_1, false>();
+  t[kFcU8C1_12][0] = make_entry<U8P_12_0, true>();
+  t[kFcU8C1_12][1] = make_entry<U8P_12_1, false>();
+  t[kFcU8C1_23][0] = make_entry<U8P_23_0, true>();
+  t[kFcU8C1_23][1] = make_entry<U8P_23_1, false>();
 }
 
 }  // namespace rows

@@ -195,7 +195,16 @@ def serving_requests(n: int = 2000, rate_hz: float = 5000.0, seed_arrivals: int 
     return out
 
 
+def request_content(height: int, width: int, dtype: int, seed: int) -> np.ndarray:
+    """One request frame with the content recipe of the batch workload of its
+    dtype: fp32 uniform plus a smooth gradient (as the 1080p fp32 batch), fp16
+    uniform plus N(0, 0.05) clipped (as the 4K fp16 batch), uint8 uniform
+    bytes (as the RGB batch)."""
+    content = {DS_F32: "gradient", DS_F16: "noisy_half", DS_U8: "bytes", DS_U8_RGB: "bytes"}[dtype]
+    w = Workload("request", 1, height, width, (1, 2), 6, dtype, seed, content)
+    return frame(w, 0)
+
+
 def request_frame(req: Request) -> np.ndarray:
-    """Pixel content of a request: uniform floats / bytes, seeded by its id."""
-    shape = (req.height, req.width) if CHANNELS[req.dtype] == 1 else (req.height, req.width, 3)
-    return random_frames(shape, req.dtype, 6000 + req.rid)
+    """Pixel content of a request, seeded by its id."""
+    return request_content(req.height, req.width, req.dtype, 6000 + req.rid)

@@ -110,3 +110,20 @@ def test_checked_build_given_taps(checked, oracle, rh, Kh, rv, Kv, dt):
         assert_parity(run_fused(pl, x), want, dt, "given taps, checked build")
     finally:
         ds.ds_destroy(pl)
+
+
+@pytest.mark.parametrize("axes,dt", [(c[0], c[1]) for c in CLASSES
+                                     if c[2] == 0 and (c[0][2] != (4, 9) or c[1] in (ds.DS_U8, ds.DS_U8_RGB))])
+@pytest.mark.parametrize("H,W", [(41, 1104), (3, 1056), (97, 1040)])
+def test_checked_build_modular_tilers(checked, oracle, H, W, axes, dt):
+    """The row copies of modular tilers (tile shape 0, the one compiled for
+    them) with every index check passing."""
+    rh, Kh, rv, Kv = axes
+    pl = ds.ds_plan_create_ex(H, W, rh, Kh, rv, Kv, dt, ds.DS_WRAP)
+    try:
+        assert '"fused_tma"' in ds.ds_plan_describe(pl) and ds.ds_plan_tile_shapes(pl) == 1
+        x = frames((H, W), dt, 3, H + W)
+        xo = x if dt in (ds.DS_U8, ds.DS_U8_RGB) else x.astype(np.float64)
+        assert_parity(run_fused(pl, x), oracle.filter_ex(xo, rh, Kh, rv, Kv, wrap=True), dt, "checked wrap")
+    finally:
+        ds.ds_destroy(pl)

@@ -68,9 +68,9 @@ def test_equal_axes_keep_the_fast_kernel():
         assert '"fused_tma"' in ds.ds_plan_describe(pl)
     finally:
         ds.ds_destroy(pl)
-    # modular tilers take the general kernels; given taps (clamp) keep the
-    # fast kernel, which launches with the plan's own tap tables
-    for kw, kernel in ((dict(boundary=ds.DS_WRAP), '"fused_general"'),
+    # modular tilers on a frame at least a strip wide and given taps keep the
+    # fast kernel (given taps: the launch carries the plan's own tap tables)
+    for kw, kernel in ((dict(boundary=ds.DS_WRAP), '"fused_tma"'),
                        (dict(weights_h=None, weights_v=np.eye(3, 8)), '"fused_tma"')):
         pl = ds.ds_plan_create_ex(1080, 1920, (3, 8), 8, (3, 8), 8, ds.DS_F32, **kw)
         try:
@@ -93,3 +93,38 @@ def test_cif_classes_take_the_fast_kernel_and_pass_the_host_check():
             finally:
                 ds.ds_destroy(pl)
     assert checked == 2 * 8 * 6
+
+
+def test_modular_tilers_take_the_fast_kernel_when_a_strip_fits():
+    """DS_WRAP plans run on the fast kernel when a row is at least a strip and
+    its halo wide (the row copies then reach at most one period past either
+    end), else on the general kernels; the host replay of the kernel's index
+    arithmetic passes on both sides of that limit and on ragged frames."""
+    checked = fast = 0
+    specs = [((3, 8), 8, (3, 8), 8), ((1, 2), 6, (1, 2), 6), ((2, 3), 6, (2, 3), 6), ((3, 8), 8, (4, 9), 8)]
+    dts = (ds.DS_F32, ds.DS_F16, ds.DS_U8_RGB, ds.DS_U8)
+    for rh, kh, rv, kv in specs:
+        for dt in dts:
+            for H, W in [(1, 1056), (5, 272), (41, 272), (200, 784), (288, 352), (144, 176), (9, 1040), (130, 1104)]:
+                try:
+                    pl = ds.ds_plan_create_ex(H, W, rh, kh, rv, kv, dt, ds.DS_WRAP)
+                except ds.DsError:
+                    continue
+                try:
+                    if '"fused_tma"' not in ds.ds_plan_describe(pl):
+                        continue
+                    fast += 1
+                    for shape in range(ds.ds_plan_tile_shapes(pl)):
+                        for rb in (1, 2, 5, 16, 1000):
+                            ds.ds_plan_set_schedule_ex(pl, rb, 0, shape)
+                            ds.ds_debug_check_plan(pl)
+                            checked += 1
+                finally:
+                    ds.ds_destroy(pl)
+    assert fast > 40 and checked == fast * 5  # modular tilers: tile shape 0 only
+    # too narrow for the row copies: the general kernels
+    pl = ds.ds_plan_create_ex(64, 64, (3, 8), 8, (3, 8), 8, ds.DS_F32, ds.DS_WRAP)
+    try:
+        assert '"fused_general"' in ds.ds_plan_describe(pl)
+    finally:
+        ds.ds_destroy(pl)

@@ -1,9 +1,10 @@
 """Serving loop and autotuner on the GPU.
 
-The continuous-batching loop groups requests of different sizes, ratios and
-dtypes into ds_batch_run launches on several streams; every request must come
-back with the bits of its solo ds_run, whatever batch it landed in, and within
-the oracle's tolerance.  The autotuner times band heights that all compute the
+The native continuous-batching loop (ds_server_run) groups requests of
+different sizes, ratios and dtypes into ds_batch_run launches on several
+streams; every request must come back with the bits of its solo ds_run,
+whatever group it landed in and in both the kernel-only and the copy mode,
+and within the oracle's tolerance.  The autotuner times band heights that all compute the
 same bits, so its choice must not change the output."""
 import numpy as np
 import pytest
@@ -42,18 +43,19 @@ def _solo(srv, r, x):
 def test_served_requests_equal_solo_runs(oracle, copies):
     reqs = _requests(48)
     pool = serve.FramePool(reqs, per_class=3, host=copies)
-    # a budget of a few frames forces many small batches and waits on admission
+    # a budget of a few frames forces many small groups and waits on admission
     srv = serve.Server(mem_budget_bytes=3 << 20, n_streams=3, max_batch=6)
     try:
-        res, outs = srv.run(reqs, pool.pinned if copies else pool.device, copies=copies, realtime=True,
-                            keep_outputs=True)
+        outs = serve.OutputPool(srv, reqs, per_request=True, host=copies)
+        res = srv.run(reqs, pool.pinned if copies else pool.device, outs, copies=copies, realtime=True)
         finish()
-        assert res.completed == len(reqs) and len(outs) == len(reqs)
-        assert res.peak_bytes <= srv.budget and res.max_batch <= 6 and res.batches >= len(reqs) // 6
-        assert len(res.latency_ms) == len(reqs) and min(res.latency_ms) >= 0
+        s = res.stats
+        assert res.completed == len(reqs)
+        assert s["peak_admitted_bytes"] <= srv.budget and s["max_batch"] <= 6 and s["batches"] >= len(reqs) // 6
+        assert len(res.latency_ms) == len(reqs) and res.latency_ms.min() >= 0 and s["launches"] >= s["batches"]
         checked = set()
         for r in reqs:
-            got = outs[r.rid].cpu().numpy()
+            got = outs(r).cpu().numpy()
             x = pool.device(r)
             np.testing.assert_array_equal(got, _solo(srv, r, x), err_msg="request %d" % r.rid)
             k = (r.height, r.width, r.ratio, r.dtype, r.rid % pool.per_class)
@@ -66,13 +68,56 @@ def test_served_requests_equal_solo_runs(oracle, copies):
         srv.close()
 
 
+def test_saturation_groups_requests_and_the_plain_baseline_matches():
+    """All requests at t=0: groups up to the batch limit; the plain per-frame
+    baseline (one fused launch per request) writes the same bits."""
+    reqs = _requests(64, seed=5)
+    pool = serve.FramePool(reqs, per_class=2)
+    srv = serve.Server(mem_budget_bytes=256 << 20, n_streams=2, max_batch=16)
+    try:
+        a = serve.OutputPool(srv, reqs, per_request=True)
+        b = serve.OutputPool(srv, reqs, per_request=True)
+        res = srv.run(reqs, pool.device, a, realtime=False)
+        assert res.completed == len(reqs) and res.stats["max_batch"] == 16 and res.stats["batches"] == 4
+        fps = srv.per_frame(reqs, pool.device, b)
+        finish()
+        assert fps > 0
+        for r in reqs:
+            np.testing.assert_array_equal(a(r).cpu().numpy(), b(r).cpu().numpy(), err_msg="request %d" % r.rid)
+    finally:
+        srv.close()
+
+
 def test_budget_too_small_for_one_request_is_rejected():
     reqs = _requests(2)
     pool = serve.FramePool(reqs, per_class=1)
     srv = serve.Server(mem_budget_bytes=1024, n_streams=1)
     try:
-        with pytest.raises(ValueError):
-            srv.run(reqs, pool.device)
+        outs = serve.OutputPool(srv, reqs, per_request=True)
+        with pytest.raises(ds.DsError) as e:
+            srv.run(reqs, pool.device, outs)
+        assert e.value.status == ds.DS_ERR_ARG
+    finally:
+        srv.close()
+
+
+def test_copy_mode_arena_allocation_failure_is_reported_and_the_server_recovers():
+    """Arenas the device cannot hold: DS_ERR_NOMEM, nothing launched; the same
+    server then serves in the kernel-only mode."""
+    reqs = _requests(4, seed=11)
+    pool = serve.FramePool(reqs, per_class=1, host=True)
+    srv = serve.Server(mem_budget_bytes=1 << 52, n_streams=2, max_batch=4)  # 2 PiB per arena
+    try:
+        host_outs = serve.OutputPool(srv, reqs, per_request=True, host=True)
+        with pytest.raises(ds.DsError) as e:
+            srv.run(reqs, pool.pinned, host_outs, copies=True)
+        assert e.value.status == ds.DS_ERR_NOMEM
+        outs = serve.OutputPool(srv, reqs, per_request=True)
+        res = srv.run(reqs, pool.device, outs, realtime=False)
+        finish()
+        assert res.completed == len(reqs)
+        for r in reqs:
+            np.testing.assert_array_equal(outs(r).cpu().numpy(), _solo(srv, r, pool.device(r)))
     finally:
         srv.close()
 
@@ -111,30 +156,3 @@ def test_autotune_keeps_bits_and_caches(oracle, dt, tmp_path, monkeypatch):
             ds.ds_destroy(pl2)
     finally:
         ds.ds_destroy(pl)
-
-
-def test_allocation_failures_requeue_and_every_request_completes():
-    """An injected allocator that runs out of memory now and then: the batch
-    goes back to the queue, nothing of it is launched, and every request
-    still completes with the bits of its solo run."""
-    import torch
-
-    calls = {"n": 0}
-
-    def flaky(shape, dtype):
-        calls["n"] += 1
-        if calls["n"] <= 3 or calls["n"] % 7 == 0:
-            raise torch.cuda.OutOfMemoryError("injected")
-        return torch.empty(shape, dtype=dtype, device="cuda")
-
-    reqs = _requests(30, seed=9)
-    pool = serve.FramePool(reqs, per_class=2)
-    srv = serve.Server(mem_budget_bytes=64 << 20, n_streams=2, max_batch=4, alloc=flaky)
-    try:
-        res, outs = srv.run(reqs, pool.device, realtime=False, keep_outputs=True)
-        finish()
-        assert res.completed == len(reqs) and res.alloc_retries >= 3
-        for r in reqs:
-            np.testing.assert_array_equal(outs[r.rid].cpu().numpy(), _solo(srv, r, pool.device(r)))
-    finally:
-        srv.close()
