@@ -224,8 +224,11 @@ ds_status ds_plan_get_schedule_ex(const ds_plan* plan, ds_schedule* schedule);
  *   2. fixed bands at the best shape (against the default adaptive band),
  *   3. fewer resident CTAs per SM at the best shape and band,
  * and keep the fastest schedule in the plan.  The default schedule (shape 0,
- * adaptive band, full occupancy) is always timed, so the result is never
- * slower than it as measured.  Every candidate produces identical bits.
+ * adaptive band, full occupancy) is timed first and a candidate replaces the
+ * best so far only when it is more than 1 % faster, so the result is never
+ * slower than the default as measured and noise between equivalent
+ * schedules does not change the choice.  Every candidate produces identical
+ * bits.
  * `in` / `out` are the caller's device buffers for n_frames frames; they are
  * written (out) during tuning.  Synchronises the stream.
  * res (if not NULL): the best schedule, its time and the default's (us per
