@@ -113,6 +113,12 @@ int ctas_per_sm(const KernelInfo& ki) {
     if (e.first == ki.fn) return e.second;
   int occ = 0;
   if (cudaFuncSetAttribute(ki.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, ki.smem) != cudaSuccess) return 0;
+  // all of the SM's configurable memory as shared memory: the rings set the
+  // resident CTAs of most classes, and the kernels read their inputs through
+  // TMA into shared memory, not through L1
+  if (cudaFuncSetAttribute(ki.fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+      cudaSuccess)
+    return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ki.fn, ki.threads, ki.smem) != cudaSuccess) return 0;
   cache.emplace_back(ki.fn, occ);
   return occ;
