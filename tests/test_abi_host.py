@@ -190,3 +190,12 @@ def test_env_selects_the_bounds_checking_build():
     code0 = "import paper_1103_4881_b300 as ds; assert not ds.ds_bounds_checked(); print('normal')"
     r = subprocess.run([sys.executable, "-c", code0], cwd=root, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "normal" in r.stdout, r.stderr
+
+
+def test_server_arguments_are_checked_before_any_device_work():
+    for args in [(0, 2, 64), (1 << 20, 0, 64), (1 << 20, 65, 64), (1 << 20, 2, 0), (1 << 20, 2, 5000)]:
+        with pytest.raises(ds.DsError):
+            ds.ds_server_create(*args)
+    with pytest.raises(ds.DsError) as e:
+        ds.ds_server_run(0, [], 0)
+    assert e.value.status == ds.DS_ERR_ARG

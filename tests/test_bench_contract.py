@@ -32,3 +32,21 @@ def test_reference_arm_on_a_planar_per_axis_workload():
     assert out.returncode == 0, out.stderr[-2000:]
     d = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][0])
     assert d["config"]["ratio_v"] == "4/9" and len(d["config"]["planes"]) == 3
+
+
+def test_committed_traffic_capture_matches_the_kernel_source():
+    """profiles/traffic.json holds a one-pass ncu capture of the headline
+    workload's launch taken on the current kernel source (bench.py reports it
+    as roofline.traffic), at the default schedule the tuner keeps there."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sched = [{"row_blocks": 0, "ctas_per_sm": 0, "shape": 0}]
+    t = bench.profiled_traffic(bench.HEADLINE, sched)
+    assert t is not None, "re-capture the headline's DRAM traffic on the current kernel source"
+    from paper_1103_4881_b300 import synth
+
+    w = synth.WORKLOADS[bench.HEADLINE]
+    alg = w.frames * w.bytes_per_frame()
+    assert 0.95 * alg < t < 1.2 * alg  # traffic near the algorithmic bytes: no wasted re-reads
+    assert bench.profiled_traffic(bench.HEADLINE, [{"row_blocks": 3, "ctas_per_sm": 1, "shape": 1}]) is None
