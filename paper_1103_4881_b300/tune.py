@@ -65,8 +65,11 @@ def apply_or_tune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: i
     with _lock:
         e = load().get(k)
     if e and all(f in e for f in ("row_blocks", "ctas_per_sm", "shape")):
-        ds.ds_plan_set_schedule_ex(plan, int(e["row_blocks"]), int(e["ctas_per_sm"]), int(e["shape"]))
-        return dict(e, cached=True)
+        try:
+            ds.ds_plan_set_schedule_ex(plan, int(e["row_blocks"]), int(e["ctas_per_sm"]), int(e["shape"]))
+            return dict(e, cached=True)
+        except (ds.DsError, TypeError, ValueError):
+            pass  # an entry this library cannot take (another build's tile shapes): tune again
     r = ds.ds_plan_autotune_ex(plan, in_ptr, out_ptr, n_frames, stream, iters)
     with _lock:
         cache = load()

@@ -62,3 +62,20 @@ def test_schedule_ex_round_trip_and_checks():
     finally:
         ds.ds_destroy(pl)
         ds.ds_destroy(gp)
+
+
+def test_a_cache_entry_the_library_cannot_take_is_tuned_again(tmp_path, monkeypatch):
+    """A stale entry (a tile shape this build does not have) is not applied:
+    apply_or_tune falls through to tuning, which needs the caller's buffers
+    (here NULL, so the library refuses with DS_ERR_ARG before any device work)."""
+    monkeypatch.setenv("DS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    pl = ds.ds_plan_create(1080, 1920, (3, 8), 8, ds.DS_F32)
+    try:
+        k = tune.key(pl, 8, "GPU|148")
+        tune.save({k: {"row_blocks": 8, "ctas_per_sm": 0, "shape": 7}})
+        with pytest.raises(ds.DsError) as e:
+            tune.apply_or_tune(pl, 0, 0, 8, device_tag="GPU|148")
+        assert e.value.status == ds.DS_ERR_ARG
+        assert ds.ds_plan_get_schedule_ex(pl)["shape"] == 0
+    finally:
+        ds.ds_destroy(pl)
