@@ -223,12 +223,15 @@ ds_status ds_plan_get_schedule_ex(const ds_plan* plan, ds_schedule* schedule);
  *   1. every tile shape at the default band,
  *   2. fixed bands at the best shape (against the default adaptive band),
  *   3. fewer resident CTAs per SM at the best shape and band,
- * and keep the fastest schedule in the plan.  The default schedule (shape 0,
- * adaptive band, full occupancy) is timed first and a candidate replaces the
- * best so far only when it is more than 1 % faster, so the result is never
- * slower than the default as measured and noise between equivalent
- * schedules does not change the choice.  Every candidate produces identical
- * bits.
+ * and keep the fastest schedule in the plan.  The GPU is first kept busy
+ * with the default schedule (shape 0, adaptive band, full occupancy) for
+ * about 30 ms, the default is timed first, and a candidate replaces the best
+ * so far only when it is more than 1 % faster; a winner other than the
+ * default is re-timed against it, alternately, three times each, and kept
+ * only if its median is still more than 1 % faster.  So the result is never
+ * slower than the default as measured, and clock drifts or noise between
+ * equivalent schedules do not change the choice.  Every candidate produces
+ * identical bits.
  * `in` / `out` are the caller's device buffers for n_frames frames; they are
  * written (out) during tuning.  Synchronises the stream.
  * res (if not NULL): the best schedule, its time and the default's (us per
