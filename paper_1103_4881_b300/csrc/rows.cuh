@@ -575,10 +575,11 @@ struct RowMath<Cl, false> {
     for (int k = 0; k < N; ++k) d.v[k] = s.v[k];
   }
   // the PV output rows of block rr from the window (CHECK: rows past OH are
-  // skipped; without it the caller knows they are all inside)
+  // skipped; without it the caller knows they are all inside); `words`: see
+  // the uint8 form
   template <bool CHECK, class PR>
   __device__ static __forceinline__ void v(const Row (&win)[Cl::LV], const PR& prm, T* obase, long long rowe,
-                                           int rr, int OH, int n_valid) {
+                                           int rr, int OH, int n_valid, bool /*words*/) {
     const float* taps = prm.t.tapsv;
 #pragma unroll
     for (int jv = 0; jv < Cl::PV; ++jv) {
@@ -687,6 +688,34 @@ __device__ __forceinline__ void store_bytes(uint8_t* o, const uint32_t* w, int n
 #pragma unroll
   for (int i = 0; i < N; ++i)
     if (i < n_valid) o[i] = (uint8_t)(w[i >> 2] >> (8 * (i & 3)));
+}
+
+// Word stores of runs whose length N is not a multiple of 4, for a warp whose
+// lanes' runs follow one another in a row that starts on a word boundary, with
+// each strip starting and ending on one: lane runs then start a = 0..3 bytes
+// into a word.  A lane shifts its bytes (zero above byte N-1) to their place
+// in the words they span and stores every word that starts inside its run,
+// the word across its end completed with the first bytes of the next lane's
+// run (a shuffle; that lane is active whenever the run ends inside a word,
+// since a row's end is on a word boundary).  A lane past the frame's edge
+// stores nothing.  Every lane of the warp must call this (the shuffle).
+template <int N>
+__device__ __forceinline__ void store_words(uint8_t* o, const uint32_t* w, int n_valid) {
+  static_assert(N % 4 != 0 && N >= 3, "runs of 3 or more bytes that are not whole words");
+  constexpr int NW = (N + 3) / 4;      // words of the run in w
+  constexpr int NX = (N + 3 + 3) / 4;  // words a run spans at offsets 0..3
+  const int a = (int)(reinterpret_cast<uintptr_t>(o) & 3u), sh = 8 * a;
+  uint32_t x[NX];
+  x[0] = w[0] << sh;
+#pragma unroll
+  for (int k = 1; k < NX; ++k) x[k] = __funnelshift_l(w[k - 1], k < NW ? w[k] : 0u, sh);
+  const uint32_t next = __shfl_down_sync(0xffffffffu, x[0], 1);
+  const uint32_t carry = ((a + N) & 3) ? next : 0u;
+  const int end = a + (n_valid < N ? n_valid : N);  // n_valid < N: the row's end, a word boundary
+  uint32_t* const base = reinterpret_cast<uint32_t*>(o - a);
+#pragma unroll
+  for (int k = 0; k < NX; ++k)
+    if ((k > 0 || a == 0) && 4 * k < end) base[k] = (4 * k + 4 > a + N) ? (x[k] | carry) : x[k];
 }
 
 // uint8 data: exact integer arithmetic with packed bytes.  A window row holds
@@ -803,9 +832,14 @@ struct RowMath<Cl, true> {
       r.w[k] = pack4(v[e], e + 1 < N ? v[e + 1] : 0, e + 2 < N ? v[e + 2] : 0, e + 3 < N ? v[e + 3] : 0);
     }
   }
+  // Runs whose length is not a whole number of words are stored as words
+  // (store_words) when `words` is set (the same for every lane of the warp),
+  // else as bytes.  Not for runs of 3 bytes: there the shifts and the
+  // shuffle cost as much as the byte stores they replace (measured slower).
+  static constexpr bool kWordRuns = N % 4 != 0 && N >= 6 && (Cl::SBLK * P * C) % 4 == 0;
   template <bool CHECK, class PR>
   __device__ static __forceinline__ void v(const Row (&win)[LV], const PR& prm, T* obase, long long rowe,
-                                           int rr, int OH, int n_valid) {
+                                           int rr, int OH, int n_valid, bool words) {
     // one word column g (4 output columns) at a time: row-pair words
     // pl = bytes 0,1 of rows 2m and 2m+1 interleaved, ph = bytes 2,3
     uint32_t o[PV][NW];
@@ -840,7 +874,15 @@ struct RowMath<Cl, true> {
 #pragma unroll
     for (int jv = 0; jv < PV; ++jv) {
       const int oy = rr * PV + jv;
-      if (!CHECK || oy < OH) store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
+      if (!CHECK || oy < OH) {
+        if constexpr (kWordRuns) {
+          if (words) {
+            store_words<N>(obase + (long long)oy * rowe, o[jv], n_valid);
+            continue;
+          }
+        }
+        store_bytes<N>(obase + (long long)oy * rowe, o[jv], n_valid);
+      }
     }
   }
 };
@@ -918,6 +960,10 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     T* const obase = reinterpret_cast<T*>(jd.out) + (long long)(frame0 + sub) * jd.out_frame +
                      (long long)blk0 * Cl::P * Cl::C;
     const long long rowe = (long long)jd.OW * Cl::C;
+    // uint8 runs of a length that is not whole words: stored as words when the
+    // output and its rows start on word boundaries (the same choice for the
+    // whole warp), else as bytes
+    const bool words = sizeof(T) == 1 && (reinterpret_cast<uintptr_t>(jd.out) & 3u) == 0 && (rowe & 3) == 0;
 
     auto issue = [&](int s) {  // stage s of the tile into slot (g + s) mod NST
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
@@ -1100,19 +1146,27 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
               if (row_ok(sb + r * Cl::BOXB)) load_row<Cl>(sb + r * Cl::BOXB, of, w);
               RM::h(w, prm, win[i]);
             } else {
-              // rows below the frame's last repeat it (filtered from the zero
-              // fill, then replaced: a select, not a branch); modular tilers
-              // loaded the frame's first rows there
-              const int y = ys + m * Q + i;
               hrow_regs(sb + r * Cl::BOXB, win[i]);
-              if (y >= H && !wrap) RM::copy(win[i], win[i - 1]);
             }
             if (q == Q - 1) {
+              // rows below the frame's last repeat it: filtered from the zero
+              // fill, then replaced, once per block and only in blocks that
+              // reach below the frame (modular tilers loaded the frame's
+              // first rows there)
+              if constexpr (!FAST && !WRAP) {
+                if (ys + m * Q + L - 1 >= H) {
+#pragma unroll
+                  for (int i2 = L - Q; i2 < L; ++i2)
+                    if (ys + m * Q + i2 >= H) RM::copy(win[i2], win[i2 - 1]);
+                }
+              }
               // the window holds block m's pattern: its P output rows
+              // (a lane whose rows fail the bounds check stores nothing but
+              // still runs the V pass: its stores may shuffle across lanes)
               if constexpr (FAST) {
-                if (store_ok(rb0 + m)) RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+                RM::template v<false>(win, prm, obase, rowe, rb0 + m, jd.OH, store_ok(rb0 + m) ? n_valid : 0, words);
               } else if (!Cl::PRO || m >= 0) {
-                if (store_ok(rb0 + m)) RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, n_valid);
+                RM::template v<true>(win, prm, obase, rowe, rb0 + m, jd.OH, store_ok(rb0 + m) ? n_valid : 0, words);
               }
 #pragma unroll
               for (int i2 = 0; i2 < L - Q; ++i2) RM::copy(win[i2], win[i2 + Q]);
@@ -1159,9 +1213,6 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     }
   }
 }
-
-// Exercise of the timeout path: one warp waits, with the kernels' bounded
-// wait, on an mbarrier that nothing will ever complete (no copy is issued
 
 // ---------------------------------------------------------------------------
 // host side of one class and shape
