@@ -374,6 +374,9 @@ int plan_bands(const FastJob* jobs, int n, int pipelines, BandedJob* out) {
 
 std::string check_plan(const ds_plan* pl) {
   if (pl->fast_class < 0 || pl->fast_class >= kFcCount) return std::string();
+  // rows that are not whole 16-byte units never reach the fast kernel (every
+  // launch of the plan takes the general one)
+  if (((size_t)pl->in_w * pl->channels * pl->elem_size) % 16 != 0) return std::string();
   JobDesc jd;
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);

@@ -136,29 +136,43 @@ def test_fused_kernel_index_arithmetic_host_check():
 
 
 def test_fast_kernel_host_check_on_random_shapes():
-    """ds_debug_check_plan over seeded random frame sizes and bands for every
-    fast class (host replay of the kernel's index arithmetic, no GPU)."""
+    """ds_debug_check_plan over seeded random frame sizes, bands, tile shapes
+    and boundaries for every fast class (host replay of the kernel's index
+    arithmetic, no GPU)."""
     rng = np.random.default_rng(77)
     specs = [((3, 8), 8, (3, 8), 8), ((1, 2), 6, (1, 2), 6), ((2, 3), 6, (2, 3), 6), ((3, 8), 8, (4, 9), 8)]
     checked = 0
-    for _ in range(150):
+    for _ in range(200):
         rh, kh, rv, kv = specs[rng.integers(len(specs))]
         dt = [ds.DS_F32, ds.DS_F16, ds.DS_U8, ds.DS_U8_RGB][rng.integers(4)]
+        bnd = ds.DS_WRAP if rng.random() < 0.3 else ds.DS_CLAMP
         H = int(rng.integers(1, 700))
         W = 16 * int(rng.integers(1, 160))
         try:
-            pl = ds.ds_plan_create_ex(H, W, rh, kh, rv, kv, dt)
+            pl = ds.ds_plan_create_ex(H, W, rh, kh, rv, kv, dt, bnd)
         except ds.DsError:
             continue
         try:
             if '"fused_tma"' not in ds.ds_plan_describe(pl):
                 continue
-            ds.ds_plan_set_schedule(pl, int(rng.integers(1, 40)), 0)
+            ds.ds_plan_set_schedule_ex(pl, int(rng.integers(1, 40)), 0, int(rng.integers(ds.ds_plan_tile_shapes(pl))))
             ds.ds_debug_check_plan(pl)
             checked += 1
         finally:
             ds.ds_destroy(pl)
-    assert checked > 60
+    assert checked > 80
+
+
+def test_host_check_passes_rows_the_fast_kernel_never_takes():
+    """A plan whose rows are not whole 16-byte units keeps its fast class
+    (ds_plan_describe) but every launch of it takes the general kernel, so
+    the replay has nothing to check: a 200-pixel one-plane row with modular
+    tilers, whose strip copies could not start on 16-byte boundaries."""
+    pl = ds.ds_plan_create_ex(17, 200, (3, 8), 8, (4, 9), 8, ds.DS_U8, ds.DS_WRAP)
+    try:
+        ds.ds_debug_check_plan(pl)
+    finally:
+        ds.ds_destroy(pl)
 
 
 def test_normal_build_is_not_bounds_checked():
