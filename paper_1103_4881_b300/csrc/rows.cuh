@@ -420,14 +420,17 @@ struct EdgeFix {
 };
 
 template <class Cl>
-__host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int W) {
+__host__ __device__ __forceinline__ EdgeFix edge_fix(int strip, int W, int OW) {
   const int seg0 = strip * Cl::SPX - Cl::LH;             // first pixel the warp reads
   const int seg1 = (strip + 1) * Cl::SPX + Cl::RH;       // one past the last
   EdgeFix f;
   f.l_lo = seg0;
   f.nl = seg0 < 0 ? ((seg1 < 0 ? seg1 : 0) - seg0) * Cl::C : 0;
   f.r_lo = W > seg0 ? W : seg0;
-  const int lim = W + Cl::NB * Cl::Q + Cl::RH;  // active lanes read no further
+  // active lanes (those with outputs) read no further than the chunk of the
+  // last of them and its right halo
+  const int npk = (OW + Cl::P - 1) / Cl::P;  // packets with outputs
+  const int lim = ((npk - 1) / Cl::NB + 1) * Cl::NB * Cl::Q + Cl::RH;
   const int r_hi = seg1 < lim ? seg1 : lim;
   f.nr = r_hi > f.r_lo ? (r_hi - f.r_lo) * Cl::C : 0;
   return f;
@@ -946,7 +949,7 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     const int ystream = ys + Cl::YOFF;  // frame row of stage 0's first row
     const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;  // window start, in elements
     const int xt = xw * Cl::SZ / kTmaElem;                          // ... in TMA elements (exact)
-    const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W);
+    const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W, jd.OW);
     constexpr bool wrap = WRAP;
     const bool fixing = !wrap && fix.nl + fix.nr > 0;
     const int frame0 = tl.frame * Cl::FPW;              // the group's first frame
@@ -1310,7 +1313,7 @@ std::string check_rows(const JobDesc& jd) {
         if (rowb % 16 || lo % 16 || hi % 16) return fail("row copy not 16-byte aligned", (int)lo, (int)hi);
         if (-lo > rowb || hi - rowb > rowb || m1 <= m0) return fail("row copy beyond one period", (int)lo, (int)hi);
       }
-      const EdgeFix fx = edge_fix<Cl>(strip, jd.W);
+      const EdgeFix fx = edge_fix<Cl>(strip, jd.W, jd.OW);
       for (int e = 0; e < (wrap ? 0 : fx.nl + fx.nr); ++e) {
         const bool left = e < fx.nl;
         const int k2 = left ? e : e - fx.nl;
