@@ -276,12 +276,10 @@ ds_status job_tensor_map(const FastJob& job, CUtensorMap* out) {
 }
 
 ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
-  if (job.plan->boundary == DS_WRAP) {
-    std::memset(&jd.tmap, 0, sizeof(jd.tmap));  // modular tilers copy rows by themselves
-  } else {
-    ds_status s = job_tensor_map(job, &jd.tmap);
-    if (s != DS_OK) return s;
-  }
+  // (modular tilers too: their stages that lie inside the frame take the
+  // tensor copy, the others row copies)
+  ds_status s = job_tensor_map(job, &jd.tmap);
+  if (s != DS_OK) return s;
   fill_job_geometry(jd, job.plan, job.out, job.n_frames, band);
   jd.in = static_cast<const uint8_t*>(job.in);
   return DS_OK;

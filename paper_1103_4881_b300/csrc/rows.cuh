@@ -1010,13 +1010,18 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
           tma_load_3d(ring + slot * Cl::RSTAGE + f * Cl::FSTR + bx * Cl::BOXSTR, &jd.tmap, &full[slot],
                       xt + bx * Cl::BOXE, ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0), frame0 + f);
     };
-    // Modular tilers: every row of a stage is copied by itself from frame row
-    // (y mod H), the window's bytes left of the row from the row's last bytes
-    // and those past its end from its first bytes (one 1-D bulk copy each,
-    // lane k taking row k); so the stage holds the window modulo the frame
-    // and no border needs fixing.  The plan only takes this path when a
-    // window spans less than one period of the row.
+    // Modular tilers: a stage whose rows and window columns all lie inside
+    // the frame is the tensor copy of the clamped form (classes of one frame
+    // per warp: 4K fp16 440 -> 416 us, 1080p RGB 1/2 474 -> 458 us; the CIF
+    // classes, whose strips are mostly frame edges, measured slower with it:
+    // RGB CIF 187 -> 195 us).  In any other stage every row is copied by
+    // itself from frame row (y mod H), the window's bytes left of the row
+    // from the row's last bytes and those past its end from its first bytes
+    // (one 1-D bulk copy each, lane k taking row k); so the stage holds the
+    // window modulo the frame and no border needs fixing.  The plan only
+    // takes this path when a window spans less than one period of the row.
     const long long rowb = (long long)jd.W * Cl::C * Cl::SZ;
+    const bool cols_inside = (long long)xw * Cl::SZ >= 0 && (long long)xw * Cl::SZ + Cl::WINB <= rowb;
     auto issue_wrap = [&](int s) {  // all lanes
       const uint32_t G = g + (uint32_t)s, slot = G % NST;
       if (lane == 0) mbar_expect_tx(&full[slot], (uint32_t)(nf * SR * Cl::WINB));
@@ -1024,8 +1029,10 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
       const long long lo = (long long)xw * Cl::SZ, hi = lo + Cl::WINB;  // window bytes within the row
       for (int k = lane; k < nf * SR; k += 32) {
         const int f = k / SR, r = k - f * SR;
-        int y = (ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0) + r) % H;
-        if (y < 0) y += H;
+        int y = ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0) + r;
+        if (y < 0) y += H;  // within one period of the frame: no division
+        else if (y >= H) y -= H;
+        if ((unsigned)y >= (unsigned)H) y = ((y % H) + H) % H;  // frames of fewer rows than a window
         const uint8_t* row = jd.in + ((long long)(frame0 + f) * H + y) * rowb;
         uint8_t* dst = ring + slot * Cl::RSTAGE + f * Cl::FSTR + r * Cl::BOXB;
         const long long m0 = lo > 0 ? lo : 0, m1 = hi < rowb ? hi : rowb;
@@ -1044,8 +1051,14 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
         if (hi > rowb) bulk_load(dst + (rowb - lo), row, (uint32_t)(hi - rowb), &full[slot]);
       }
     };
+    // fill stage s of modular tilers (all lanes call it)
+    auto fill_wrap = [&](int s) {
+      const int y0 = ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0);
+      if (Cl::FPW > 1 || !(cols_inside && y0 >= 0 && y0 + SR <= H)) issue_wrap(s);
+      else if (lane == 0) issue(s);
+    };
     if constexpr (WRAP) {
-      for (int s = 0; s < NST && s < nst; ++s) issue_wrap(s);
+      for (int s = 0; s < NST && s < nst; ++s) fill_wrap(s);
     } else {
       if (lane == 0)
         for (int s = 0; s < NST && s < nst; ++s) issue(s);
@@ -1065,7 +1078,7 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     auto stage_release = [&](int s) {
       __syncwarp();
       if (s + NST < nst) {
-        if constexpr (WRAP) issue_wrap(s + NST);
+        if constexpr (WRAP) fill_wrap(s + NST);
         else if (lane == 0) issue(s + NST);
         issued = g + (uint32_t)(s + NST + 1);
       }
