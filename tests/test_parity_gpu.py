@@ -77,6 +77,29 @@ def test_schedule_does_not_change_bits(oracle, rb):
             ds.ds_destroy(pl)
 
 
+@pytest.mark.parametrize("ratio,K", FAST)
+@pytest.mark.parametrize("W", [356, 364, 1924, 100, 260, 268])
+def test_right_border_where_the_last_packet_ends(oracle, W, ratio, K):
+    """The right border fix covers only what the frame's last lane with
+    outputs reads.  fp32 rows of 4 (mod 8) pixels take the fast kernel and put
+    the end of that lane's last packet past the row's end (3/8), on it (1/2)
+    or before it (2/3 at widths 1 (mod 3)): every output matches the oracle,
+    and the fused, general and unfused forms agree bit for bit."""
+    H = 23
+    pl, x, got = _case(oracle, H, W, ratio, K, ds.DS_F32, n=3, seed=W)
+    try:
+        assert '"fused_tma"' in ds.ds_plan_describe(pl)
+        np.testing.assert_array_equal(run_unfused(pl, x), got)
+    finally:
+        ds.ds_destroy(pl)
+    with general_kernel():
+        pg = ds.ds_plan_create(H, W, ratio, K, ds.DS_F32)
+    try:
+        np.testing.assert_array_equal(run_fused(pg, x), got)
+    finally:
+        ds.ds_destroy(pg)
+
+
 @pytest.mark.parametrize("H,W,ratio,K,dt", [
     (37, 61, (3, 8), 8, ds.DS_F32),      # odd width: general kernel
     (5, 7, (1, 2), 6, ds.DS_F16),
