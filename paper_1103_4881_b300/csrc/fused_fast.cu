@@ -204,6 +204,8 @@ const ClassTaps& class_taps(int cls) {
 // row blocks per tile, 0 = the plan's.
 void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, int band = 0) {
   const HostGeom& hg = entry_of(pl).geom;
+  jd.nar = 0;
+  jd.strip0 = 0;
   jd.out = out;
   jd.out_frame = (long long)pl->out_frame_elems();
   jd.H = pl->in_h;
@@ -223,16 +225,19 @@ void fill_job_geometry(JobDesc& jd, const ds_plan* pl, void* out, int n_frames, 
 }
 
 // The tensor map of a job's input: 3-D (row bytes / 8 eight-byte elements, H
-// rows, n frames), boxes of the shape's strip window by its stage rows.
-// Plans keep the maps of their last few (input, frame count, shape) in a
-// small cache, so repeated launches on the same buffers skip the encode.
-ds_status job_tensor_map(const FastJob& job, CUtensorMap* out) {
+// rows, n frames), boxes of the shape's strip window by its stage rows.  A
+// narrow tail strip's map orders the axes (x, frame, row) instead, with boxes
+// of its window by 2 frames by the stage rows, so that a box lands two
+// frames' windows side by side in each row.  Plans keep the maps of their
+// last few (input, frame count, shape, kind) in a small cache, so repeated
+// launches on the same buffers skip the encode.
+ds_status job_tensor_map(const FastJob& job, CUtensorMap* out, bool narrow = false) {
   const ds_plan* pl = job.plan;
   TmapCache* tc = pl->tmaps.get();
   if (tc) {
     std::lock_guard<std::mutex> lock(tc->mu);
     for (TmapCache::Entry& e : tc->e)
-      if (e.used && e.in == job.in && e.n_frames == job.n_frames && e.shape == pl->shape) {
+      if (e.used && e.in == job.in && e.n_frames == job.n_frames && e.shape == pl->shape && e.narrow == narrow) {
         e.stamp = ++tc->clock;
         std::memcpy(out, &e.map, sizeof(CUtensorMap));
         return DS_OK;
@@ -248,6 +253,15 @@ ds_status job_tensor_map(const FastJob& job, CUtensorMap* out) {
   cuuint64_t dims[3] = {row_bytes / kTmaElem, (cuuint64_t)pl->in_h, (cuuint64_t)job.n_frames};
   cuuint64_t strides[2] = {row_bytes, row_bytes * (cuuint64_t)pl->in_h};
   cuuint32_t box[3] = {(cuuint32_t)hg.boxe, (cuuint32_t)hg.sr, 1};
+  if (narrow) {
+    dims[1] = (cuuint64_t)job.n_frames;
+    dims[2] = (cuuint64_t)pl->in_h;
+    strides[0] = row_bytes * (cuuint64_t)pl->in_h;
+    strides[1] = row_bytes;
+    box[0] = (cuuint32_t)(hg.wn / kTmaElem);
+    box[1] = 2;
+    box[2] = (cuuint32_t)hg.sr;
+  }
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(out, hg.dt, 3, const_cast<void*>(job.in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -269,10 +283,41 @@ ds_status job_tensor_map(const FastJob& job, CUtensorMap* out) {
     victim->in = job.in;
     victim->n_frames = job.n_frames;
     victim->shape = pl->shape;
+    victim->narrow = narrow;
     victim->stamp = ++tc->clock;
     std::memcpy(&victim->map, out, sizeof(CUtensorMap));
   }
   return DS_OK;
+}
+
+// Whether a plan's frames take a narrow tail-strip job: one-channel classes
+// with frame pairs, clamp-to-edge tilers, a last strip of at most npn packets
+// whose border fix is at most one element per lane of the four frames.
+bool narrow_split(const ds_plan* pl) {
+  const RowsEntry& e = entry_of(pl);
+  if (!e.geom.narrow || pl->boundary == DS_WRAP) return false;
+  const int npk = (pl->out_w + e.geom.p - 1) / e.geom.p;  // packets with outputs
+  const int strips = (npk + e.geom.sblk - 1) / e.geom.sblk;
+  return npk - (strips - 1) * e.geom.sblk <= e.geom.npn && e.narrow_fix(strips - 1, pl->in_w, pl->out_w) <= 32;
+}
+
+// Split a job descriptor (geometry filled) into the job without its last
+// strip (none if that was its only strip) and the last strip's narrow job,
+// four frames per tile.  Returns the number of descriptors written to out.
+int split_narrow_geometry(const JobDesc& full, JobDesc* out) {
+  int n = 0;
+  if (full.strips > 1) {
+    out[n] = full;
+    out[n].strips = full.strips - 1;
+    out[n].tiles = out[n].strips * full.chunks * ((full.nframes + 1) / 2);
+    ++n;
+  }
+  out[n] = full;
+  out[n].nar = 1;
+  out[n].strip0 = full.strips - 1;
+  out[n].strips = 1;
+  out[n].tiles = full.chunks * ((full.nframes + 3) / 4);
+  return n + 1;
 }
 
 ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
@@ -283,6 +328,22 @@ ds_status encode_job(JobDesc& jd, const FastJob& job, int band) {
   fill_job_geometry(jd, job.plan, job.out, job.n_frames, band);
   jd.in = static_cast<const uint8_t*>(job.in);
   return DS_OK;
+}
+
+// The descriptors of one job: encode_job's, or with `narrow` its split into
+// the job without the last strip and the narrow tail-strip job (which gets
+// its own tensor map).  Returns the number written to out (1 or 2).
+ds_status encode_job_split(JobDesc* out, int room, const FastJob& job, int band, bool narrow, int* n) {
+  JobDesc full;
+  ds_status s = encode_job(full, job, band);
+  if (s != DS_OK) return s;
+  if (!narrow || room < 2) {
+    out[0] = full;
+    *n = 1;
+    return DS_OK;
+  }
+  *n = split_narrow_geometry(full, out);
+  return job_tensor_map(job, &out[*n - 1].tmap, true);
 }
 
 // Band heights (output row blocks per tile) of the jobs of one launch.  A
@@ -375,10 +436,12 @@ std::string check_plan(const ds_plan* pl) {
   // rows that are not whole 16-byte units never reach the fast kernel (every
   // launch of the plan takes the general one)
   if (((size_t)pl->in_w * pl->channels * pl->elem_size) % 16 != 0) return std::string();
-  JobDesc jd;
+  JobDesc jd, jds[2];
   std::memset(&jd, 0, sizeof(jd));
   fill_job_geometry(jd, pl, nullptr, 1);
-  return entry_of(pl).check(jd);
+  if (!narrow_split(pl)) return entry_of(pl).check(&jd, 1);
+  const int n = split_narrow_geometry(jd, jds);
+  return entry_of(pl).check(jds, n);
 }
 
 // ---------------------------------------------------------------------------
@@ -461,19 +524,26 @@ void give_direct_slot(DirectSlots* ds_, int slot, cudaStream_t st, bool launched
 }
 
 // Fill the launch parameters and launch.
+// `narrow`: jobs whose plan takes narrow tail strips get their split (the
+// caller has checked that the descriptors fit).
 template <int MAXJ>
 ds_status launch_with(FastParams<MAXJ>& prm, const KernelInfo& ki, int cls, const ClassTaps& taps,
-                      const BandedJob* banded, int nb, int occ, cudaStream_t st) {
+                      const BandedJob* banded, int nb, int occ, cudaStream_t st, bool narrow) {
   const int per_cta = ki.threads / 32;  // one tile per warp
   prm.t = taps;
-  int tiles = 0;
+  int tiles = 0, nj = 0;
   for (int i = 0; i < nb; ++i) {
-    ds_status s = encode_job(prm.jobs[i], banded[i].job, banded[i].band);
+    int k = 0;
+    ds_status s = encode_job_split(prm.jobs + nj, MAXJ - nj, banded[i].job, banded[i].band,
+                                   narrow && narrow_split(banded[i].job.plan), &k);
     if (s != DS_OK) return s;
-    prm.jobs[i].tile_begin = tiles;
-    tiles += prm.jobs[i].tiles;
+    for (int m = nj; m < nj + k; ++m) {
+      prm.jobs[m].tile_begin = tiles;
+      tiles += prm.jobs[m].tiles;
+    }
+    nj += k;
   }
-  prm.n_jobs = nb;
+  prm.n_jobs = nj;
   prm.total_tiles = tiles;
   if (tiles == 0) return DS_OK;
   prm.dev = dev_state();
@@ -535,13 +605,23 @@ ds_status launch_chunk(const FastJob* jobs, int n, cudaStream_t st) {
   if (want_ctas > 0) occ = std::min(occ, want_ctas);
   BandedJob banded[kMaxJobs];
   const int nb = plan_bands(jobs, n, sm_count() * occ * (kmany.threads / 32), banded);
-  if (nb <= kFewJobs) {
+  // descriptors with the narrow tail-strip jobs; without them if they would
+  // not fit one launch
+  int nd = nb;
+  for (int i = 0; i < nb; ++i) {
+    const ds_plan* pl = banded[i].job.plan;
+    const int npk = (pl->out_w + re.geom.p - 1) / re.geom.p;
+    if (narrow_split(pl) && npk > re.geom.sblk) ++nd;  // a second descriptor when the frame has other strips
+  }
+  const bool narrow = nd <= kMaxJobs;
+  if (!narrow) nd = nb;
+  if (nd <= kFewJobs) {
     static thread_local FastParams<kFewJobs> few;
     if (ctas_per_sm(kfew) <= 0) return cuda_fail(cudaGetLastError(), "k_rows attributes");
-    return launch_with(few, kfew, cls, taps, banded, nb, occ, st);
+    return launch_with(few, kfew, cls, taps, banded, nb, occ, st, narrow);
   }
   static thread_local FastParams<kMaxJobs> many;  // ~17 KB: not on the caller's stack
-  return launch_with(many, kmany, cls, taps, banded, nb, occ, st);
+  return launch_with(many, kmany, cls, taps, banded, nb, occ, st, narrow);
 }
 
 }  // namespace

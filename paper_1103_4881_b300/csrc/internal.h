@@ -48,6 +48,7 @@ struct TmapCache {
     CUtensorMap map;  // 64-byte aligned by its type
     const void* in = nullptr;
     int n_frames = 0, shape = 0;
+    bool narrow = false;  // the (x, frame, row) map of a narrow tail strip
     bool used = false;
     unsigned long long stamp = 0;
   };

@@ -181,6 +181,16 @@ struct Cls {
   static constexpr int NVT = HB + NV + HA;             // vectors per lane and row
   static constexpr int NWT = NVT * VB / 4;             // words per lane and row
   static constexpr int NOUT = NB * P * C;              // H outputs per lane and row
+  // Narrow tail strips (one-channel classes with frame pairs): a frame's last
+  // strip, when it has at most NPN packets, is filtered four frames per warp
+  // in groups of 8 lanes.  Its window (WN bytes: NPN packets and the halo) is
+  // half a box row, so one TMA box of (WN bytes, 2 frames, SR rows) puts two
+  // frames' windows side by side at the usual row pitch: four frames fill
+  // exactly the stage of a frame pair, with the same bytes per stage.
+  static constexpr int NPN = (BOXB / 2 - HLB - RHB) / (Q * C * SZ);
+  static constexpr int WN = HLB + NPN * Q * C * SZ + RHB;
+  static constexpr bool NARROW =
+      FPW_ == 2 && C_ == 1 && NB_ == 1 && NBOX == 1 && NPN >= 1 && NPN <= 8 && 2 * WN == BOXB && WN % 16 == 0;
   // vertical axis: the row stream and the register window
   static constexpr int BMINV = phase_b(PV, QV, KV, 0);
   static constexpr int BMAXV = phase_b(PV, QV, KV, PV - 1);
@@ -237,6 +247,8 @@ struct JobDesc {
   int rbc, tile_begin, tiles, out_vec;
   const uint8_t* in;       // the frames, for the row copies of modular tilers
   int wrap;                // 1: modular tilers (launched on the WRAP kernels)
+  int nar;                 // 1: a narrow tail strip (four frames per warp; tmap is (x, frame, row))
+  int strip0;              // the job's first strip of the frame
 };
 static_assert(sizeof(JobDesc) == 256 && alignof(JobDesc) == 128, "job descriptor layout");
 
@@ -393,6 +405,28 @@ __device__ __forceinline__ Offs<Cl> thread_offs(int lane) {
   return o;
 }
 
+// Narrow tail strips: lane group g = lane / 8 holds frame g of the tile; box
+// g / 2 of the stage holds frames 2(g/2) and 2(g/2) + 1 side by side, WN
+// bytes each, in rows of BOXB bytes.  Offset of byte `byte` of the window
+// row 0 of group g.
+template <class Cl>
+__host__ __device__ __forceinline__ int narrow_base(int g) {
+  return (g >> 1) * Cl::FSTR + (g & 1) * Cl::WN;
+}
+
+// The lane's vector offsets in a narrow tail strip.  Lanes past the window's
+// NPN packets (never active: their packets lie past the frame's last one)
+// read the last packet's vectors.
+template <class Cl>
+__device__ __forceinline__ Offs<Cl> thread_offs_narrow(int lane) {
+  Offs<Cl> o;
+  const int g = lane >> 3, li = min(lane & 7, Cl::NPN - 1);
+  const int first = narrow_base<Cl>(g) + Cl::HLB + li * Cl::EB - Cl::HB * Cl::VB;
+#pragma unroll
+  for (int v = 0; v < Cl::NVT; ++v) o.v[v] = first + v * Cl::VB;
+  return o;
+}
+
 // Load the lane's vectors of one window row into words w[0..NWT).
 template <class Cl>
 __device__ __forceinline__ void load_row(const uint8_t* rowbase, const Offs<Cl>& o, uint32_t* w) {
@@ -449,6 +483,18 @@ __device__ __forceinline__ void edge_elem(const EdgeFix& f, int e2, int W, int x
   const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
   src = sub * Cl::FSTR + win_off<Cl>(((left ? 0 : W - 1) * Cl::C + c - xw) * Cl::SZ);
   dst = sub * Cl::FSTR + win_off<Cl>((px * Cl::C + c - xw) * Cl::SZ);
+}
+
+// The same for a narrow tail strip (four frames, at most one element per lane).
+template <class Cl>
+__device__ __forceinline__ void edge_elem_narrow(const EdgeFix& f, int e2, int W, int xw, int& src, int& dst) {
+  const int n = f.nl + f.nr;
+  const int g = e2 / n, e = e2 - g * n;
+  const bool left = e < f.nl;
+  const int k = left ? e : e - f.nl;
+  const int px = (left ? f.l_lo : f.r_lo) + k / Cl::C, c = k % Cl::C;
+  src = narrow_base<Cl>(g) + ((left ? 0 : W - 1) * Cl::C + c - xw) * Cl::SZ;
+  dst = narrow_base<Cl>(g) + (px * Cl::C + c - xw) * Cl::SZ;
 }
 
 // One element's copy in all SR rows of a stage.
@@ -937,7 +983,6 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncwarp();
-  const Offs<Cl> of = thread_offs<Cl>(lane);
   const unsigned nwarps = gridDim.x * WPC;
   unsigned* const next = &prm.dev->tile_next[prm.sched_slot];
   // the first tile of every warp is its warp index (so the launch does not
@@ -965,9 +1010,15 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     const int ys = rb0 * Q + Cl::BMINV;  // first pattern row; < 0 only for the top band (then == BMINV)
     const int nst = Cl::STG0 + ((nblk + Cl::VBLK) * Q + SR - 1) / SR;
     const int ystream = ys + Cl::YOFF;  // frame row of stage 0's first row
-    const int xw = tl.strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;  // window start, in elements
+    // a narrow tail strip (its own job): four frames per warp in 8-lane
+    // groups, the windows of frames 2k and 2k + 1 side by side in box k
+    const bool nar = !WRAP && Cl::NARROW && jd.nar != 0;
+    const int fpw = nar ? 4 : Cl::FPW, lps = nar ? 8 : Cl::LPS;
+    const int strip = Cl::NARROW ? jd.strip0 + tl.strip : tl.strip;  // the strip of the frame
+    const Offs<Cl> of = nar ? thread_offs_narrow<Cl>(lane) : thread_offs<Cl>(lane);
+    const int xw = strip * Cl::SPX * Cl::C - Cl::HLB / Cl::SZ;  // window start, in elements
     const int xt = xw * Cl::SZ / kTmaElem;                          // ... in TMA elements (exact)
-    const EdgeFix fix = edge_fix<Cl>(tl.strip, jd.W, jd.OW);
+    const EdgeFix fix = edge_fix<Cl>(strip, jd.W, jd.OW);
     constexpr bool wrap = WRAP;
     const bool fixing = !wrap && fix.nl + fix.nr > 0;
     // a fix of at most one element per lane: the lane's offsets, once per
@@ -975,13 +1026,16 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
     // -1.9 %, 4:2:0 CIF -3.8 %); three-channel classes keep the per-stage
     // offsets, which measured faster there (RGB CIF +2.3 % per tile, 1080p
     // RGB 1/2 unchanged)
-    const bool fix_one = Cl::C == 1 && Cl::FPW * (fix.nl + fix.nr) <= 32;
+    const bool fix_one = nar || (Cl::C == 1 && Cl::FPW * (fix.nl + fix.nr) <= 32);  // narrow: at most 32 (host)
     int fix_src = 0, fix_dst = -1;
-    if (fixing && fix_one && lane < Cl::FPW * (fix.nl + fix.nr)) edge_elem<Cl>(fix, lane, jd.W, xw, fix_src, fix_dst);
-    const int frame0 = tl.frame * Cl::FPW;              // the group's first frame
-    const int nf = Cl::FPW == 1 ? 1 : min(Cl::FPW, jd.nframes - frame0);  // frames in the group
-    const int sub = lane / Cl::LPS;                     // this lane's frame in the group
-    const int blk0 = tl.strip * Cl::SBLK + (lane % Cl::LPS) * Cl::NB;
+    if (fixing && fix_one && lane < fpw * (fix.nl + fix.nr)) {
+      if (nar) edge_elem_narrow<Cl>(fix, lane, jd.W, xw, fix_src, fix_dst);
+      else edge_elem<Cl>(fix, lane, jd.W, xw, fix_src, fix_dst);
+    }
+    const int frame0 = tl.frame * fpw;                  // the group's first frame
+    const int nf = Cl::FPW == 1 ? 1 : min(fpw, jd.nframes - frame0);  // frames in the group
+    const int sub = lane / lps;                         // this lane's frame in the group
+    const int blk0 = strip * Cl::SBLK + (lane % lps) * Cl::NB;
     const bool active = sub < nf && blk0 * Cl::P < jd.OW;
     // elements this lane stores per output row (none for an inactive lane,
     // which runs the same code on in-window data with its stores masked)
@@ -1002,6 +1056,14 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
           mbar_expect_tx(&full[slot], 0u);  // completes the phase with no copy
           return;
         }
+      }
+      if (nar) {  // box k: frames frame0 + 2k and + 2k + 1 (x, frame, row map)
+        const int nbx = (nf + 1) >> 1;
+        mbar_expect_tx(&full[slot], (uint32_t)(nbx * Cl::RTX));
+        for (int k = 0; k < nbx; ++k)
+          tma_load_3d(ring + slot * Cl::RSTAGE + k * Cl::FSTR, &jd.tmap, &full[slot], xt, frame0 + 2 * k,
+                      ystream + s * SR + (s == 0 ? Cl::S0SHIFT : 0));
+        return;
       }
       mbar_expect_tx(&full[slot], (uint32_t)(nf * Cl::RTX));
       for (int f = 0; f < nf; ++f)
@@ -1221,7 +1283,7 @@ __global__ void __launch_bounds__(Cl::WPC * 32, Cl::MINB) k_rows(const __grid_co
       }
     };
     // every frame of the group present
-    const bool group_full = nf == Cl::FPW;
+    const bool group_full = nf == fpw;
     const int nunits = (nblk + Cl::VBLK + Cl::UBLK - 1) / Cl::UBLK;
     for (int u = 0; ok && u < nunits; ++u) {
       if constexpr (Cl::FASTPATH) {
@@ -1263,6 +1325,8 @@ struct HostGeom {
   int sblk, spx, p, q, pv, boxe, sr, sz, c, fpw;
   CUtensorMapDataType dt;
   int hlb, rhb;  // halo bytes of a strip's window, left and right
+  bool narrow;   // narrow tail strips: last strips of at most npn packets, windows of wn bytes
+  int npn, wn;
 };
 
 struct KernelInfo {
@@ -1279,14 +1343,15 @@ struct RowsEntry {
   HostGeom geom;
   KernelInfo few, many;       // clamp-to-edge
   KernelInfo few_wrap, many_wrap;
-  std::string (*check)(const JobDesc& jd);
+  std::string (*check)(const JobDesc* jds, int njobs);
   int nb, sr, nst, wpc, minb;
+  int (*narrow_fix)(int strip, int W, int OW);  // border-fix elements of a narrow strip's four frames
 };
 
 template <class Cl>
 HostGeom host_geom() {
   return HostGeom{Cl::SBLK, Cl::SPX, Cl::P, Cl::Q, Cl::PV, Cl::BOXE, Cl::SRR, Cl::SZ, Cl::C, Cl::FPW, kTmaType,
-                  Cl::HLB, Cl::RHB};
+                  Cl::HLB, Cl::RHB, Cl::NARROW, Cl::NPN, Cl::WN};
 }
 
 // Registers are budgeted for Cl::MINB resident CTAs (of Cl::WPC warps) per SM.
@@ -1309,8 +1374,10 @@ KernelInfo rows_info(bool few) {
 // every V block must see exactly the clamped rows of its window, every
 // stream row must be the next frame row in order, every output element is
 // written once.
+// The jobs of one frame: a plan's one job, or its job without the last strip
+// and the narrow tail-strip job (four frames per warp).
 template <class Cl>
-std::string check_rows(const JobDesc& jd) {
+std::string check_rows(const JobDesc* jds, int njobs) {
   constexpr int WPC = Cl::WPC;
   char buf[256];
   auto fail = [&](const char* what, int a, int b) {
@@ -1321,13 +1388,24 @@ std::string check_rows(const JobDesc& jd) {
   if (smem > 227 * 1024) return fail("shared memory above 227 KB", smem, 0);
   if (Cl::BOXSTR < Cl::SRR * Cl::BOXB || Cl::BOXSTR % 128 != 0) return fail("stage layout", Cl::BOXSTR, 0);
   if (Cl::LPS * Cl::FPW != 32) return fail("lanes per frame", Cl::LPS, Cl::FPW);
-  const int win = Cl::NBOX * Cl::BOXB;
+  if (njobs < 1) return fail("no jobs", njobs, 0);
   // L, Q, P: the vertical axis; PH: the horizontal phases per packet
   constexpr int L = Cl::LV, Q = Cl::QV, P = Cl::PV, PH = Cl::P;
-  std::vector<int> written((size_t)jd.OH * jd.OW * Cl::C, 0);
+  std::vector<int> written((size_t)jds[0].OH * jds[0].OW * Cl::C, 0);
+  for (int jx = 0; jx < njobs; ++jx) {
+  const JobDesc& jd = jds[jx];
+  const bool nar = jd.nar != 0;
+  if (nar && !Cl::NARROW) return fail("narrow job on a class without narrow strips", jx, 0);
+  if (nar && (jd.strips != 1 || jd.wrap)) return fail("narrow job shape", jd.strips, jd.wrap);
+  // a lane's window: the box row (frame pairs), or its half (narrow strips)
+  const int win = nar ? Cl::WN : Cl::NBOX * Cl::BOXB;
+  const int lps = nar ? 8 : Cl::LPS;
+  if (nar && (2 * Cl::WN != Cl::BOXB || 2 * Cl::SRR * Cl::WN != Cl::RTX))
+    return fail("narrow box layout", Cl::WN, Cl::BOXB);
   const int nby = (jd.OH + P - 1) / P;
   for (int chunk = 0; chunk < jd.chunks; ++chunk) {
-    for (int strip = 0; strip < jd.strips; ++strip) {
+    for (int strip_i = 0; strip_i < jd.strips; ++strip_i) {
+      const int strip = jd.strip0 + strip_i;
       const int rb0 = chunk * jd.rbc;
       const int nblk = std::min(jd.rbc, nby - rb0);
       if (nblk < 1) return fail("empty tile", chunk, strip);
@@ -1353,6 +1431,7 @@ std::string check_rows(const JobDesc& jd) {
         if (-lo > rowb || hi - rowb > rowb || m1 <= m0) return fail("row copy beyond one period", (int)lo, (int)hi);
       }
       const EdgeFix fx = edge_fix<Cl>(strip, jd.W, jd.OW);
+      if (nar && 4 * (fx.nl + fx.nr) > 32) return fail("narrow border fix above one element per lane", fx.nl, fx.nr);
       for (int e = 0; e < (wrap ? 0 : fx.nl + fx.nr); ++e) {
         const bool left = e < fx.nl;
         const int k2 = left ? e : e - fx.nl;
@@ -1362,8 +1441,9 @@ std::string check_rows(const JobDesc& jd) {
           return fail("edge fix outside the window", src, dst);
       }
       // every frame of a warp's group has the same window layout: lanes li of the strip
-      for (int lane = 0; lane < Cl::LPS; ++lane) {
-        const int first = Cl::HLB + lane * Cl::EB - Cl::HB * Cl::VB;
+      for (int lane = 0; lane < lps; ++lane) {
+        const int li = nar ? std::min(lane, Cl::NPN - 1) : lane;  // narrow: lanes past the window read its last packet
+        const int first = Cl::HLB + li * Cl::EB - Cl::HB * Cl::VB;
         for (int v = 0; v < Cl::NVT; ++v) {
           const int b0 = first + v * Cl::VB;
           if (b0 < 0 || b0 + Cl::VB > win || b0 / Cl::BOXB != (b0 + Cl::VB - 1) / Cl::BOXB)
@@ -1371,6 +1451,9 @@ std::string check_rows(const JobDesc& jd) {
         }
         const int blk0 = strip * Cl::SBLK + lane * Cl::NB, px0 = blk0 * Cl::Q;
         if (blk0 * PH >= jd.OW || wrap) continue;
+        if (nar && (lane >= Cl::NPN || (px0 - Cl::LH) * Cl::C - xw < 0 ||
+                    (px0 + Cl::NB * Cl::Q + Cl::RH) * Cl::C - xw > win / Cl::SZ))
+          return fail("narrow lane's pixels outside its window", lane, px0);
         for (int px = px0 - Cl::LH; px < px0 + Cl::NB * Cl::Q + Cl::RH; ++px) {
           if (px < 0 && !(px >= fx.l_lo && fx.nl > 0)) return fail("left border pixel not fixed", lane, px);
           if (px >= jd.W && !(px >= fx.r_lo && px < fx.r_lo + fx.nr / Cl::C)) return fail("right border pixel not fixed", lane, px);
@@ -1430,7 +1513,7 @@ std::string check_rows(const JobDesc& jd) {
               want = wrap ? wrapped(want) : (want < 0 ? 0 : (want > jd.H - 1 ? jd.H - 1 : want));
               if (wrow[i2] != want) return fail("window row mismatch", i2, wrow[i2]);
             }
-            for (int lane = 0; lane < Cl::LPS; ++lane) {
+            for (int lane = 0; lane < lps; ++lane) {
               const int blk0 = strip * Cl::SBLK + lane * Cl::NB;
               if (blk0 * PH >= jd.OW) continue;
               const int nv = std::min(Cl::NOUT, jd.OW * Cl::C - blk0 * PH * Cl::C);
@@ -1448,9 +1531,16 @@ std::string check_rows(const JobDesc& jd) {
       if (sr != want_rows) return fail("stream rows left over", sr, want_rows);
     }
   }
+  }
   for (size_t i = 0; i < written.size(); ++i)
     if (written[i] != 1) return fail("output element written != 1 times", (int)i, written[i]);
   return std::string();
+}
+
+template <class Cl>
+int narrow_fix_elems(int strip, int W, int OW) {
+  const EdgeFix f = edge_fix<Cl>(strip, W, OW);
+  return 4 * (f.nl + f.nr);
 }
 
 // with_wrap: also compile the class for modular tilers (tile shape 0 only:
@@ -1459,7 +1549,7 @@ template <class Cl, bool WITH_WRAP>
 RowsEntry make_entry() {
   RowsEntry e{true, WITH_WRAP, host_geom<Cl>(), rows_info<Cl, false>(true), rows_info<Cl, false>(false),
               KernelInfo{nullptr, 0, 0}, KernelInfo{nullptr, 0, 0}, &check_rows<Cl>,
-              Cl::NB, Cl::SRR, Cl::NST, Cl::WPC, Cl::MINB};
+              Cl::NB, Cl::SRR, Cl::NST, Cl::WPC, Cl::MINB, &narrow_fix_elems<Cl>};
   if constexpr (WITH_WRAP) {
     e.few_wrap = rows_info<Cl, true>(true);
     e.many_wrap = rows_info<Cl, true>(false);

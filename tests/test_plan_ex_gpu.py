@@ -237,3 +237,68 @@ def test_batch_mixes_given_and_library_taps_of_one_class(oracle):
     finally:
         for pl in plans:
             ds.ds_destroy(pl)
+
+
+# One-plane CIF frames whose last strip has at most 6 packets (width mod 128
+# in {16, 32, 48}): the launch gives that strip a job of its own, filtered
+# four frames per warp in groups of 8 lanes, two frames' windows side by
+# side in each TMA box.
+NARROW_W = [16, 32, 48, 144, 160, 176, 304]
+
+
+@pytest.mark.parametrize("W", NARROW_W)
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 9])
+def test_narrow_tail_strips(oracle, W, n):
+    """Counts that leave the last group of four 1-3 frames short: the missing
+    frames are neither loaded nor written (the output frame after the last,
+    a sentinel, stays untouched), and every output matches the oracle."""
+    import torch
+
+    from tests.gpu_util import finish, stream, to_dev
+    H = 144 if W != 304 else 37  # 37 rows: a ragged last block
+    pl = ds.ds_plan_create_ex(H, W, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        oh, ow, _ = ds.ds_plan_out_shape(pl)
+        x = frames((H, W), ds.DS_U8, n, 500 + W + n)
+        xd = to_dev(x)
+        out = torch.full((n + 1, oh, ow), 201, dtype=torch.uint8, device="cuda")
+        ds.ds_run_frames(pl, xd.data_ptr(), out.data_ptr(), n, stream())
+        finish()
+        got = out.cpu().numpy()
+        assert_parity(got[:n], oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8, "narrow %dx%d n=%d" % (H, W, n))
+        assert (got[n] == 201).all()
+    finally:
+        ds.ds_destroy(pl)
+
+
+def test_narrow_tail_strips_in_one_batch(oracle):
+    """Jobs with and without narrow tail strips, of several frame counts, in
+    one launch; then the same jobs again, each alone, give the same bytes."""
+    from tests.gpu_util import finish, out_buffer, stream, to_dev
+    shapes = [(144, 176, 5), (30, 48, 3), (288, 352, 2), (70, 160, 7), (144, 176, 1)]
+    plans = [ds.ds_plan_create_ex(h, w, (3, 8), 8, (4, 9), 8, ds.DS_U8) for h, w, _ in shapes]
+    try:
+        xs = [frames((h, w), ds.DS_U8, n, 900 + k) for k, (h, w, n) in enumerate(shapes)]
+        ins = [to_dev(a) for a in xs]
+        outs = [out_buffer(pl, n) for pl, (_, _, n) in zip(plans, shapes)]
+        ds.ds_batch_run([(pl, i.data_ptr(), o.data_ptr(), n) for pl, i, o, (_, _, n) in zip(plans, ins, outs, shapes)],
+                        stream())
+        finish()
+        for pl, x, o in zip(plans, xs, outs):
+            got = o.cpu().numpy()
+            assert_parity(got, oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8)
+            np.testing.assert_array_equal(run_fused(pl, x), got)
+    finally:
+        for pl in plans:
+            ds.ds_destroy(pl)
+
+
+def test_narrow_tail_strips_split_tail(oracle):
+    """1201 chroma planes: the launch's last units run in shorter bands, the
+    job split by frames, and each part gets its own narrow tail-strip job."""
+    pl = ds.ds_plan_create_ex(144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        x = frames((144, 176), ds.DS_U8, 1201, 1202)
+        assert_parity(run_fused(pl, x), oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8, "narrow 1201 frames")
+    finally:
+        ds.ds_destroy(pl)
