@@ -71,3 +71,40 @@ def test_extreme_ratios_and_tap_counts(oracle, ratio, K, dt):
         np.testing.assert_array_equal(run_unfused(pl, x), got)
     finally:
         ds.ds_destroy(pl)
+
+
+def _cif_cases(n, seed):
+    """The paper's CIF axes (H 3/8 K=8, V 4/9 K=8): random heights, widths on
+    and off the fast path's 16-byte rows (widths mod 128 in {16, 32, 48} give
+    one-plane frames a narrow tail strip), 1-9 frames, both boundaries, and
+    caller-given taps for some."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        H = int(rng.integers(3, 320))
+        W = 16 * int(rng.integers(1, 50)) if rng.random() < 0.8 else int(rng.integers(3, 500))
+        if W * 3 // 8 < 1 or H * 4 // 9 < 1:
+            continue
+        dt = ds.DS_U8 if rng.random() < 0.6 else ds.DS_U8_RGB
+        out.append((H, W, dt, int(rng.integers(1, 10)), int(rng.random() < 0.2), int(rng.random() < 0.25),
+                    int(rng.integers(1 << 30))))
+    return out
+
+
+@pytest.mark.parametrize("H,W,dt,n,wrap,given,seed", _cif_cases(30, 4881))
+def test_random_cif_plans_match_the_oracle(oracle, H, W, dt, n, wrap, given, seed):
+    rng = np.random.default_rng(seed)
+    wh = wv = None
+    if given:
+        wh, wv = rng.normal(0, 0.2, (3, 8)), rng.normal(0, 0.2, (4, 8))
+        wh[:, 3] += 1.0
+        wv[:, 4] += 1.0
+    pl = ds.ds_plan_create_ex(H, W, (3, 8), 8, (4, 9), 8, dt, ds.DS_WRAP if wrap else ds.DS_CLAMP, wh, wv)
+    try:
+        x = frames((H, W), dt, n, seed % 100000)
+        got = run_fused(pl, x)
+        want = oracle.filter_ex(x, (3, 8), 8, (4, 9), 8, wrap=bool(wrap), weights_h=wh, weights_v=wv)
+        assert_parity(got, want, dt, ds.ds_plan_describe(pl))
+        np.testing.assert_array_equal(run_unfused(pl, x), got)
+    finally:
+        ds.ds_destroy(pl)
