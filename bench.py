@@ -401,14 +401,9 @@ def main():
     fin = fbytes[0][0]
 
     # the schedule: the autotuner's choice for this GPU and workload (cached)
-    schedule = []
-    for pl, xi, o in zip(plans, xins, outs):
-        if args.no_tune or len(plans) > 1:  # planar batches: see side_workloads
-            schedule.append(dict(ds.ds_plan_get_schedule_ex(pl), tuned=False))
-        else:
-            r = tune.apply_or_tune(pl, xi.data_ptr(), o.data_ptr(), n, st, 10)
-            schedule.append(dict(r, tuned=True))
-        schedule[-1]["describe"] = json.loads(ds.ds_plan_describe(pl))
+    schedule = tuned_schedules(args, ds, tune, plans, xins, outs, n, st)
+    for sc, pl in zip(schedule, plans):
+        sc["describe"] = json.loads(ds.ds_plan_describe(pl))
 
     # the step: one batched persistent launch over the n frames (of every
     # plane), replayed as a CUDA graph
@@ -529,6 +524,22 @@ def main():
         pg.destroy_process_group()
 
 
+def tuned_schedules(args, ds, tune, plans, xins, outs, n, st):
+    """The autotuner's schedule for a workload's plans (cached per GPU): one
+    plan is tuned alone, the planes of a planar workload as one batch (they
+    share a launch, whose bands and tail a plan tuned alone does not see);
+    with --no-tune, the plans' defaults.  One entry per plan."""
+    if args.no_tune:
+        return [dict(ds.ds_plan_get_schedule_ex(pl), tuned=False) for pl in plans]
+    if len(plans) > 1:
+        r = tune.apply_or_tune_batch([(pl, xi.data_ptr(), o.data_ptr(), n) for pl, xi, o in zip(plans, xins, outs)],
+                                     st, 10)
+        extra = {k: r[k] for k in ("us_per_launch", "default_us_per_launch", "candidates", "cached") if k in r}
+        return [dict(sc, tuned=True, batch=True, **extra) for sc in r["schedules"]]
+    pl, xi, o = plans[0], xins[0], outs[0]
+    return [dict(tune.apply_or_tune(pl, xi.data_ptr(), o.data_ptr(), n, st, 10), tuned=True)]
+
+
 def side_workloads(args, ds, synth, resident, timed, dev_index, peak):
     """The other workloads, each as its own batched graph launch at the
     autotuner's schedule (as the headline; the default with --no-tune):
@@ -548,14 +559,7 @@ def side_workloads(args, ds, synth, resident, timed, dev_index, peak):
         plans, xs, xins, outs = resident(wl, 0, wl.frames)
         fbytes = [ds.ds_plan_frame_bytes(pl) for pl in plans]
         alg = wl.frames * sum(fi + fo for fi, fo in fbytes)
-        tuned = []
-        for pl, xi, o in zip(plans, xins, outs):
-            # planes share one launch, whose bands and tail the tuner, timing
-            # each plan alone, does not see: planar batches keep the default
-            if args.no_tune or len(plans) > 1:
-                tuned.append(dict(ds.ds_plan_get_schedule_ex(pl), tuned=False))
-            else:
-                tuned.append(dict(tune.apply_or_tune(pl, xi.data_ptr(), o.data_ptr(), wl.frames, st, 10), tuned=True))
+        tuned = tuned_schedules(args, ds, tune, plans, xins, outs, wl.frames, st)
         g = ds.ds_graph_create([(pl, xi.data_ptr(), o.data_ptr(), wl.frames) for pl, xi, o in zip(plans, xins, outs)])
         step = lambda: ds.ds_graph_launch(g, st)
         for _ in range(max(3, args.warmup)):

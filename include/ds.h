@@ -296,6 +296,29 @@ typedef struct {
 ds_status ds_batch_run(const ds_job* jobs, int n, void* stream);
 
 /*
+ * Autotuner of a batch (the launch topology of Sec. 3.B.1 for the whole
+ * video's repetitions at once, measured instead of derived from
+ * thresholds): as ds_plan_autotune_ex, but it times ds_batch_run(jobs, n,
+ * stream) and applies each candidate to every fused-kernel plan of the
+ * batch.  Tiles of all the batch's jobs share one launch per kernel class,
+ * so a plan tuned alone does not see the others' tiles, bands or tail.  The
+ * candidates: every tile shape that all those plans have, at the default
+ * band; fixed bands at the best shape, up to the tallest plan's block rows;
+ * then fewer resident CTAs per SM (one or two fewer, three quarters, half of
+ * what fits each plan's kernel).  The same warm-up, 1 % margin and
+ * alternating confirmation against the default keep the result no slower
+ * than the default as measured.  The jobs' plans keep the chosen schedule
+ * (a plan that also serves other batches runs those at it too); plans on the
+ * general kernels keep theirs.  Output buffers are written during tuning.
+ * Synchronises the stream.  res (if not NULL): the first fused plan's
+ * schedule, the batch's time at the best schedule and at the default (us per
+ * batch), and the number of candidates timed.  DS_ERR_ARG on NULL pointers,
+ * n < 1 or iters < 1; DS_ERR_UNSUPPORTED when no job runs on the fused
+ * kernel; on any other failure the plans keep the schedules they had.
+ */
+ds_status ds_batch_autotune(const ds_job* jobs, int n, void* stream, int iters, ds_tune_result* res);
+
+/*
  * The unfused two-kernel form: a horizontal kernel writes the intermediate
  * (FP32 for float dtypes, uint8 for uint8 dtypes) to `workspace` in device
  * memory, a vertical kernel reads it back.  Same results as ds_run, bit for

@@ -41,6 +41,7 @@ ABI_SYMBOLS = (
     "ds_debug_timeout_probe", "ds_plan_create_ex", "ds_plan_get_axes", "ds_plan_get_axis_taps",
     "ds_bounds_checked", "ds_debug_bounds_probe", "ds_plan_tile_shapes", "ds_plan_set_schedule_ex",
     "ds_plan_get_schedule_ex", "ds_plan_autotune_ex", "ds_server_create", "ds_server_run", "ds_server_destroy",
+    "ds_batch_autotune",
 )
 DS_SERVE_REALTIME, DS_SERVE_COPIES, DS_SERVE_PLAIN = 1, 2, 4
 
@@ -142,6 +143,7 @@ def lib() -> ctypes.CDLL:
         "ds_server_run": (i, [vp, ctypes.POINTER(ds_request), i, i, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ds_serve_stats)]),
         "ds_server_destroy": (None, [vp]),
+        "ds_batch_autotune": (i, [vp, i, vp, i, ctypes.POINTER(ds_tune_result)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -377,6 +379,18 @@ def ds_batch_run(jobs: Iterable, stream: int = 0) -> None:
     """jobs: iterable of (plan, in_ptr, out_ptr[, n_frames])."""
     arr, n = _jobs_array(jobs)
     _check(lib().ds_batch_run(arr, n, _ptr(stream)))
+
+
+def ds_batch_autotune(jobs: Iterable, stream: int = 0, iters: int = 10) -> dict:
+    """Time schedules of the whole batch (as ds_batch_run) and keep the
+    fastest in its plans; returns each job's plan schedule (in job order), the
+    batch's time at it and at the default, and the candidates timed."""
+    jobs = list(jobs)
+    arr, n = _jobs_array(jobs)
+    r = ds_tune_result()
+    _check(lib().ds_batch_autotune(arr, n, _ptr(stream), iters, ctypes.byref(r)))
+    return {"schedules": [ds_plan_get_schedule_ex(j[0]) for j in jobs], "us_per_launch": r.best_us,
+            "default_us_per_launch": r.default_us, "candidates": r.candidates}
 
 
 def ds_plan_workspace_bytes(plan: int) -> int:

@@ -48,6 +48,41 @@ ds_status time_schedule(ds_plan* plan, const void* in, void* out, int n_frames, 
   return DS_OK;
 }
 
+// Time `iters` runs of a batch at its plans' current schedules after one
+// warm-up, in microseconds per batch.
+ds_status time_batch(const ds_job* jobs, int n, cudaStream_t st, int iters, cudaEvent_t e0, cudaEvent_t e1,
+                     float* us) {
+  ds_status s = ds_batch_run(jobs, n, st);
+  if (s != DS_OK) return s;
+  cudaEventRecord(e0, st);
+  for (int i = 0; i < iters && s == DS_OK; ++i) s = ds_batch_run(jobs, n, st);
+  cudaEventRecord(e1, st);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (s != DS_OK) return s;
+  if (e != cudaSuccess) return cuda_fail(e, "ds_batch_autotune: timing");
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  *us = ms * 1000.0f / iters;
+  return DS_OK;
+}
+
+// A batch candidate: one band and tile shape for every fast plan, and the
+// resident CTAs per SM as a rule on each plan's own occupancy (0: all that
+// fit; 1, 2: one or two fewer; 3: three quarters; 4: half).
+struct BatchCand {
+  int row_blocks, cta_rule, shape;
+};
+
+int cta_count(int rule, int occ) {
+  switch (rule) {
+    case 1: return occ - 1;
+    case 2: return occ - 2;
+    case 3: return (occ * 3) / 4;
+    case 4: return occ / 2;
+    default: return 0;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -175,6 +210,146 @@ ds_status ds_plan_autotune(ds_plan* plan, const void* in, void* out, int n_frame
   if (s != DS_OK) return s;
   if (best_row_blocks) *best_row_blocks = plan->row_blocks;
   if (best_us) *best_us = r.best_us;
+  return DS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+ds_status ds_batch_autotune(const ds_job* jobs, int n, void* stream, int iters, ds_tune_result* res) {
+  clear_error();
+  if (!jobs || n < 1 || iters < 1) {
+    set_error("ds_batch_autotune: bad arguments");
+    return DS_ERR_ARG;
+  }
+  // the distinct fast plans of the batch (a batch may hold one plan several
+  // times); general-kernel plans keep their schedule
+  std::vector<ds_plan*> plans;
+  for (int i = 0; i < n; ++i) {
+    if (!jobs[i].plan || !jobs[i].in || !jobs[i].out) {
+      set_error("ds_batch_autotune: NULL plan or pointer in job %d", i);
+      return DS_ERR_ARG;
+    }
+    ds_plan* pl = const_cast<ds_plan*>(jobs[i].plan);
+    if (pl->fast_class >= 0 && std::find(plans.begin(), plans.end(), pl) == plans.end()) plans.push_back(pl);
+  }
+  if (plans.empty()) {
+    set_error("ds_batch_autotune: no job of the batch runs on the fused kernel");
+    return DS_ERR_UNSUPPORTED;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "ds_batch_autotune: events");
+  }
+  std::vector<ds_schedule> keep(plans.size());
+  for (size_t k = 0; k < plans.size(); ++k) ds_plan_get_schedule_ex(plans[k], &keep[k]);
+  auto restore = [&]() {
+    for (size_t k = 0; k < plans.size(); ++k) ds_plan_set_schedule_ex(plans[k], &keep[k]);
+  };
+  // every plan at candidate c; the CTA rule is applied to each plan's
+  // occupancy at the candidate's shape
+  auto apply = [&](const BatchCand& c) -> ds_status {
+    for (ds_plan* pl : plans) {
+      ds_schedule sc{c.row_blocks, 0, c.shape};
+      ds_status r = ds_plan_set_schedule_ex(pl, &sc);
+      if (r != DS_OK) return r;
+      if (c.cta_rule) {
+        const int ctas = cta_count(c.cta_rule, fast_ctas_per_sm(pl));
+        if (ctas < 1) continue;
+        sc.ctas_per_sm = ctas;
+        r = ds_plan_set_schedule_ex(pl, &sc);
+        if (r != DS_OK) return r;
+      }
+    }
+    return DS_OK;
+  };
+  const BatchCand def{0, 0, 0};
+  ds_status s = apply(def);
+  {  // warm the GPU at the default schedule
+    float us = 0.0f, spent = 0.0f;
+    for (int i = 0; i < 200 && s == DS_OK && spent < kWarmMs * 1000.0f; ++i) {
+      s = time_batch(jobs, n, st, iters, e0, e1, &us);
+      spent += us * (iters + 1);
+    }
+  }
+  BatchCand best = def;
+  float best_us = 1e30f, default_us = 0.0f;
+  int tried = 0;
+  auto trial = [&](const BatchCand& c) -> ds_status {
+    ds_status r = apply(c);
+    if (r != DS_OK) return r;
+    float us = 0.0f;
+    r = time_batch(jobs, n, st, iters, e0, e1, &us);
+    if (r != DS_OK) return r;
+    ++tried;
+    if (c.row_blocks == 0 && c.cta_rule == 0 && c.shape == 0) default_us = us;
+    if (us < best_us * kMargin) {
+      best_us = us;
+      best = c;
+    }
+    return DS_OK;
+  };
+  // 1. tile shapes every plan has, at the default band (shape 0 first)
+  int shapes = 1 << 30, nby = 1;
+  for (ds_plan* pl : plans) {
+    shapes = std::min(shapes, std::max(1, ds_plan_tile_shapes(pl)));
+    nby = std::max(nby, (pl->out_h + pl->pv - 1) / pl->pv);
+  }
+  for (int sh = 0; sh < shapes && s == DS_OK; ++sh) s = trial(BatchCand{0, 0, sh});
+  // 2. fixed bands at the best shape, up to the tallest plan's block rows
+  std::vector<int> bands;
+  for (int c : {2, 3, 4, 6, 8, 10, 12, 16, 20, 24, 32, 40, 48, 64})
+    if (c <= nby) bands.push_back(c);
+  if (bands.empty() || bands.back() < nby) bands.push_back(std::min(nby, 96));
+  {
+    const int shape = best.shape;
+    for (int b : bands) {
+      if (s != DS_OK) break;
+      s = trial(BatchCand{b, 0, shape});
+    }
+  }
+  // 3. fewer resident CTAs per SM at the best shape and band
+  {
+    const BatchCand base = best;
+    for (int rule = 1; rule <= 4 && s == DS_OK; ++rule) s = trial(BatchCand{base.row_blocks, rule, base.shape});
+  }
+  // confirm a winner other than the default, alternating with the default
+  const bool is_default = best.row_blocks == 0 && best.cta_rule == 0 && best.shape == 0;
+  if (s == DS_OK && !is_default) {
+    float tb[3], td[3];
+    for (int k = 0; k < 3 && s == DS_OK; ++k) {
+      s = apply(def);
+      if (s == DS_OK) s = time_batch(jobs, n, st, iters, e0, e1, &td[k]);
+      if (s == DS_OK) s = apply(best);
+      if (s == DS_OK) s = time_batch(jobs, n, st, iters, e0, e1, &tb[k]);
+    }
+    if (s == DS_OK) {
+      std::sort(tb, tb + 3);
+      std::sort(td, td + 3);
+      default_us = td[1];
+      best_us = tb[1];
+      if (!(tb[1] < td[1] * kMargin)) {
+        best = def;
+        best_us = td[1];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == DS_OK) s = apply(best);
+  if (s != DS_OK) {
+    restore();
+    return s;
+  }
+  if (res) {
+    ds_plan_get_schedule_ex(plans[0], &res->best);
+    res->best_us = best_us;
+    res->default_us = default_us;
+    res->candidates = tried;
+  }
   return DS_OK;
 }
 

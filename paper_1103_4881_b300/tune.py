@@ -76,3 +76,35 @@ def apply_or_tune(plan: int, in_ptr: int, out_ptr: int, n_frames: int, stream: i
         cache[k] = r
         save(cache)
     return dict(r, cached=False)
+
+
+def batch_key(jobs, device_tag: str | None = None) -> str:
+    """The cache key of a batch: its jobs' plan keys (with their frame
+    counts), in job order."""
+    tag = device_tag or _device_tag()
+    return "batch[" + ";".join(key(j[0], j[3] if len(j) > 3 else 1, tag) for j in jobs) + "]"
+
+
+def apply_or_tune_batch(jobs, stream: int = 0, iters: int = 10, device_tag: str | None = None) -> dict:
+    """Set the schedules of a batch's plans from the cache, tuning the batch
+    as a whole (``ds_batch_autotune``: its jobs share one launch per kernel
+    class) on a miss.  jobs: (plan, in_ptr, out_ptr, n_frames) tuples, as for
+    ``ds_batch_run``.  Returns the schedule of each job's plan (in job order)
+    and, on a miss, the batch's time at it and at the default schedule."""
+    jobs = list(jobs)
+    k = batch_key(jobs, device_tag)
+    with _lock:
+        e = load().get(k)
+    if e and isinstance(e.get("schedules"), list) and len(e["schedules"]) == len(jobs):
+        try:
+            for j, sc in zip(jobs, e["schedules"]):
+                ds.ds_plan_set_schedule_ex(j[0], int(sc["row_blocks"]), int(sc["ctas_per_sm"]), int(sc["shape"]))
+            return dict(e, cached=True)
+        except (ds.DsError, TypeError, ValueError, KeyError):
+            pass  # an entry this library cannot take: tune again
+    r = ds.ds_batch_autotune(jobs, stream, iters)
+    with _lock:
+        cache = load()
+        cache[k] = r
+        save(cache)
+    return dict(r, cached=False)

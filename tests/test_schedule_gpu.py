@@ -1,7 +1,7 @@
 """Schedules on the GPU: every compiled tile shape of every fast class gives
 the oracle's results and the same bits as the default shape; the autotuner
 never picks a schedule slower than the default on the full-size 1080p fp32
-and 4K fp16 batches; more direct launches in flight than there are
+and 4K fp16 batches, nor the batch tuner on the 4:2:0 CIF planes; more direct launches in flight than there are
 scheduling slots (queued behind a busy stream) all complete correctly; a
 fused launch inside a capture the caller started is refused."""
 import numpy as np
@@ -90,6 +90,46 @@ def test_tuned_schedule_is_no_slower_than_the_default(name):
         assert mt <= md * 1.03, (md, mt, tuned)
     finally:
         ds.ds_destroy(pl)
+
+
+def test_batch_tuned_schedule_is_no_slower_than_the_default():
+    """The batch tuner on the 2000-frame 4:2:0 CIF workload (Y, U and V planes
+    in one launch): the same bits at the tuned schedules, and the batch no
+    slower than at the default when the two are re-timed alternately."""
+    import torch
+
+    w = synth.WORKLOADS["cif2000_yuv420_u8"]
+    plans = [ds.ds_plan_create_ex(h, ww, w.ratio, w.taps, w.vratio, w.vtaps, w.dtype) for h, ww in w.plane_shapes()]
+    try:
+        ins = [torch.from_numpy(x).cuda() for x in synth.plane_frames(w)]
+        outs = [out_buffer(pl, w.frames) for pl in plans]
+        jobs = [(pl, i.data_ptr(), o.data_ptr(), w.frames) for pl, i, o in zip(plans, ins, outs)]
+        st = stream()
+        ds.ds_batch_run(jobs, st)
+        finish()
+        want = [o.cpu().numpy() for o in outs]
+        r = ds.ds_batch_autotune(jobs, st, 10)
+        finish()
+        assert r["candidates"] >= 10 and r["us_per_launch"] <= r["default_us_per_launch"]
+        assert len(r["schedules"]) == 3
+        run = lambda: ds.ds_batch_run(jobs, st)
+        t_default, t_tuned = [], []
+        for _ in range(5):  # alternate, so drifts of the clock hit both
+            for pl in plans:
+                ds.ds_plan_set_schedule_ex(pl, 0, 0, 0)
+            t_default.append(_time(run, st, 20))
+            for pl, sc in zip(plans, r["schedules"]):
+                ds.ds_plan_set_schedule_ex(pl, sc["row_blocks"], sc["ctas_per_sm"], sc["shape"])
+            t_tuned.append(_time(run, st, 20))
+        finish()
+        for o, x in zip(outs, want):
+            np.testing.assert_array_equal(o.cpu().numpy(), x)
+        md, mt = float(np.median(t_default)), float(np.median(t_tuned))
+        print("yuv batch: default %.1f us, tuned %s %.1f us" % (md, r["schedules"], mt))
+        assert mt <= md * 1.03, (md, mt, r["schedules"])
+    finally:
+        for pl in plans:
+            ds.ds_destroy(pl)
 
 
 def test_more_launches_in_flight_than_slots(oracle):

@@ -79,3 +79,50 @@ def test_a_cache_entry_the_library_cannot_take_is_tuned_again(tmp_path, monkeypa
         assert ds.ds_plan_get_schedule_ex(pl)["shape"] == 0
     finally:
         ds.ds_destroy(pl)
+
+
+def test_batch_autotune_rejects_bad_arguments():
+    """Checked before any GPU work: no jobs, iters < 1, a NULL buffer, and a
+    batch with no job on the fused kernel."""
+    pl = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    gp = ds.ds_plan_create(100, 100, (3, 4), 4, ds.DS_F32)  # general kernels only
+    try:
+        with pytest.raises(ds.DsError) as e:
+            ds.ds_batch_autotune([], 0, 10)
+        assert e.value.status == ds.DS_ERR_ARG
+        with pytest.raises(ds.DsError) as e:
+            ds.ds_batch_autotune([(pl, 16, 16, 1)], 0, 0)
+        assert e.value.status == ds.DS_ERR_ARG
+        with pytest.raises(ds.DsError) as e:
+            ds.ds_batch_autotune([(pl, 16, 16, 1), (pl, 0, 16, 1)], 0, 10)
+        assert e.value.status == ds.DS_ERR_ARG
+        with pytest.raises(ds.DsError) as e:
+            ds.ds_batch_autotune([(gp, 16, 16, 1)], 0, 10)
+        assert e.value.status == ds.DS_ERR_UNSUPPORTED
+        assert ds.ds_plan_get_schedule_ex(pl) == {"row_blocks": 0, "ctas_per_sm": 0, "shape": 0}
+    finally:
+        ds.ds_destroy(pl)
+        ds.ds_destroy(gp)
+
+
+def test_batch_cache_key_and_hit(tmp_path, monkeypatch):
+    """A batch is cached under its jobs' keys in order; a hit sets every
+    job's plan schedule without touching a GPU."""
+    monkeypatch.setenv("DS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    y = ds.ds_plan_create_ex(288, 352, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    c = ds.ds_plan_create_ex(144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        jobs = [(y, 16, 16, 2000), (c, 16, 16, 2000), (c, 16, 16, 2000)]
+        k = tune.batch_key(jobs, "GPU|148")
+        assert k != tune.batch_key(jobs[:2], "GPU|148") and k != tune.batch_key(list(reversed(jobs)), "GPU|148")
+        assert k != tune.batch_key([(y, 16, 16, 1000)] + jobs[1:], "GPU|148")
+        assert k.count("288x352") == 1 and k.count("144x176") == 2
+        sc = [{"row_blocks": 0, "ctas_per_sm": 20, "shape": 0}, {"row_blocks": 0, "ctas_per_sm": 20, "shape": 0},
+              {"row_blocks": 0, "ctas_per_sm": 20, "shape": 0}]
+        tune.save({k: {"schedules": sc, "us_per_launch": 90.5}})
+        got = tune.apply_or_tune_batch(jobs, device_tag="GPU|148")
+        assert got["cached"]
+        assert ds.ds_plan_get_schedule_ex(y) == sc[0] and ds.ds_plan_get_schedule_ex(c) == sc[1]
+    finally:
+        ds.ds_destroy(y)
+        ds.ds_destroy(c)
