@@ -169,12 +169,26 @@ ds_status ds_server_run(ds_server* sv, const ds_request* reqs, int n, int flags,
   auto elapsed = [&]() { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); };
   ds_status status = DS_OK;
 
+  // Waiting for an arrival or a completion: the loop keeps its core, with the
+  // CPU's spin hint, rather than yielding it -- a yield on a busy host can
+  // hand the core to another process for a scheduler time slice, which then
+  // shows as request latency.
+  auto relax = []() {
+#if defined(__x86_64__) || defined(__i386__)
+    __builtin_ia32_pause();
+#elif defined(__aarch64__)
+    asm volatile("yield" ::: "memory");
+#else
+    std::this_thread::yield();
+#endif
+  };
+
   if (plain) {
     // the baseline: one plain fused launch per request, in arrival order, on one stream
     for (int k = 0; k < n && status == DS_OK; ++k) {
       const int i = order[k];
       if (realtime)
-        while (elapsed() < reqs[i].arrival_s) std::this_thread::yield();
+        while (elapsed() < reqs[i].arrival_s) relax();
       jobs[0] = ds_job{reqs[i].plan, reqs[i].in, reqs[i].out, 1};
       status = run_jobs(jobs.data(), 1, sv->streams[0]);
     }
@@ -282,7 +296,7 @@ ds_status ds_server_run(ds_server* sv, const ds_request* reqs, int n, int flags,
         }
       }
     }
-    if (!progress) std::this_thread::yield();
+    if (!progress) relax();
   }
   // leave nothing in flight (also after an error)
   for (cudaStream_t s : sv->streams) {
