@@ -84,10 +84,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, schedule=None):
-    """DRAM bytes per launch from the committed ncu captures (one entry per
-    workload and schedule), if one was taken on the current kernel source
-    with the same schedule (else None)."""
+def profiled_capture(workload: str, schedule=None):
+    """The committed one-pass ncu capture of a workload's launch (DRAM bytes,
+    warp instructions) taken on the current kernel source with the same
+    schedule, or None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -101,10 +101,37 @@ def profiled_traffic(workload: str, schedule=None):
                 continue
             if schedule is not None and e.get("schedule") is not None and e["schedule"] != schedule:
                 continue
-            return int(e["dram_bytes_per_launch"])
+            return e
     except Exception:
         pass
     return None
+
+
+def profiled_traffic(workload: str, schedule=None):
+    """DRAM bytes per launch from the committed ncu captures (one entry per
+    workload and schedule), if one was taken on the current kernel source
+    with the same schedule (else None)."""
+    e = profiled_capture(workload, schedule)
+    return int(e["dram_bytes_per_launch"]) if e else None
+
+
+def issue_roofline(workload: str, schedule, launch_s: float, clocks: dict, sms: int):
+    """Instruction issue against its peak: the launch's warp instructions
+    (committed capture) per second of the CUDA-event launch time, against
+    4 schedulers x 1 warp instruction per clock x the SM count x the median
+    SM clock sampled during the timed region.  The bound of the uint8
+    classes, whose HBM fraction alone understates how busy they are."""
+    e = profiled_capture(workload, schedule)
+    mhz = clocks.get("sm_mhz")
+    if not e or "warp_instructions_per_launch" not in e or not mhz or launch_s <= 0:
+        return None
+    inst = int(e["warp_instructions_per_launch"])
+    peak = 4.0 * sms * mhz * 1e6 / 1e9
+    achieved = inst / launch_s / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp instructions/s",
+            "frac": achieved / peak, "warp_instructions_per_launch": inst,
+            "peak_source": "4 schedulers x 1 warp instruction per clock x %d SMs x %.0f MHz (median SM clock of "
+                           "the timed region)" % (sms, mhz)}
 
 
 class ClockSampler:
@@ -448,6 +475,9 @@ def main():
         "gpu_launches": launches,
         "schedule": schedule,
     }
+    if n == synth.WORKLOADS[w.name].frames:
+        line["issue_roofline"] = issue_roofline(w.name, sched_key, launch_s, clk,
+                                                torch.cuda.get_device_properties(dev_index).multi_processor_count)
 
     if rank == 0:
         line["accuracy"] = accuracy(w, xs, outs, a)
@@ -581,6 +611,8 @@ def side_workloads(args, ds, synth, resident, timed, dev_index, peak):
             "clocks": clocks.summary(), "schedule": tuned,
             "accuracy": accuracy(wl, xs, outs, 0),
         }
+        res[name]["issue_roofline"] = issue_roofline(name, sched, us * 1e-6, res[name]["clocks"],
+                                                     torch.cuda.get_device_properties(dev_index).multi_processor_count)
         ds.ds_graph_destroy(g)
         for pl in plans:
             ds.ds_destroy(pl)

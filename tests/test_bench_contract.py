@@ -50,3 +50,22 @@ def test_committed_traffic_capture_matches_the_kernel_source():
     alg = w.frames * w.bytes_per_frame()
     assert 0.95 * alg < t < 1.2 * alg  # traffic near the algorithmic bytes: no wasted re-reads
     assert bench.profiled_traffic(bench.HEADLINE, [{"row_blocks": 3, "ctas_per_sm": 1, "shape": 1}]) is None
+
+
+def test_issue_roofline_from_the_committed_capture():
+    """The headline's committed capture also holds the launch's warp
+    instructions; the issue roofline divides them by the launch time and
+    compares with 4 warp instructions per SM per clock at the sampled clock."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sched = [{"row_blocks": 0, "ctas_per_sm": 0, "shape": 0}]
+    e = bench.profiled_capture(bench.HEADLINE, sched)
+    assert e is not None and e["warp_instructions_per_launch"] > 0
+    r = bench.issue_roofline(bench.HEADLINE, sched, 400e-6, {"sm_mhz": 2000.0}, 148)
+    assert r["peak"] == 4 * 148 * 2000.0 * 1e6 / 1e9
+    assert abs(r["achieved"] - e["warp_instructions_per_launch"] / 400e-6 / 1e9) < 1e-6
+    assert 0.0 < r["frac"] < 1.0 and r["bound"] == "issue"
+    assert bench.issue_roofline(bench.HEADLINE, sched, 400e-6, {"sm_mhz": None}, 148) is None
+    assert bench.issue_roofline(bench.HEADLINE, [{"row_blocks": 3, "ctas_per_sm": 1, "shape": 1}], 400e-6,
+                                {"sm_mhz": 2000.0}, 148) is None
