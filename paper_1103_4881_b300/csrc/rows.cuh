@@ -904,6 +904,12 @@ struct RowMath<Cl, true> {
   // else as bytes.  Not for runs of 3 bytes: there the shifts and the
   // shuffle cost as much as the byte stores they replace (measured slower).
   static constexpr bool kWordRuns = N % 4 != 0 && N >= 6 && (Cl::SBLK * P * C) % 4 == 0;
+  // V windows that start on an odd row read odd-aligned row pairs (rows 2m+1
+  // and 2m+2) with the even-parity tap pairs: KV/2 dp2a per output instead of
+  // KV/2 + 1, for two more byte permutes per pair.  Three-channel classes,
+  // where dp2a is the busier pipe, except the 3/8 vertical axis, where it
+  // measured slower (CIF RGB -0.7 %, RGB 2/3 -2.2 %, RGB 3/8 +0.5 %).
+  static constexpr bool VODD = C == 3 && KV % 2 == 0 && !(PV == 3 && Cl::QV == 8);
   template <bool CHECK, class PR>
   __device__ static __forceinline__ void v(const Row (&win)[LV], const PR& prm, T* obase, long long rowe,
                                            int rr, int OH, int n_valid, bool words) {
@@ -912,17 +918,25 @@ struct RowMath<Cl, true> {
     uint32_t o[PV][NW];
 #pragma unroll
     for (int g = 0; g < NW; ++g) {
-      uint32_t pl[NPR], ph[NPR];
+      uint32_t pl[NPR], ph[NPR], ql[NPR], qh[NPR];
 #pragma unroll
       for (int m = 0; m < NPR; ++m) {
         const int r0 = 2 * m < LV ? 2 * m : LV - 1, r1 = 2 * m + 1 < LV ? 2 * m + 1 : LV - 1;
         pl[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x5140u);
         ph[m] = __byte_perm(win[r0].w[g], win[r1].w[g], 0x7362u);
+        if constexpr (VODD) {  // odd-aligned pairs, the same interleave
+          const int q0 = 2 * m + 1 < LV ? 2 * m + 1 : LV - 1, q1 = 2 * m + 2 < LV ? 2 * m + 2 : LV - 1;
+          ql[m] = __byte_perm(win[q0].w[g], win[q1].w[g], 0x5140u);
+          qh[m] = __byte_perm(win[q0].w[g], win[q1].w[g], 0x7362u);
+        }
       }
 #pragma unroll
       for (int jv = 0; jv < PV; ++jv) {
         const int s0 = Cl::bv(jv) - BMINV;
-        const int par = s0 & 1, pr0 = (s0 - par) / 2, npair = (KV + par + 1) / 2;
+        const int par = s0 & 1;
+        const bool odd = VODD && par;  // an odd start read from odd-aligned pairs
+        const int pr0 = odd ? (s0 - 1) / 2 : (s0 - par) / 2, npair = odd ? KV / 2 : (KV + par + 1) / 2;
+        const int tpar = odd ? 0 : par;
         int v[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -930,8 +944,8 @@ struct RowMath<Cl, true> {
           int acc = 8192;
 #pragma unroll
           for (int i = 0; i < npair; ++i) {
-            const uint32_t word = (e & 2) ? ph[pr0 + i] : pl[pr0 + i];
-            acc = (e & 1) ? dp2a<1>(tpv(prm, par, jv, i), word, acc) : dp2a<0>(tpv(prm, par, jv, i), word, acc);
+            const uint32_t word = odd ? ((e & 2) ? qh[pr0 + i] : ql[pr0 + i]) : ((e & 2) ? ph[pr0 + i] : pl[pr0 + i]);
+            acc = (e & 1) ? dp2a<1>(tpv(prm, tpar, jv, i), word, acc) : dp2a<0>(tpv(prm, tpar, jv, i), word, acc);
           }
           v[e] = u8_round(acc);
         }
