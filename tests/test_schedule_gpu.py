@@ -132,6 +132,37 @@ def test_batch_tuned_schedule_is_no_slower_than_the_default():
             ds.ds_destroy(pl)
 
 
+def test_batch_autotune_on_a_mixed_batch(oracle):
+    """A batch of two fused classes and a plan on the general kernels: the
+    tuner sets schedules on the fused plans only, the general plan keeps its
+    own, and every output keeps its bits (and matches the oracle)."""
+    specs = [((120, 528), (3, 8), 8, ds.DS_F32, 5), ((90, 256), (1, 2), 6, ds.DS_U8_RGB, 7),
+             ((77, 100), (3, 4), 4, ds.DS_F32, 3)]
+    plans = [ds.ds_plan_create(h, w, r, k, dt) for (h, w), r, k, dt, _ in specs]
+    try:
+        xs = [frames(hw, dt, n, 300 + j) for j, (hw, _, _, dt, n) in enumerate(specs)]
+        ins = [to_dev(x) for x in xs]
+        outs = [out_buffer(pl, n) for pl, (_, _, _, _, n) in zip(plans, specs)]
+        jobs = [(pl, i.data_ptr(), o.data_ptr(), n) for pl, i, o, (_, _, _, _, n) in zip(plans, ins, outs, specs)]
+        st = stream()
+        ds.ds_batch_run(jobs, st)
+        finish()
+        want = [o.cpu().numpy() for o in outs]
+        r = ds.ds_batch_autotune(jobs, st, 3)
+        finish()
+        assert r["candidates"] >= 3 and r["us_per_launch"] <= r["default_us_per_launch"]
+        assert ds.ds_plan_get_schedule_ex(plans[2]) == {"row_blocks": 0, "ctas_per_sm": 0, "shape": 0}
+        ds.ds_batch_run(jobs, st)
+        finish()
+        for o, w_, x, ((h, ww), rr, k, dt, n) in zip(outs, want, xs, specs):
+            got = o.cpu().numpy()
+            np.testing.assert_array_equal(got, w_)
+            assert_parity(got, oracle_out(oracle, x, rr[0], rr[1], k, dt), dt, "mixed batch")
+    finally:
+        for pl in plans:
+            ds.ds_destroy(pl)
+
+
 def test_more_launches_in_flight_than_slots(oracle):
     """640 one-frame fused launches over 4 streams, queued behind a busy
     kernel on each stream, so that more of them are in flight than there are
