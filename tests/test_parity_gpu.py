@@ -225,6 +225,32 @@ def test_pipeline_host_buffers(oracle):
         ds.ds_destroy(pl)
 
 
+@pytest.mark.parametrize("chunk", [1, 3, 5])
+def test_pipeline_host_buffers_chroma_planes(oracle, chunk):
+    """The host-buffer pipeline on 176x144 chroma planes (CIF axes): each
+    chunk of 1, 3 or 5 frames is one launch whose tail strips run as a narrow
+    job with a part-empty group of four; the result equals the device path
+    and the oracle, bit for bit."""
+    import torch
+
+    pl = ds.ds_plan_create_ex(144, 176, (3, 8), 8, (4, 9), 8, ds.DS_U8)
+    try:
+        n = 13
+        x = frames((144, 176), ds.DS_U8, n, 170 + chunk)
+        xin = torch.from_numpy(x).pin_memory()
+        oh, ow, _ = ds.ds_plan_out_shape(pl)
+        yout = torch.zeros((n, oh, ow), dtype=torch.uint8).pin_memory()
+        pp = ds.ds_pipeline_create(pl, chunk, 2)
+        try:
+            ds.ds_pipeline_run(pp, xin.data_ptr(), yout.data_ptr(), n)
+        finally:
+            ds.ds_pipeline_destroy(pp)
+        np.testing.assert_array_equal(yout.numpy(), run_fused(pl, x))
+        assert_parity(yout.numpy(), oracle.filter_ex(x, (3, 8), 8, (4, 9), 8), ds.DS_U8, "pipeline chunk %d" % chunk)
+    finally:
+        ds.ds_destroy(pl)
+
+
 def test_constant_and_impulse_frames(oracle):
     H, W = 64, 256
     for dt in DTYPES:
